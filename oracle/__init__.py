@@ -1,0 +1,40 @@
+"""Plain FP64 CPU oracle for known-pose, preconditioned-SGD cryo-EM refinement.
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, obviously correct
+statement of what the CUDA path computes, written from Toader, Brubaker &
+Lederman, arXiv 2311.16100 (Definition 2.1, Eqs. fwd model, optim cp,
+hessian, hutch, diag est rule, thresh value, thresh, stochastic armijo and
+Algorithm 1).  Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import it; the product path never does, and the
+oracle shares no code with the CUDA path (only the seeded input generator in
+``paper_2311_16100_gb300.synth`` feeds both).
+
+Parity status per function (what pins it, see tests/test_oracle_pins.py):
+  quat_to_rot          pinned: quaternion sandwich product, axis rotations
+  nearest/trilinear    pinned: affine volumes (trilinear reproduces them
+                       exactly), identity/90-degree rotations, brute-force
+                       argmin over all grid points
+  ctf                  pinned: textbook electron wavelengths, CTF zeros
+  slice/adjoint        pinned: adjoint identity <Px, y> = <x, P*y>
+  loss_grad            pinned: central finite differences (exact for a quadratic)
+  hvp / dense H        pinned: linearity of the gradient, symmetry
+  exact_diag           pinned: |Omega_j| + lam by brute-force counting,
+                       diagonal of the dense Hessian, Proposition 3.1 bound
+  splitmix64           pinned: published test vector
+  hutchinson_diag      pinned: exact under nearest (Remark 3.3), unbiased
+                       under trilinear (z-score against the dense Hessian)
+  alpha_threshold      pinned: shell-ratio asymptotics, shell mean of diag(H)
+  alg1_step            pinned: EM M-step equivalence (nearest, exact D, eta=1),
+                       monotone decrease under the Armijo rule
+  cg_solve             pinned: closed form under nearest interpolation
+"""
+from .geometry import (ball_mask, ctf_of_s2, ctf_pixels, default_r_max, disc_mask,
+                       electron_wavelength_A, freq_axis, nearest_coords_fp32,
+                       pixel_coords, quat_to_rot, sample_points, stencil)
+from .operators import (backproject_adjoint, coverage_features, dense_hessian,
+                        exact_diag, hvp, loss, loss_grad, slice_project)
+from .hutchinson import hutchinson_diag, probe_words, rademacher_probes, splitmix64
+from .sgd import (alg1_step, alpha_threshold, cg_solve, full_rhs, rel_err,
+                  shell_counts)
+
+__all__ = [n for n in dir() if not n.startswith("_")]

@@ -1,0 +1,129 @@
+"""Oracle: threshold alpha, Algorithm 1, ground truth and error (FP64, CPU).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .geometry import ball_mask, ctf_pixels
+from .hutchinson import hutchinson_diag
+from .operators import backproject_adjoint, hvp, loss, loss_grad
+
+
+def shell_counts(M: int, R: int):
+    """(P_x(R), P_v(R)): pixels / voxels of the grid in the Fourier shell R.
+
+    Section 3.3 leaves the shell width open; we take 1-voxel shells,
+    round(|k|) = R, i.e. R^2 - R + 1 <= |k|^2 <= R^2 + R for integer R >= 1
+    (|k|^2 is an integer, so no point sits on a half-integer radius).
+    """
+    k = np.arange(M) - M // 2
+    lo, hi = R * R - R + 1, R * R + R
+    q2 = k[:, None] ** 2 + k[None, :] ** 2
+    q3 = q2[None, :, :] + (k ** 2)[:, None, None]
+    return int(np.count_nonzero((q2 >= lo) & (q2 <= hi))), \
+        int(np.count_nonzero((q3 >= lo) & (q3 <= hi)))
+
+
+def alpha_threshold(defocus_all, M, r_max, ctf, lam, scale_alpha=1.0, R=None):
+    """alpha = H-bar of Eq. (thresh value), at the maximum radius R = r_max.
+
+    H-bar = P_x(R)/P_v(R) * sum_{i=1}^N |C_i(R)|^2 + lam, the expected Hessian
+    entry at radius R for uniform orientations; C_i(R) is the CTF of image i
+    at |k| = R (ones without CTF).  ``scale_alpha`` multiplies the sum (1 when
+    ``defocus_all`` holds the whole dataset).  ``R`` overrides the radius.
+    """
+    if R is None:
+        R = r_max
+    Px, Pv = shell_counts(M, R)
+    d = np.asarray(defocus_all, dtype=np.float64)
+    if ctf is None:
+        c2 = float(d.size)
+    else:
+        c2 = sum(float(ctf_pixels(float(R * R), di, M, ctf)) ** 2 for di in d)
+    return Px / Pv * scale_alpha * float(c2) + lam
+
+
+def alg1_step(v, D, D_avg, eta_prev, k, images, R, defocus, M, r_max, interp,
+              ctf, lam, scale, alpha, beta, c, mode, n_probes=1, seed=0,
+              max_halvings=64):
+    """One iteration k (1-based) of Algorithm 1, executed literally.
+
+    mode "hutchinson": Hutchinson's estimate on the batch with fresh probes
+    (probe block k), running mean D_avg (Eq. hutch update as written in the
+    algorithm), EMA D (Eq. exp avg update), threshold (Eq. thresh).
+    mode "fixed": D is given (a precomputed preconditioner), thresholded.
+    mode "plain": no preconditioner (D-hat = I).
+    Then eta = eta_prev, v+ = v - eta D-hat^{-1} g, halving eta while the
+    stochastic Armijo condition (Eq. stochastic armijo) fails, with f_I
+    re-evaluated at every trial point.
+    Returns dict(v, D, D_avg, eta, halvings, loss, G).
+    """
+    v = np.asarray(v, dtype=np.complex128)
+    if mode == "hutchinson":
+        D_est = hutchinson_diag(R, defocus, M, r_max, interp, ctf, lam, scale,
+                                n_probes, seed, k)
+        D_avg = (k - 1) / k * D_avg + D_est / k
+        D = beta * D + (1 - beta) * D_avg
+        Dhat = np.maximum(np.abs(D), alpha)
+    elif mode == "fixed":
+        Dhat = np.maximum(np.abs(D), alpha)
+    elif mode == "plain":
+        Dhat = np.ones((M, M, M))
+    else:
+        raise ValueError(mode)
+    f0, g = loss_grad(v, images, R, defocus, M, r_max, interp, ctf, lam, scale)
+    d = g / Dhat
+    G = float(np.sum(np.abs(g) ** 2 / Dhat))
+    eta = eta_prev
+    v_new = v - eta * d
+    h = 0
+    while (loss(v_new, images, R, defocus, M, r_max, interp, ctf, lam, scale)
+           > f0 - c * eta * G) and h < max_halvings:
+        eta /= 2
+        v_new = v - eta * d
+        h += 1
+    return dict(v=v_new, D=D, D_avg=D_avg, eta=eta, halvings=h, loss=f0, G=G)
+
+
+def full_rhs(images, R, defocus, M, r_max, interp, ctf):
+    """b = sum_i P_i^* C_i x_i over the whole dataset (Eq. lin sys)."""
+    return backproject_adjoint(images, R, defocus, M, r_max, interp, ctf)
+
+
+def cg_solve(b, R, defocus, M, r_max, interp, ctf, lam, tol=1e-12, max_iter=2000):
+    """v* solving H v = b (Eq. lin sys), by conjugate gradients in FP64.
+
+    The paper computes its ground truth with L-BFGS; for lam > 0 H is SPD and
+    CG on H v = b reaches the same minimiser.  H is real, so the real and
+    imaginary parts are two independent systems solved together.
+    """
+    def Hmul(x):
+        return (hvp(x.real, R, defocus, M, r_max, interp, ctf, lam, 1.0)
+                + 1j * hvp(x.imag, R, defocus, M, r_max, interp, ctf, lam, 1.0))
+    b = np.asarray(b, dtype=np.complex128)
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = np.vdot(r, r).real
+    bn = np.sqrt(np.vdot(b, b).real)
+    for it in range(max_iter):
+        if np.sqrt(rr) <= tol * bn:
+            break
+        Hp = Hmul(p)
+        a = rr / np.vdot(p, Hp).real
+        x += a * p
+        r -= a * Hp
+        rr_new = np.vdot(r, r).real
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x, it
+
+
+def rel_err(v, v_star, M, r_max):
+    """|v - v*| / |v*| over the ball |k| <= r_max (voxels outside are unseen)."""
+    m = ball_mask(M, r_max)
+    a = np.asarray(v).ravel()[m]
+    b = np.asarray(v_star).ravel()[m]
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
