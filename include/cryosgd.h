@@ -1,0 +1,259 @@
+/*
+ * cryosgd.h -- C ABI of libcryosgd: the GPU hot path of known-pose,
+ * diagonally preconditioned SGD for cryo-EM volume refinement
+ * (Toader, Brubaker & Lederman, "Efficient high-resolution refinement in
+ * cryo-EM with stochastic gradient descent", arXiv 2311.16100).
+ *
+ * Conventions (all entry points)
+ * ------------------------------
+ * Grid.  M is the grid side, even, 4 <= M <= CS_MAX_M.  Voxel (iz, iy, ix)
+ *   has linear index (iz*M + iy)*M + ix and Fourier coordinates
+ *   (kx, ky, kz) = (ix - M/2, iy - M/2, iz - M/2); DC sits at index M/2.
+ *   Image pixel (iy, ix) has (kx, ky) as above and index iy*M + ix.  (Section
+ *   2.1 only requires the images to be the z = 0 plane of the volume grid.)
+ * Complex data.  A complex64 array is interleaved (re, im) float pairs:
+ *   a volume is float[M^3 * 2], a stack of B images float[B * M * M * 2].
+ * Poses.  rot is float[B][9], the row-major rotation matrix R_i of each image.
+ *   Pixel r = (kx, ky, 0) reads the volume at R_i^T r (Section 2.1:
+ *   (R v)(r) = v(R^T r)).  No in-plane shift (T_i = I).
+ * Disc.  Only pixels with kx^2 + ky^2 <= r_max^2 belong to the model
+ *   (1 <= r_max <= M/2 - 1).  slice_project writes 0 elsewhere; the adjoint,
+ *   loss and gradient ignore the other pixels.
+ * Interpolation.  CS_NEAREST (Eq. def nn interp): voxel at rint() of each
+ *   coordinate c_a = R[0][a]*kx + R[1][a]*ky, evaluated as two single
+ *   precision products and one sum without fused multiply-add, rounded half
+ *   to even.  CS_TRILINEAR (Eq. def tri interp): the eight corners of the
+ *   cell holding R^T r with trilinear weights.  Corners outside the grid
+ *   contribute nothing.
+ * CTF.  When enabled, C_i(q) = -(sqrt(1-A^2) sin chi + A cos chi) with
+ *   chi = pi lam df_i s^2 - (pi/2) Cs lam^3 s^4, s^2 = q / (M pixel)^2,
+ *   q = kx^2 + ky^2, lam the relativistic electron wavelength at kv.
+ *   (The paper only requires C_i real, diagonal, radially symmetric.)
+ * Memory.  Every array argument is a device pointer unless stated
+ *   otherwise; the caller owns it.  The library owns only the opaque handle
+ *   and the workspace inside it.
+ * Streams.  stream is a cudaStream_t (NULL = legacy default stream).  All
+ *   work is enqueued asynchronously on it; no call synchronises unless
+ *   stated.
+ * Errors.  Every call returns a cs_status.  Arguments are validated on the
+ *   host before anything is enqueued; on error nothing is enqueued and
+ *   cs_last_error() describes the cause.  The library never aborts, traps or
+ *   exits.  CS_ERR_CUDA reports a failed CUDA runtime call (launch or
+ *   allocation) with its message.
+ */
+#ifndef CRYOSGD_H
+#define CRYOSGD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CS_MAX_M 512
+
+typedef enum {
+  CS_OK = 0,
+  CS_ERR_ARG = 1,      /* null pointer, bad enum, non-finite scalar */
+  CS_ERR_SHAPE = 2,    /* M, r_max, B or a count out of range */
+  CS_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+  CS_ERR_TIMEOUT = 4,  /* a bounded device-side wait ran out */
+  CS_ERR_INTERNAL = 5, /* an internal consistency check failed */
+  CS_ERR_ALLOC = 6     /* workspace allocation failed */
+} cs_status;
+
+typedef enum { CS_NEAREST = 0, CS_TRILINEAR = 1 } cs_interp;
+
+typedef enum {
+  CS_PLAIN = 0,       /* no preconditioner, D-hat = I */
+  CS_HUTCHINSON = 1,  /* Algorithm 1: D estimated on the fly */
+  CS_FIXED = 2        /* D given (precomputed or learned), thresholded */
+} cs_sgd_mode;
+
+/* Microscope parameters of the CTF (Sections 2.1, 3.3). */
+typedef struct {
+  float kv;       /* accelerating voltage, kV (> 0) */
+  float cs_mm;    /* spherical aberration, mm (>= 0) */
+  float amp;      /* amplitude contrast A, 0 <= A < 1 */
+  float pixel_A;  /* pixel size, Angstrom (> 0) */
+  int enabled;    /* 0: C_i = I and defocus may be NULL */
+} cs_ctf;
+
+/* Geometry shared by every operator call. */
+typedef struct {
+  int M;        /* grid side (even, 4..CS_MAX_M) */
+  int r_max;    /* disc / ball radius in pixels (1..M/2-1) */
+  int interp;   /* cs_interp */
+  cs_ctf ctf;
+} cs_geom;
+
+typedef struct cs_handle cs_handle;
+
+/* Create a handle bound to CUDA device `device` (made current for the
+ * call).  *h receives the handle (NULL on failure).  The handle holds a
+ * lazily grown workspace; it is not thread safe: use one per host thread. */
+int cs_create(cs_handle** h, int device);
+/* Free the handle and its workspace (synchronises the device first).
+ * NULL is accepted. */
+int cs_destroy(cs_handle* h);
+/* Message of the last failed call on h ("" if none).  Owned by h. */
+const char* cs_last_error(const cs_handle* h);
+/* Static name of a status code. */
+const char* cs_status_string(int status);
+/* Grow the workspace for grids of side <= M and batches of <= max_batch
+ * images, so that later calls with those sizes allocate nothing (and can be
+ * captured in a CUDA graph).  Synchronous. */
+int cs_reserve(cs_handle* h, int M, int max_batch);
+/* Bytes of device workspace currently held by h. */
+size_t cs_workspace_bytes(const cs_handle* h);
+
+/* Pose -> rotation.  quat float[B][4] unit quaternions (w, x, y, z),
+ * Hamilton convention (R v = q (0, v) q*; normalised first); rot float[B][9]
+ * row-major R.  The paper's pose carries R directly (Definition 2.1); this
+ * converts the usual quaternion parameterisation. */
+int cs_quat_to_rot(cs_handle* h, const float* quat, int B, float* rot,
+                   void* stream);
+
+/* Forward operator (Eq. fwd model without noise): out_i = C_i P_i v for
+ * i < B.  vol complex64[M^3]; out complex64[B][M][M] (overwritten, 0 outside
+ * the disc); defocus float[B] in Angstrom (may be NULL if CTF disabled). */
+int cs_slice_project(cs_handle* h, const cs_geom* g, const float* vol,
+                     const float* rot, const float* defocus, int B, float* out,
+                     void* stream);
+
+/* Adjoint (Definition 2.1, P^* = conjugate transpose):
+ * vol_accum += scale * sum_i P_i^* C_i y_i.  images complex64[B][M][M];
+ * vol_accum complex64[M^3] is ACCUMULATED into (the caller zeroes it), so a
+ * batch split across calls (or devices) sums to the unsplit result. */
+int cs_backproject_adjoint(cs_handle* h, const cs_geom* g, const float* images,
+                           const float* rot, const float* defocus, int B,
+                           float scale, float* vol_accum, void* stream);
+
+/* Mini-batch loss and gradient (Eq. optim cp with batch scale, Section 3):
+ *   f = scale/2 sum_i |x_i - C_i P_i v|^2 + lambda/2 |v|^2,
+ *   grad = scale sum_i P_i^* C_i (C_i P_i v - x_i) + lambda v.
+ * vol, images as above; grad complex64[M^3] is OVERWRITTEN; loss is a
+ * device double (may be NULL) OVERWRITTEN with f.  scale = N/|I| for a batch
+ * I of a dataset of N images.  The loss sum is deterministic. */
+int cs_loss_grad(cs_handle* h, const cs_geom* g, const float* vol,
+                 const float* images, const float* rot, const float* defocus,
+                 int B, float lambda, float scale, float* grad, double* loss,
+                 void* stream);
+
+/* Hessian-vector product (Eq. hessian with CTF):
+ *   Hz = scale sum_i P_i^* C_i^2 P_i z + lambda z,  z, Hz real float[M^3]
+ * (Hz overwritten; z and Hz must not alias). */
+int cs_hvp(cs_handle* h, const cs_geom* g, const float* z, const float* rot,
+           const float* defocus, int B, float lambda, float scale, float* Hz,
+           void* stream);
+
+/* Hutchinson's diagonal estimate (Eq. hutch) with K = n_probes (1..32)
+ * Rademacher probes on the mini-batch Hessian:
+ *   diag_out = (1/K) sum_k z_k (.) H z_k   (float[M^3], overwritten).
+ * Probe k of voxel j is -1 if bit k of W_j is set, +1 otherwise, where W_j
+ * is the low 32 bits of output number probe_block*M^3 + j of a SplitMix64
+ * stream seeded with `seed`.  Computed exactly (up to rounding) without
+ * forming the K products separately. */
+int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
+                       const float* defocus, int B, float lambda, float scale,
+                       int n_probes, uint64_t seed, uint64_t probe_block,
+                       float* diag_out, void* stream);
+
+/* Exact diagonal of the mini-batch Hessian (Eq. hessian; under nearest
+ * interpolation without CTF it is |Omega_j| + lambda, Eq. H diag):
+ *   diag_out_j = lambda + scale sum_i sum_p C_ip^2 w_pj^2,
+ * and the per-voxel features coverage_j = sum_i sum_p w_pj (the pose
+ * coverage count |Omega_j| of Section 3.1 under nearest interpolation) and
+ * ctf2w_j = sum_i sum_p C_ip^2 w_pj.  All float[M^3], overwritten; each of
+ * the three outputs may be NULL. */
+int cs_exact_diag(cs_handle* h, const cs_geom* g, const float* rot,
+                  const float* defocus, int B, float lambda, float scale,
+                  float* diag_out, float* coverage_out, float* ctf2w_out,
+                  void* stream);
+
+/* Threshold alpha of Eq. (thresh value) at R = r_max:
+ *   alpha = P_x(R)/P_v(R) * scale_alpha * sum_{i<N} C_i(R)^2 + lambda,
+ * with 1-voxel Fourier shells (round(|k|) = R) counted on the grid and
+ * C_i(R) the CTF of image i at |k| = R (1 without CTF).  defocus_all
+ * float[N] (may be NULL without CTF); alpha_out one device double. */
+int cs_threshold_alpha(cs_handle* h, const cs_geom* g, const float* defocus_all,
+                       int N, double lambda, double scale_alpha,
+                       double* alpha_out, void* stream);
+
+/* Scalars of the SGD state, one device double each (index into
+ * cs_sgd_state.scalars). */
+enum {
+  CS_S_ETA = 0,      /* in/out: step size eta (eta^(k-1) in, eta^(k) out) */
+  CS_S_K = 1,        /* in/out: iterations done; the step runs k+1 */
+  CS_S_ALPHA = 2,    /* in: threshold alpha of Eq. (thresh) */
+  CS_S_LOSS = 3,     /* out: f_I(v^(k)) before the step */
+  CS_S_G = 4,        /* out: |grad|^2 in the D-hat^{-1} norm */
+  CS_S_Q = 5,        /* out: curvature of f_I along the step direction */
+  CS_S_HALVINGS = 6, /* out: number of halvings of eta in this step */
+  CS_S_STATUS = 7,   /* out: 0 ok, 1 no descent (G = 0 or Q <= 0) */
+  CS_NSCALARS = 8
+};
+
+/* State of Algorithm 1 (Section 3.4).  Arrays are device float[M^3]
+ * (v complex64[M^3]); all are owned by the caller and updated in place. */
+typedef struct {
+  float* v;          /* iterate v^(k) */
+  float* D;          /* HUTCHINSON: D^(k-1) in (init I), D^(k) out; FIXED: D */
+  float* D_avg;      /* HUTCHINSON: running Hutchinson mean (init 0) */
+  double* scalars;   /* device double[CS_NSCALARS] */
+  int mode;          /* cs_sgd_mode */
+  int n_probes;      /* Rademacher probes per step (1..32, HUTCHINSON) */
+  uint64_t seed;     /* probe seed; step k uses probe block k */
+  float beta;        /* EMA weight of Eq. (exp avg update), 0 < beta < 1 */
+  float c;           /* Armijo constant of Eq. (stochastic armijo), 0 < c < 1 */
+  int max_halvings;  /* cap on halvings per step (>= 0) */
+} cs_sgd_state;
+
+/* One iteration of Algorithm 1 on the mini-batch (images, rot, defocus):
+ *   HUTCHINSON: D_est = Hutchinson(batch, probe block k+1);
+ *     D_avg = k/(k+1) D_avg + D_est/(k+1); D = beta D + (1-beta) D_avg;
+ *   D-hat = max(|D|, alpha) (PLAIN: I);  g = grad f_I(v);  d = g / D-hat;
+ *   eta = eta_prev 2^-m with the smallest m >= 0 such that the stochastic
+ *   Armijo condition holds: since f_I is quadratic, f_I(v - eta d) =
+ *   f_I(v) - eta G + eta^2 Q / 2 with G = <g, d>, Q = <d, H_I d>, so the
+ *   condition is eta <= 2 (1 - c) G / Q, tested without re-evaluating f_I;
+ *   v = v - eta d; k = k + 1.
+ * Stream ordered, no host synchronisation; uses the handle's workspace
+ * (call cs_reserve first to make the step capturable in a CUDA graph). */
+int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
+                        const float* images, const float* rot,
+                        const float* defocus, int B, float lambda, float scale,
+                        void* stream);
+
+/* Phases of cs_precond_sgd_step timed by the profiler. */
+enum {
+  CS_PH_PRECOND = 0,   /* probe words, Hutchinson estimate, D update (or D-hat) */
+  CS_PH_LOSS_GRAD = 1, /* fused forward, residual, loss and adjoint scatter */
+  CS_PH_DIRECTION = 2, /* d = g / D-hat and its norms */
+  CS_PH_CURVATURE = 3, /* |C P d|^2 for the Armijo step */
+  CS_PH_UPDATE = 4,    /* eta and v -= eta d */
+  CS_NPHASES = 5
+};
+
+/* Per-phase device timing of cs_precond_sgd_step with CUDA events recorded
+ * on the call's stream.  cs_profile_enable(h, 1) starts a fresh record (up to
+ * max_steps steps; later steps are not timed), 0 stops recording.
+ * cs_profile_read synchronises on the recorded events and writes, per phase,
+ * the summed milliseconds and the number of timed steps (arrays of
+ * CS_NPHASES, host memory). */
+int cs_profile_enable(cs_handle* h, int enable, int max_steps);
+int cs_profile_read(cs_handle* h, double* ms, int* counts);
+
+/* Kernels launched by this library in this process so far (all handles). */
+uint64_t cs_kernel_launches(void);
+
+/* Relative error over the ball |k| <= r_max:
+ *   |v - v_ref| / |v_ref| -> *out (device double). */
+int cs_rel_err(cs_handle* h, const cs_geom* g, const float* v, const float* v_ref,
+               double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRYOSGD_H */

@@ -1,0 +1,566 @@
+// C ABI of libcryosgd (declared in include/cryosgd.h): handle, workspace,
+// host-side argument validation and the stream-ordered composition of the
+// kernels into the calls of the paper's problem statement.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+
+#include "internal.h"
+
+namespace cs {
+
+std::atomic<uint64_t> g_launches{0};
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+size_t workspace_bytes(int M) {
+  const size_t n = (size_t)M * M * M;
+  return align256(n * sizeof(float2)) * 2 + align256(n * sizeof(float)) * 2 +
+         align256(n * sizeof(uint32_t)) + align256(kPartSlots * sizeof(double));
+}
+
+Workspace carve(void* base, int M) {
+  const size_t n = (size_t)M * M * M;
+  char* p = static_cast<char*>(base);
+  Workspace w;
+  w.g = reinterpret_cast<float2*>(p);     p += align256(n * sizeof(float2));
+  w.d = reinterpret_cast<float2*>(p);     p += align256(n * sizeof(float2));
+  w.dhat = reinterpret_cast<float*>(p);   p += align256(n * sizeof(float));
+  w.dest = reinterpret_cast<float*>(p);   p += align256(n * sizeof(float));
+  w.bits = reinterpret_cast<uint32_t*>(p); p += align256(n * sizeof(uint32_t));
+  w.part = reinterpret_cast<double*>(p);
+  return w;
+}
+
+Geo make_geo(const cs_geom& g) {
+  Geo G{};
+  G.M = g.M;
+  G.half = g.M / 2;
+  G.r2max = g.r_max * g.r_max;
+  G.interp = g.interp;
+  G.ctf_on = g.ctf.enabled ? 1 : 0;
+  if (G.ctf_on) {
+    const double V = (double)g.ctf.kv * 1e3;
+    const double lam = 12.2643 / std::sqrt(V * (1.0 + 0.978466e-6 * V));
+    const double box = (double)g.M * (double)g.ctf.pixel_A;
+    const double ka = lam / (box * box);
+    const double kb = 0.5 * (double)g.ctf.cs_mm * 1e7 * lam * lam * lam / (box * box * box * box);
+    G.ka_hi = (float)ka;
+    G.ka_lo = (float)(ka - (double)G.ka_hi);
+    G.kb = (float)kb;
+    const double A = (double)g.ctf.amp;
+    G.wsin = (float)std::sqrt(1.0 - A * A);
+    G.wcos = (float)A;
+  }
+  return G;
+}
+
+int pixel_grid(int num_sms, int B, int M) {
+  const long nch = ((long)M * M + kBlock - 1) / kBlock;
+  const long total = (long)B * nch;
+  const long cap = (long)num_sms * 8;   // 8 blocks of 256 threads per SM
+  long g = total < cap ? total : cap;
+  return (int)(g > 0 ? g : 1);
+}
+
+}  // namespace cs
+
+using namespace cs;
+
+namespace {
+
+int fail(cs_handle* h, int code, const char* fmt, ...) {
+  if (h) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    h->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(cs_handle* h, cudaError_t e, const char* what) {
+  return fail(h, CS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceScope {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) err = cudaSetDevice(dev);
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+int check_geom(cs_handle* h, const cs_geom* g) {
+  if (!g) return fail(h, CS_ERR_ARG, "geometry pointer is NULL");
+  if (g->M < 4 || g->M > CS_MAX_M || (g->M & 1))
+    return fail(h, CS_ERR_SHAPE, "M=%d must be even and in [4, %d]", g->M, CS_MAX_M);
+  if (g->r_max < 1 || g->r_max > g->M / 2 - 1)
+    return fail(h, CS_ERR_SHAPE, "r_max=%d must be in [1, M/2-1=%d]", g->r_max, g->M / 2 - 1);
+  if (g->interp != CS_NEAREST && g->interp != CS_TRILINEAR)
+    return fail(h, CS_ERR_ARG, "interp=%d is not CS_NEAREST or CS_TRILINEAR", g->interp);
+  if (g->ctf.enabled) {
+    const cs_ctf& c = g->ctf;
+    if (!(is_finite(c.kv) && c.kv > 0) || !(is_finite(c.pixel_A) && c.pixel_A > 0) ||
+        !(is_finite(c.cs_mm) && c.cs_mm >= 0) || !(is_finite(c.amp) && c.amp >= 0 && c.amp < 1))
+      return fail(h, CS_ERR_ARG, "CTF parameters out of range (kv>0, pixel>0, Cs>=0, 0<=A<1)");
+  }
+  return CS_OK;
+}
+
+int check_batch(cs_handle* h, const cs_geom* g, int B, const float* rot,
+                const float* defocus) {
+  if (B < 0) return fail(h, CS_ERR_SHAPE, "batch size B=%d is negative", B);
+  const long nch = ((long)g->M * g->M + kBlock - 1) / kBlock;
+  if ((long)B * nch > 0x7fffffffL || (long)B * g->M * g->M * 2 > (long)1 << 62)
+    return fail(h, CS_ERR_SHAPE, "batch size B=%d too large for M=%d", B, g->M);
+  if (B > 0 && !rot) return fail(h, CS_ERR_ARG, "rot is NULL");
+  if (B > 0 && g->ctf.enabled && !defocus)
+    return fail(h, CS_ERR_ARG, "defocus is NULL but the CTF is enabled");
+  return CS_OK;
+}
+
+int ensure_ws(cs_handle* h, int M, Workspace* w) {
+  const size_t need = workspace_bytes(M);
+  if (h->ws_bytes < need) {
+    if (const char* f = getenv("CS_FAULT_INJECT_ALLOC"))
+      if (f[0] == '1') return fail(h, CS_ERR_ALLOC, "workspace allocation failed (injected)");
+    if (h->ws) {
+      cudaError_t e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return cuda_fail(h, e, "synchronise before workspace growth");
+      cudaFree(h->ws);
+      h->ws = nullptr;
+      h->ws_bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, CS_ERR_ALLOC, "workspace of %zu bytes: %s", need, cudaGetErrorString(e));
+    }
+    h->ws = p;
+    h->ws_bytes = need;
+  }
+  *w = carve(h->ws, M);
+  return CS_OK;
+}
+
+inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+#define CS_TRY(expr)             \
+  do {                           \
+    int _rc = (expr);            \
+    if (_rc != CS_OK) return _rc; \
+  } while (0)
+
+#define CS_CUDA(expr, what)                          \
+  do {                                               \
+    cudaError_t _e = (expr);                         \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, what); \
+  } while (0)
+
+#define CS_SCOPE(h)                                                   \
+  DeviceScope _scope((h)->device);                                    \
+  if (_scope.err != cudaSuccess) return cuda_fail((h), _scope.err, "cudaSetDevice")
+
+// Records boundary event `b` (0..CS_NPHASES) of the current timed step.
+void prof_mark(cs_handle* h, int b, cudaStream_t s) {
+  if (!h->prof || h->prof_steps >= h->prof_max_steps) return;
+  const size_t i = (size_t)h->prof_steps * (CS_NPHASES + 1) + b;
+  if (i < h->prof_events.size()) cudaEventRecord(h->prof_events[i], s);
+  if (b == CS_NPHASES) ++h->prof_steps;
+}
+
+void prof_free(cs_handle* h) {
+  for (cudaEvent_t e : h->prof_events) cudaEventDestroy(e);
+  h->prof_events.clear();
+  h->prof_steps = 0;
+  h->prof_max_steps = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cs_create(cs_handle** out, int device) {
+  if (!out) return CS_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return CS_ERR_CUDA;
+  }
+  if (device < 0 || device >= n) return CS_ERR_ARG;
+  cs_handle* h = new (std::nothrow) cs_handle();
+  if (!h) return CS_ERR_ALLOC;
+  h->device = device;
+  {
+    DeviceScope scope(device);
+    if (scope.err != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return CS_ERR_CUDA;
+    }
+  }
+  *out = h;
+  return CS_OK;
+}
+
+int cs_destroy(cs_handle* h) {
+  if (!h) return CS_OK;
+  {
+    DeviceScope scope(h->device);
+    if (h->ws) {
+      cudaDeviceSynchronize();
+      cudaFree(h->ws);
+    }
+    prof_free(h);
+  }
+  delete h;
+  return CS_OK;
+}
+
+const char* cs_last_error(const cs_handle* h) { return h ? h->err.c_str() : ""; }
+
+const char* cs_status_string(int s) {
+  switch (s) {
+    case CS_OK: return "CS_OK";
+    case CS_ERR_ARG: return "CS_ERR_ARG";
+    case CS_ERR_SHAPE: return "CS_ERR_SHAPE";
+    case CS_ERR_CUDA: return "CS_ERR_CUDA";
+    case CS_ERR_TIMEOUT: return "CS_ERR_TIMEOUT";
+    case CS_ERR_INTERNAL: return "CS_ERR_INTERNAL";
+    case CS_ERR_ALLOC: return "CS_ERR_ALLOC";
+    default: return "CS_UNKNOWN";
+  }
+}
+
+int cs_reserve(cs_handle* h, int M, int max_batch) {
+  if (!h) return CS_ERR_ARG;
+  if (M < 4 || M > CS_MAX_M || (M & 1))
+    return fail(h, CS_ERR_SHAPE, "M=%d must be even and in [4, %d]", M, CS_MAX_M);
+  if (max_batch < 0) return fail(h, CS_ERR_SHAPE, "max_batch=%d is negative", max_batch);
+  CS_SCOPE(h);
+  Workspace w;
+  CS_TRY(ensure_ws(h, M, &w));
+  CS_CUDA(cudaDeviceSynchronize(), "cs_reserve");
+  return CS_OK;
+}
+
+size_t cs_workspace_bytes(const cs_handle* h) { return h ? h->ws_bytes : 0; }
+
+int cs_quat_to_rot(cs_handle* h, const float* quat, int B, float* rot, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  if (B < 0) return fail(h, CS_ERR_SHAPE, "B=%d is negative", B);
+  if (B == 0) return CS_OK;
+  if (!quat || !rot) return fail(h, CS_ERR_ARG, "quat or rot is NULL");
+  CS_SCOPE(h);
+  CS_CUDA(launch_quat_to_rot(quat, B, rot, S(stream)), "quat_to_rot launch");
+  return CS_OK;
+}
+
+int cs_slice_project(cs_handle* h, const cs_geom* g, const float* vol, const float* rot,
+                     const float* defocus, int B, float* out, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_geom(h, g));
+  CS_TRY(check_batch(h, g, B, rot, defocus));
+  if (B == 0) return CS_OK;
+  if (!vol || !out) return fail(h, CS_ERR_ARG, "vol or out is NULL");
+  CS_SCOPE(h);
+  Geo G = make_geo(*g);
+  CS_CUDA(launch_slice_project(G, reinterpret_cast<const float2*>(vol), rot, defocus, B,
+                               reinterpret_cast<float2*>(out),
+                               pixel_grid(h->num_sms, B, g->M), S(stream)),
+          "slice_project launch");
+  return CS_OK;
+}
+
+int cs_backproject_adjoint(cs_handle* h, const cs_geom* g, const float* images,
+                           const float* rot, const float* defocus, int B, float scale,
+                           float* vol_accum, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_geom(h, g));
+  CS_TRY(check_batch(h, g, B, rot, defocus));
+  if (!is_finite(scale)) return fail(h, CS_ERR_ARG, "scale is not finite");
+  if (B == 0) return CS_OK;
+  if (!images || !vol_accum) return fail(h, CS_ERR_ARG, "images or vol_accum is NULL");
+  CS_SCOPE(h);
+  Geo G = make_geo(*g);
+  CS_CUDA(launch_backproject(G, reinterpret_cast<const float2*>(images), rot, defocus, B,
+                             scale, reinterpret_cast<float2*>(vol_accum),
+                             pixel_grid(h->num_sms, B, g->M), S(stream)),
+          "backproject launch");
+  return CS_OK;
+}
+
+int cs_loss_grad(cs_handle* h, const cs_geom* g, const float* vol, const float* images,
+                 const float* rot, const float* defocus, int B, float lambda, float scale,
+                 float* grad, double* loss, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_geom(h, g));
+  CS_TRY(check_batch(h, g, B, rot, defocus));
+  if (!is_finite(lambda) || !is_finite(scale)) return fail(h, CS_ERR_ARG, "lambda/scale not finite");
+  if (!vol || !grad || (B > 0 && !images))
+    return fail(h, CS_ERR_ARG, "vol, grad or images is NULL");
+  CS_SCOPE(h);
+  Workspace w;
+  CS_TRY(ensure_ws(h, g->M, &w));
+  Geo G = make_geo(*g);
+  int nvv = 0;
+  CS_CUDA(launch_loss_grad(G, reinterpret_cast<const float2*>(vol),
+                           reinterpret_cast<const float2*>(images), rot, defocus, B,
+                           lambda, scale, reinterpret_cast<float2*>(grad), loss, w.part,
+                           w.part + kPartRegion, &nvv, pixel_grid(h->num_sms, B, g->M),
+                           h->num_sms, S(stream)),
+          "loss_grad launch");
+  return CS_OK;
+}
+
+int cs_hvp(cs_handle* h, const cs_geom* g, const float* z, const float* rot,
+           const float* defocus, int B, float lambda, float scale, float* Hz,
+           void* stream) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_geom(h, g));
+  CS_TRY(check_batch(h, g, B, rot, defocus));
+  if (!is_finite(lambda) || !is_finite(scale)) return fail(h, CS_ERR_ARG, "lambda/scale not finite");
+  if (!z || !Hz) return fail(h, CS_ERR_ARG, "z or Hz is NULL");
+  if (z == Hz) return fail(h, CS_ERR_ARG, "z and Hz must not alias");
+  CS_SCOPE(h);
+  Geo G = make_geo(*g);
+  CS_CUDA(launch_hvp(G, z, rot, defocus, B, lambda, scale, Hz,
+                     pixel_grid(h->num_sms, B, g->M), h->num_sms, S(stream)),
+          "hvp launch");
+  return CS_OK;
+}
+
+int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
+                       const float* defocus, int B, float lambda, float scale,
+                       int n_probes, uint64_t seed, uint64_t probe_block, float* diag_out,
+                       void* stream) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_geom(h, g));
+  CS_TRY(check_batch(h, g, B, rot, defocus));
+  if (!is_finite(lambda) || !is_finite(scale)) return fail(h, CS_ERR_ARG, "lambda/scale not finite");
+  if (n_probes < 1 || n_probes > 32)
+    return fail(h, CS_ERR_SHAPE, "n_probes=%d must be in [1, 32]", n_probes);
+  if (!diag_out) return fail(h, CS_ERR_ARG, "diag_out is NULL");
+  CS_SCOPE(h);
+  Workspace w;
+  CS_TRY(ensure_ws(h, g->M, &w));
+  Geo G = make_geo(*g);
+  if (g->interp == CS_TRILINEAR)
+    CS_CUDA(launch_probe_bits(g->M, seed, probe_block, nullptr, w.bits, h->num_sms, S(stream)),
+            "probe_bits launch");
+  CS_CUDA(launch_hutchinson(G, w.bits, rot, defocus, B, lambda, scale, n_probes, diag_out,
+                            pixel_grid(h->num_sms, B, g->M), h->num_sms, S(stream)),
+          "hutchinson launch");
+  return CS_OK;
+}
+
+int cs_exact_diag(cs_handle* h, const cs_geom* g, const float* rot, const float* defocus,
+                  int B, float lambda, float scale, float* diag_out, float* coverage_out,
+                  float* ctf2w_out, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_geom(h, g));
+  CS_TRY(check_batch(h, g, B, rot, defocus));
+  if (!is_finite(lambda) || !is_finite(scale)) return fail(h, CS_ERR_ARG, "lambda/scale not finite");
+  if (!diag_out && !coverage_out && !ctf2w_out) return CS_OK;
+  CS_SCOPE(h);
+  Geo G = make_geo(*g);
+  CS_CUDA(launch_exact_diag(G, rot, defocus, B, lambda, scale, diag_out, coverage_out,
+                            ctf2w_out, pixel_grid(h->num_sms, B, g->M), h->num_sms,
+                            S(stream)),
+          "exact_diag launch");
+  return CS_OK;
+}
+
+int cs_threshold_alpha(cs_handle* h, const cs_geom* g, const float* defocus_all, int N,
+                       double lambda, double scale_alpha, double* alpha_out,
+                       void* stream) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_geom(h, g));
+  if (N < 0) return fail(h, CS_ERR_SHAPE, "N=%d is negative", N);
+  if (!alpha_out) return fail(h, CS_ERR_ARG, "alpha_out is NULL");
+  if (N > 0 && g->ctf.enabled && !defocus_all)
+    return fail(h, CS_ERR_ARG, "defocus_all is NULL but the CTF is enabled");
+  if (!is_finite(lambda) || !is_finite(scale_alpha))
+    return fail(h, CS_ERR_ARG, "lambda/scale_alpha not finite");
+  // 1-voxel shells round(|k|) = R: R^2 - R + 1 <= |k|^2 <= R^2 + R
+  const long R = g->r_max, lo = R * R - R + 1, hi = R * R + R;
+  const int M = g->M, half = M / 2;
+  long px = 0, pv = 0;
+  for (int y = -half; y < half; ++y)
+    for (int x = -half; x < half; ++x) {
+      const long q2 = (long)x * x + (long)y * y;
+      if (q2 >= lo && q2 <= hi) ++px;
+      if (q2 > hi) continue;
+      for (int z = -half; z < half; ++z) {
+        const long q3 = q2 + (long)z * z;
+        if (q3 >= lo && q3 <= hi) ++pv;
+      }
+    }
+  if (pv == 0) return fail(h, CS_ERR_INTERNAL, "empty 3-D shell at R=%ld", R);
+  CS_SCOPE(h);
+  Geo G = make_geo(*g);
+  CS_CUDA(launch_alpha(G, defocus_all, N, (double)px / (double)pv, lambda, scale_alpha,
+                       alpha_out, S(stream)),
+          "alpha launch");
+  return CS_OK;
+}
+
+int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
+                        const float* images, const float* rot, const float* defocus, int B,
+                        float lambda, float scale, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_geom(h, g));
+  CS_TRY(check_batch(h, g, B, rot, defocus));
+  if (!st) return fail(h, CS_ERR_ARG, "state is NULL");
+  if (!is_finite(lambda) || !is_finite(scale)) return fail(h, CS_ERR_ARG, "lambda/scale not finite");
+  if (!st->v || !st->scalars || (B > 0 && !images))
+    return fail(h, CS_ERR_ARG, "state.v, state.scalars or images is NULL");
+  if (st->mode != CS_PLAIN && st->mode != CS_HUTCHINSON && st->mode != CS_FIXED)
+    return fail(h, CS_ERR_ARG, "mode=%d is not a cs_sgd_mode", st->mode);
+  if (st->mode != CS_PLAIN && !st->D) return fail(h, CS_ERR_ARG, "state.D is NULL");
+  if (st->mode == CS_HUTCHINSON) {
+    if (!st->D_avg) return fail(h, CS_ERR_ARG, "state.D_avg is NULL");
+    if (st->n_probes < 1 || st->n_probes > 32)
+      return fail(h, CS_ERR_SHAPE, "n_probes=%d must be in [1, 32]", st->n_probes);
+    if (!(st->beta > 0.f && st->beta < 1.f))
+      return fail(h, CS_ERR_ARG, "beta=%g must be in (0, 1)", (double)st->beta);
+  }
+  if (!(st->c > 0.f && st->c < 1.f)) return fail(h, CS_ERR_ARG, "c=%g must be in (0, 1)", (double)st->c);
+  if (st->max_halvings < 0) return fail(h, CS_ERR_ARG, "max_halvings is negative");
+  CS_SCOPE(h);
+  Workspace w;
+  CS_TRY(ensure_ws(h, g->M, &w));
+  const Geo G = make_geo(*g);
+  const int n = g->M * g->M * g->M;
+  const int grid = pixel_grid(h->num_sms, B, g->M);
+  cudaStream_t s = S(stream);
+  double* pL = w.part;                   // data-term partials
+  double* pV = w.part + kPartRegion;     // |v|^2 partials
+  double* pD = w.part + 2 * kPartRegion; // direction partials (G, |d|^2)
+  double* pQ = w.part + 3 * kPartRegion; // curvature partials
+  const float* dhat = nullptr;
+  prof_mark(h, 0, s);
+  if (st->mode == CS_HUTCHINSON) {
+    if (g->interp == CS_TRILINEAR)
+      CS_CUDA(launch_probe_bits(g->M, st->seed, 0, st->scalars + CS_S_K, w.bits, h->num_sms, s),
+              "probe_bits launch");
+    CS_CUDA(launch_hutchinson(G, w.bits, rot, defocus, B, lambda, scale, st->n_probes,
+                              w.dest, grid, h->num_sms, s),
+            "hutchinson launch");
+    CS_CUDA(launch_precond_update(n, w.dest, st->D, st->D_avg, w.dhat, st->scalars,
+                                  st->beta, h->num_sms, s),
+            "precond_update launch");
+    dhat = w.dhat;
+  } else if (st->mode == CS_FIXED) {
+    CS_CUDA(launch_fixed_dhat(n, st->D, w.dhat, st->scalars, h->num_sms, s),
+            "fixed_dhat launch");
+    dhat = w.dhat;
+  }
+  int nvv = 0, nd = 0;
+  prof_mark(h, CS_PH_LOSS_GRAD, s);
+  CS_CUDA(launch_loss_grad(G, reinterpret_cast<const float2*>(st->v),
+                           reinterpret_cast<const float2*>(images), rot, defocus, B, lambda,
+                           scale, w.g, nullptr, pL, pV, &nvv, grid, h->num_sms, s),
+          "loss_grad launch");
+  prof_mark(h, CS_PH_DIRECTION, s);
+  CS_CUDA(launch_direction(n, w.g, dhat, w.d, pD, &nd, h->num_sms, s), "direction launch");
+  prof_mark(h, CS_PH_CURVATURE, s);
+  if (B > 0)
+    CS_CUDA(launch_curvature(G, w.d, rot, defocus, B, pQ, grid, s), "curvature launch");
+  prof_mark(h, CS_PH_UPDATE, s);
+  CS_CUDA(launch_eta(st->scalars, pL, B > 0 ? grid : 0, pV, nvv, pD, pD + nd, nd, pQ,
+                     B > 0 ? grid : 0, lambda, scale, st->c, st->max_halvings, s),
+          "eta launch");
+  CS_CUDA(launch_update(n, reinterpret_cast<float2*>(st->v), w.d, st->scalars, h->num_sms, s),
+          "update launch");
+  prof_mark(h, CS_NPHASES, s);
+  return CS_OK;
+}
+
+int cs_profile_enable(cs_handle* h, int enable, int max_steps) {
+  if (!h) return CS_ERR_ARG;
+  if (enable && max_steps < 1) return fail(h, CS_ERR_ARG, "max_steps=%d must be >= 1", max_steps);
+  CS_SCOPE(h);
+  if (!enable) {
+    h->prof = false;
+    return CS_OK;
+  }
+  CS_CUDA(cudaDeviceSynchronize(), "profile_enable");
+  prof_free(h);
+  const size_t n = (size_t)max_steps * (CS_NPHASES + 1);
+  h->prof_events.reserve(n);
+  for (size_t i = 0; i < n; ++i) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) {
+      prof_free(h);
+      return cuda_fail(h, err, "cudaEventCreate");
+    }
+    h->prof_events.push_back(e);
+  }
+  h->prof_max_steps = max_steps;
+  h->prof_steps = 0;
+  h->prof = true;
+  return CS_OK;
+}
+
+int cs_profile_read(cs_handle* h, double* ms, int* counts) {
+  if (!h) return CS_ERR_ARG;
+  if (!ms || !counts) return fail(h, CS_ERR_ARG, "ms or counts is NULL");
+  CS_SCOPE(h);
+  for (int p = 0; p < CS_NPHASES; ++p) {
+    ms[p] = 0.0;
+    counts[p] = 0;
+  }
+  for (int st = 0; st < h->prof_steps; ++st) {
+    const cudaEvent_t* e = &h->prof_events[(size_t)st * (CS_NPHASES + 1)];
+    CS_CUDA(cudaEventSynchronize(e[CS_NPHASES]), "cudaEventSynchronize");
+    for (int p = 0; p < CS_NPHASES; ++p) {
+      float t = 0.f;
+      CS_CUDA(cudaEventElapsedTime(&t, e[p], e[p + 1]), "cudaEventElapsedTime");
+      ms[p] += t;
+      counts[p] += 1;
+    }
+  }
+  return CS_OK;
+}
+
+uint64_t cs_kernel_launches(void) { return g_launches.load(); }
+
+int cs_rel_err(cs_handle* h, const cs_geom* g, const float* v, const float* v_ref,
+               double* out, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_geom(h, g));
+  if (!v || !v_ref || !out) return fail(h, CS_ERR_ARG, "v, v_ref or out is NULL");
+  CS_SCOPE(h);
+  Workspace w;
+  CS_TRY(ensure_ws(h, g->M, &w));
+  Geo G = make_geo(*g);
+  CS_CUDA(launch_rel_err(G, reinterpret_cast<const float2*>(v),
+                         reinterpret_cast<const float2*>(v_ref), w.part, out, h->num_sms,
+                         S(stream)),
+          "rel_err launch");
+  return CS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Device-side building blocks shared by the kernels of libcryosgd:
+// grid geometry, the interpolation stencils of Definition 2.1, the CTF and
+// the SplitMix64 probe generator.  sm_103a only.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cs {
+
+// Kernel-side copy of the geometry.  The CTF phase (in units of pi) is
+//   chi/pi = a_i q - b q^2,  a_i = ka * defocus_i,
+// ka = lam / (M pix)^2 and b = Cs lam^3 / (2 (M pix)^4), prepared on the
+// host in FP64; ka is carried as an unevaluated float pair (hi + lo) so that
+// the large term a_i q can be reduced modulo 2 without losing accuracy.
+struct Geo {
+  int M;
+  int half;       // M / 2
+  int r2max;      // r_max^2
+  int interp;     // 0 nearest, 1 trilinear
+  int ctf_on;
+  float ka_hi, ka_lo;
+  float kb;
+  float wsin;     // sqrt(1 - A^2)
+  float wcos;     // A
+};
+
+// Per-image CTF coefficient a_i = ka * df as a float pair (error-free
+// product of ka_hi and df via fmaf, plus the ka_lo term).
+__device__ __forceinline__ void ctf_coeff(const Geo& G, float df, float& a_hi,
+                                          float& a_lo) {
+  float p = G.ka_hi * df;
+  float e = fmaf(G.ka_hi, df, -p);
+  a_hi = p;
+  a_lo = fmaf(G.ka_lo, df, e);
+}
+
+// C_i at pixel radius^2 q.  The product a_hi*q is split exactly into its
+// rounded value p and error e (fmaf), p is reduced modulo 2 exactly
+// (p - 2 rint(p/2) is exact by Sterbenz' lemma), and the small remaining
+// terms are added to the reduced phase before sincospif.
+__device__ __forceinline__ float ctf_value(const Geo& G, float a_hi, float a_lo,
+                                           int q) {
+  if (!G.ctf_on) return 1.0f;
+  float fq = (float)q;
+  float p = a_hi * fq;
+  float e = fmaf(a_hi, fq, -p);
+  float r = p - 2.0f * rintf(0.5f * p);
+  r += fmaf(a_lo, fq, e);
+  r = fmaf(-G.kb, fq * fq, r);
+  float s, c;
+  sincospif(r, &s, &c);
+  return -(G.wsin * s + G.wcos * c);
+}
+
+// Rotation of one image, row-major R[0..8].
+struct Rot {
+  float r0x, r0y, r0z, r1x, r1y, r1z;   // rows 0 and 1 of R
+};
+
+__device__ __forceinline__ Rot load_rot(const float* __restrict__ rot, int b) {
+  const float* p = rot + 9 * (size_t)b;
+  Rot R;
+  R.r0x = __ldg(p + 0); R.r0y = __ldg(p + 1); R.r0z = __ldg(p + 2);
+  R.r1x = __ldg(p + 3); R.r1y = __ldg(p + 4); R.r1z = __ldg(p + 5);
+  return R;
+}
+
+// Interpolation stencil of one pixel: up to 8 voxel indices and weights.
+// Corners outside the grid get weight 0 and a clamped (valid) index, so a
+// gather or scatter through the stencil never leaves the volume.
+struct Stencil {
+  int n;          // 1 (nearest) or 8 (trilinear)
+  int idx[8];
+  float w[8];
+};
+
+// Nearest rule: coordinate a = R[0][a]*kx + R[1][a]*ky as two rounded
+// products and a rounded sum (no contraction), rounded half to even.
+__device__ __forceinline__ int nearest_axis(float r0, float r1, float kx, float ky,
+                                            int half) {
+  float c = __fadd_rn(__fmul_rn(r0, kx), __fmul_rn(r1, ky));
+  return (int)rintf(c) + half;
+}
+
+template <int INTERP>
+__device__ __forceinline__ void make_stencil(const Geo& G, const Rot& R, int kx,
+                                             int ky, Stencil& S) {
+  const float fx = (float)kx, fy = (float)ky;
+  const int M = G.M;
+  if (INTERP == 0) {
+    int ix = nearest_axis(R.r0x, R.r1x, fx, fy, G.half);
+    int iy = nearest_axis(R.r0y, R.r1y, fx, fy, G.half);
+    int iz = nearest_axis(R.r0z, R.r1z, fx, fy, G.half);
+    bool ok = (unsigned)ix < (unsigned)M && (unsigned)iy < (unsigned)M &&
+              (unsigned)iz < (unsigned)M;
+    S.n = 1;
+    S.idx[0] = ok ? (iz * M + iy) * M + ix : 0;
+    S.w[0] = ok ? 1.0f : 0.0f;
+    return;
+  }
+  // trilinear: cell of s = R^T r, weights (1-t, t) per axis
+  float sx = fmaf(R.r1x, fy, R.r0x * fx) + (float)G.half;
+  float sy = fmaf(R.r1y, fy, R.r0y * fx) + (float)G.half;
+  float sz = fmaf(R.r1z, fy, R.r0z * fx) + (float)G.half;
+  float flx = floorf(sx), fly = floorf(sy), flz = floorf(sz);
+  int x0 = (int)flx, y0 = (int)fly, z0 = (int)flz;
+  float tx = sx - flx, ty = sy - fly, tz = sz - flz;
+  S.n = 8;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+    int ix = x0 + dx, iy = y0 + dy, iz = z0 + dz;
+    bool ok = (unsigned)ix < (unsigned)M && (unsigned)iy < (unsigned)M &&
+              (unsigned)iz < (unsigned)M;
+    int cx = min(max(ix, 0), M - 1), cy = min(max(iy, 0), M - 1),
+        cz = min(max(iz, 0), M - 1);
+    float w = (dx ? tx : 1.0f - tx) * (dy ? ty : 1.0f - ty) * (dz ? tz : 1.0f - tz);
+    S.idx[c] = (cz * M + cy) * M + cx;
+    S.w[c] = ok ? w : 0.0f;
+  }
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): output number c of the stream
+// seeded with `seed` is mix(seed + (c + 1) * golden_gamma).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t c) {
+  uint64_t z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum in a fixed order (deterministic); every thread must call.
+// Result valid in thread 0.  Needs blockDim.x a multiple of 32, <= 1024.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    t = lane < nw ? red[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+}  // namespace cs

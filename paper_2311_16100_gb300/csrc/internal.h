@@ -1,0 +1,115 @@
+// Host-side internals of libcryosgd: the handle, its workspace, argument
+// preparation and the kernel launchers each translation unit provides.
+#pragma once
+
+#include <atomic>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/cryosgd.h"
+#include "device.cuh"
+
+struct cs_handle {
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  // workspace (grown on demand, released in cs_destroy)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // profiler: CS_NPHASES + 1 boundary events per timed step
+  bool prof = false;
+  int prof_max_steps = 0;
+  int prof_steps = 0;
+  std::vector<cudaEvent_t> prof_events;
+};
+
+namespace cs {
+
+// Kernel launches made by the library (reported by cs_kernel_launches).
+extern std::atomic<uint64_t> g_launches;
+inline void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// Workspace layout for a grid of side M: offsets are 256-byte aligned.
+struct Workspace {
+  float2* g;         // gradient, complex [M^3]
+  float2* d;         // step direction, complex [M^3]
+  float* dhat;       // thresholded preconditioner [M^3]
+  float* dest;       // Hutchinson estimate of the batch [M^3]
+  uint32_t* bits;    // probe words [M^3]
+  double* part;      // block partial sums [kPartSlots]
+};
+
+constexpr int kPartRegion = 8192;           // doubles per partial-sum region
+constexpr int kPartSlots = 4 * kPartRegion; // four regions
+constexpr int kBlock = 256;            // threads per block of the pixel kernels
+
+size_t workspace_bytes(int M);
+Workspace carve(void* base, int M);
+
+// Geometry for the kernels; FP64 CTF constants folded on the host.
+Geo make_geo(const cs_geom& g);
+
+// Number of blocks of the grid-stride pixel kernels.
+int pixel_grid(int num_sms, int B, int M);
+
+// ---- launchers (return the cudaError_t of the launch) ----
+cudaError_t launch_quat_to_rot(const float* quat, int B, float* rot, cudaStream_t s);
+cudaError_t launch_slice_project(const Geo& G, const float2* vol, const float* rot,
+                                 const float* df, int B, float2* out, int grid,
+                                 cudaStream_t s);
+cudaError_t launch_backproject(const Geo& G, const float2* img, const float* rot,
+                               const float* df, int B, float scale, float2* vol,
+                               int grid, cudaStream_t s);
+// loss_grad: grad = lambda v (init) then += scatter; data-term partials in
+// part_loss[0..grid), |v|^2 partials in part_vv[0..*n_vv); if loss != NULL the
+// final loss is written there.
+cudaError_t launch_loss_grad(const Geo& G, const float2* vol, const float2* img,
+                             const float* rot, const float* df, int B, float lambda,
+                             float scale, float2* grad, double* loss, double* part_loss,
+                             double* part_vv, int* n_vv, int grid, int num_sms,
+                             cudaStream_t s);
+cudaError_t launch_hvp(const Geo& G, const float* z, const float* rot, const float* df,
+                       int B, float lambda, float scale, float* Hz, int grid,
+                       int num_sms, cudaStream_t s);
+cudaError_t launch_probe_bits(int M, uint64_t seed, uint64_t block_host,
+                              const double* k_dev, uint32_t* bits, int num_sms,
+                              cudaStream_t s);
+cudaError_t launch_hutchinson(const Geo& G, const uint32_t* bits, const float* rot,
+                              const float* df, int B, float lambda, float scale,
+                              int n_probes, float* diag, int grid, int num_sms,
+                              cudaStream_t s);
+cudaError_t launch_exact_diag(const Geo& G, const float* rot, const float* df, int B,
+                              float lambda, float scale, float* diag, float* cov,
+                              float* c2w, int grid, int num_sms, cudaStream_t s);
+cudaError_t launch_alpha(const Geo& G, const float* df, int N, double px_over_pv,
+                         double lambda, double scale_alpha, double* alpha,
+                         cudaStream_t s);
+// SGD step pieces
+cudaError_t launch_precond_update(int n, const float* dest, float* D, float* Davg,
+                                  float* dhat, const double* scalars, float beta,
+                                  int num_sms, cudaStream_t s);
+cudaError_t launch_fixed_dhat(int n, const float* D, float* dhat, const double* scalars,
+                              int num_sms, cudaStream_t s);
+// d = g / dhat (dhat NULL: d = g); part[0..gb) <- sum |g|^2/dhat,
+// part[gb..2gb) <- sum |d|^2; returns gb through *nblk.
+cudaError_t launch_direction(int n, const float2* g, const float* dhat, float2* d,
+                             double* part, int* nblk, int num_sms, cudaStream_t s);
+// part[0..grid) <- sum_i sum_p |C P d|^2
+cudaError_t launch_curvature(const Geo& G, const float2* d, const float* rot,
+                             const float* df, int B, double* part, int grid,
+                             cudaStream_t s);
+cudaError_t launch_eta(double* scalars, const double* part_loss, int n_loss,
+                       const double* part_vv, int n_vv, const double* part_G,
+                       const double* part_dd, int n_dir, const double* part_Q,
+                       int n_Q, float lambda, float scale, float c, int max_halvings,
+                       cudaStream_t s);
+cudaError_t launch_update(int n, float2* v, const float2* d, const double* scalars,
+                          int num_sms, cudaStream_t s);
+cudaError_t launch_rel_err(const Geo& G, const float2* v, const float2* vref,
+                           double* part, double* out, int num_sms, cudaStream_t s);
+
+}  // namespace cs

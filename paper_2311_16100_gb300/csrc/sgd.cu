@@ -1,0 +1,249 @@
+// Element-wise and scalar kernels of Algorithm 1 (Section 3.4): pose
+// conversion, the preconditioner update (Eqs. hutch update, exp avg update,
+// thresh), the step direction, the closed-form stochastic Armijo step
+// (Eq. stochastic armijo), the threshold alpha (Eq. thresh value) and the
+// relative volume error.
+#include "internal.h"
+
+namespace cs {
+
+namespace {
+
+int elem_grid(int n, int num_sms) {
+  int g = (n + kBlock - 1) / kBlock;
+  return g < num_sms * 4 ? (g > 0 ? g : 1) : num_sms * 4;
+}
+
+__global__ void k_quat_to_rot(const float* __restrict__ q, int B, float* __restrict__ R) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  float w = q[4 * b], x = q[4 * b + 1], y = q[4 * b + 2], z = q[4 * b + 3];
+  float inv = rsqrtf(w * w + x * x + y * y + z * z);
+  w *= inv; x *= inv; y *= inv; z *= inv;
+  float* r = R + 9 * b;
+  r[0] = 1.f - 2.f * (y * y + z * z);
+  r[1] = 2.f * (x * y - w * z);
+  r[2] = 2.f * (x * z + w * y);
+  r[3] = 2.f * (x * y + w * z);
+  r[4] = 1.f - 2.f * (x * x + z * z);
+  r[5] = 2.f * (y * z - w * x);
+  r[6] = 2.f * (x * z - w * y);
+  r[7] = 2.f * (y * z + w * x);
+  r[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Running mean of the Hutchinson estimates, EMA and threshold, for step
+// k = (iterations done) + 1.
+__global__ void __launch_bounds__(kBlock)
+k_precond_update(int n, const float* __restrict__ dest, float* __restrict__ D,
+                 float* __restrict__ Davg, float* __restrict__ dhat,
+                 const double* __restrict__ sc, float beta) {
+  const double k = sc[CS_S_K] + 1.0;
+  const float wold = (float)((k - 1.0) / k), wnew = (float)(1.0 / k);
+  const float alpha = (float)sc[CS_S_ALPHA];
+  for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) {
+    float a = fmaf(wold, Davg[j], wnew * dest[j]);
+    float d = fmaf(beta, D[j], (1.0f - beta) * a);
+    Davg[j] = a;
+    D[j] = d;
+    dhat[j] = fmaxf(fabsf(d), alpha);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_fixed_dhat(int n, const float* __restrict__ D, float* __restrict__ dhat,
+             const double* __restrict__ sc) {
+  const float alpha = (float)sc[CS_S_ALPHA];
+  for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock)
+    dhat[j] = fmaxf(fabsf(D[j]), alpha);
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_direction(int n, const float2* __restrict__ g, const float* __restrict__ dhat,
+            float2* __restrict__ d, double* __restrict__ part) {
+  double aG = 0.0, aD = 0.0;
+  for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) {
+    float2 x = g[j];
+    float inv = dhat ? 1.0f / dhat[j] : 1.0f;
+    float2 y = make_float2(x.x * inv, x.y * inv);
+    d[j] = y;
+    aG += (double)(fmaf(x.x, x.x, x.y * x.y) * inv);
+    aD += (double)fmaf(y.x, y.x, y.y * y.y);
+  }
+  double tG = block_sum(aG);
+  double tD = block_sum(aD);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = tG;
+    part[gridDim.x + blockIdx.x] = tD;
+  }
+}
+
+__device__ double sum_fixed(const double* p, int n) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += p[i];
+  return block_sum(a);
+}
+
+// Closed-form stochastic Armijo: f_I(v - eta d) = f_I(v) - eta G + eta^2 Q/2
+// (f_I quadratic), so the halving loop of Algorithm 1 stops at the first
+// eta = eta_prev 2^-m with eta <= 2 (1 - c) G / Q.
+__global__ void __launch_bounds__(1024)
+k_eta(double* sc, const double* pl, int nl, const double* pv, int nv, const double* pG,
+      const double* pD, int nd, const double* pQ, int nq, float lambda, float scale,
+      float c, int max_halvings) {
+  double L = sum_fixed(pl, nl);
+  double V = sum_fixed(pv, nv);
+  double G = sum_fixed(pG, nd);
+  double DD = sum_fixed(pD, nd);
+  double Qd = sum_fixed(pQ, nq);
+  if (threadIdx.x != 0) return;
+  double Q = (double)scale * Qd + (double)lambda * DD;
+  double eta = sc[CS_S_ETA];
+  int h = 0;
+  double status = 1.0;
+  if (G > 0.0 && Q > 0.0) {
+    const double bound = 2.0 * (1.0 - (double)c) * G / Q;
+    while (eta > bound && h < max_halvings) {
+      eta *= 0.5;
+      ++h;
+    }
+    status = 0.0;
+  }
+  sc[CS_S_LOSS] = 0.5 * (double)scale * L + 0.5 * (double)lambda * V;
+  sc[CS_S_G] = G;
+  sc[CS_S_Q] = Q;
+  sc[CS_S_HALVINGS] = (double)h;
+  sc[CS_S_ETA] = eta;
+  sc[CS_S_STATUS] = status;
+  sc[CS_S_K] = sc[CS_S_K] + 1.0;
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_update(int n, float2* __restrict__ v, const float2* __restrict__ d,
+         const double* __restrict__ sc) {
+  const float eta = (float)sc[CS_S_ETA];
+  for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) {
+    float2 a = v[j], b = d[j];
+    v[j] = make_float2(fmaf(-eta, b.x, a.x), fmaf(-eta, b.y, a.y));
+  }
+}
+
+// sum_i C_i(R)^2 over the dataset, then alpha.
+__global__ void __launch_bounds__(1024)
+k_alpha(Geo G, const float* __restrict__ df, int N, int q, double px_over_pv,
+        double lambda, double scale_alpha, double* alpha) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    float C = 1.0f;
+    if (G.ctf_on) {
+      float a_hi, a_lo;
+      ctf_coeff(G, df[i], a_hi, a_lo);
+      C = ctf_value(G, a_hi, a_lo, q);
+    }
+    a += (double)C * (double)C;
+  }
+  a = block_sum(a);
+  if (threadIdx.x == 0) *alpha = px_over_pv * scale_alpha * a + lambda;
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_rel_err_part(Geo G, const float2* __restrict__ v, const float2* __restrict__ r,
+               double* __restrict__ part) {
+  const int n = G.M * G.M * G.M;
+  double e = 0.0, t = 0.0;
+  for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) {
+    int x = j % G.M, y = (j / G.M) % G.M, z = j / (G.M * G.M);
+    int kx = x - G.half, ky = y - G.half, kz = z - G.half;
+    if (kx * kx + ky * ky + kz * kz > G.r2max) continue;
+    float2 a = v[j], b = r[j];
+    float dx = a.x - b.x, dy = a.y - b.y;
+    e += (double)fmaf(dx, dx, dy * dy);
+    t += (double)fmaf(b.x, b.x, b.y * b.y);
+  }
+  double se = block_sum(e);
+  double st = block_sum(t);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = se;
+    part[gridDim.x + blockIdx.x] = st;
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+k_rel_err_final(const double* part, int nb, double* out) {
+  double e = sum_fixed(part, nb);
+  double t = sum_fixed(part + nb, nb);
+  if (threadIdx.x == 0) *out = t > 0.0 ? sqrt(e / t) : 0.0;
+}
+
+}  // namespace
+
+cudaError_t launch_quat_to_rot(const float* quat, int B, float* rot, cudaStream_t s) {
+  k_quat_to_rot<<<(B + 127) / 128, 128, 0, s>>>(quat, B, rot);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_precond_update(int n, const float* dest, float* D, float* Davg,
+                                  float* dhat, const double* scalars, float beta,
+                                  int num_sms, cudaStream_t s) {
+  k_precond_update<<<elem_grid(n, num_sms), kBlock, 0, s>>>(n, dest, D, Davg, dhat,
+                                                            scalars, beta);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fixed_dhat(int n, const float* D, float* dhat, const double* scalars,
+                              int num_sms, cudaStream_t s) {
+  k_fixed_dhat<<<elem_grid(n, num_sms), kBlock, 0, s>>>(n, D, dhat, scalars);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_direction(int n, const float2* g, const float* dhat, float2* d,
+                             double* part, int* nblk, int num_sms, cudaStream_t s) {
+  const int gb = elem_grid(n, num_sms);
+  *nblk = gb;
+  k_direction<<<gb, kBlock, 0, s>>>(n, g, dhat, d, part);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eta(double* scalars, const double* part_loss, int n_loss,
+                       const double* part_vv, int n_vv, const double* part_G,
+                       const double* part_dd, int n_dir, const double* part_Q, int n_Q,
+                       float lambda, float scale, float c, int max_halvings,
+                       cudaStream_t s) {
+  k_eta<<<1, 1024, 0, s>>>(scalars, part_loss, n_loss, part_vv, n_vv, part_G, part_dd,
+                           n_dir, part_Q, n_Q, lambda, scale, c, max_halvings);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(int n, float2* v, const float2* d, const double* scalars,
+                          int num_sms, cudaStream_t s) {
+  k_update<<<elem_grid(n, num_sms), kBlock, 0, s>>>(n, v, d, scalars);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_alpha(const Geo& G, const float* df, int N, double px_over_pv,
+                         double lambda, double scale_alpha, double* alpha,
+                         cudaStream_t s) {
+  const int R = (int)llround(sqrt((double)G.r2max));
+  k_alpha<<<1, 1024, 0, s>>>(G, df, N, R * R, px_over_pv, lambda, scale_alpha, alpha);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rel_err(const Geo& G, const float2* v, const float2* vref,
+                           double* part, double* out, int num_sms, cudaStream_t s) {
+  const int n = G.M * G.M * G.M;
+  const int gb = elem_grid(n, num_sms);
+  k_rel_err_part<<<gb, kBlock, 0, s>>>(G, v, vref, part);
+  count_launches(1);
+  k_rel_err_final<<<1, 1024, 0, s>>>(part, gb, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace cs

@@ -1,0 +1,286 @@
+"""Thin Python binding of libcryosgd: same names as the C ABI, argument
+marshalling only.  Tensors are CUDA tensors owned by the caller (complex64
+volumes / images, float32 rotations, defocus and real volumes, float64
+scalars); every computation runs in the library's kernels on the current
+torch CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import torch
+
+from . import native as N
+
+
+class CryoSGDError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__(f"{fn} -> {status_string(status)}: {msg}")
+        self.status = status
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libcryosgd in this process so far."""
+    return int(N.load().cs_kernel_launches())
+
+
+def status_string(code: int) -> str:
+    return N.load().cs_status_string(code).decode()
+
+
+@dataclass
+class CTF:
+    """Microscope parameters of the CTF (kV, Cs in mm, amplitude contrast,
+    pixel size in Angstrom)."""
+    kv: float = 300.0
+    cs_mm: float = 2.7
+    amp: float = 0.1
+    pixel_A: float = 1.5
+
+
+@dataclass
+class Geometry:
+    """Grid side M, disc radius r_max (default M/2-1), interpolation
+    ("nearest" | "trilinear") and an optional CTF."""
+    M: int
+    r_max: int | None = None
+    interp: str = "trilinear"
+    ctf: CTF | None = None
+    _c: N.CsGeom = field(init=False, repr=False)
+
+    def __post_init__(self):
+        if self.r_max is None:
+            self.r_max = self.M // 2 - 1
+        c = N.CsGeom()
+        c.M = self.M
+        c.r_max = self.r_max
+        c.interp = {"nearest": N.CS_NEAREST, "trilinear": N.CS_TRILINEAR}.get(self.interp, -1)
+        if self.ctf is not None:
+            c.ctf = N.CsCtf(self.ctf.kv, self.ctf.cs_mm, self.ctf.amp, self.ctf.pixel_A, 1)
+        else:
+            c.ctf = N.CsCtf(0, 0, 0, 0, 0)
+        self._c = c
+
+    @property
+    def c(self):
+        return ctypes.byref(self._c)
+
+
+def _ptr(t: torch.Tensor | None, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Handle:
+    """Owns a cs_handle (device binding + workspace)."""
+
+    def __init__(self, device: int | None = None):
+        self.lib = N.load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = self.lib.cs_create(ctypes.byref(h), device)
+        if rc != N.CS_OK:
+            raise CryoSGDError("cs_create", rc, "no usable CUDA device")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, fn: str, rc: int):
+        if rc != N.CS_OK:
+            raise CryoSGDError(fn, rc, self.lib.cs_last_error(self.h).decode())
+
+    # ------------------------------------------------------------ calls
+    def reserve(self, M: int, max_batch: int = 0):
+        self._check("cs_reserve", self.lib.cs_reserve(self.h, M, max_batch))
+
+    def workspace_bytes(self) -> int:
+        return int(self.lib.cs_workspace_bytes(self.h))
+
+    def quat_to_rot(self, quat, rot=None, stream=None):
+        B = quat.shape[0]
+        if rot is None:
+            rot = torch.empty((B, 3, 3), dtype=torch.float32, device=quat.device)
+        self._check("cs_quat_to_rot", self.lib.cs_quat_to_rot(
+            self.h, _ptr(quat, torch.float32, "quat"), B, _ptr(rot, torch.float32, "rot"),
+            _stream(stream)))
+        return rot
+
+    def slice_project(self, geom: Geometry, vol, rot, defocus=None, out=None, stream=None):
+        B = rot.shape[0]
+        M = geom.M
+        if out is None:
+            out = torch.empty((B, M, M), dtype=torch.complex64, device=vol.device)
+        self._check("cs_slice_project", self.lib.cs_slice_project(
+            self.h, geom.c, _ptr(vol, torch.complex64, "vol"), _ptr(rot, torch.float32, "rot"),
+            _ptr(defocus, torch.float32, "defocus"), B, _ptr(out, torch.complex64, "out"),
+            _stream(stream)))
+        return out
+
+    def backproject_adjoint(self, geom: Geometry, images, rot, defocus=None, scale=1.0,
+                            vol_accum=None, stream=None):
+        B = rot.shape[0]
+        M = geom.M
+        if vol_accum is None:
+            vol_accum = torch.zeros((M, M, M), dtype=torch.complex64, device=images.device)
+        self._check("cs_backproject_adjoint", self.lib.cs_backproject_adjoint(
+            self.h, geom.c, _ptr(images, torch.complex64, "images"),
+            _ptr(rot, torch.float32, "rot"), _ptr(defocus, torch.float32, "defocus"), B,
+            float(scale), _ptr(vol_accum, torch.complex64, "vol_accum"), _stream(stream)))
+        return vol_accum
+
+    def loss_grad(self, geom: Geometry, vol, images, rot, defocus=None, lam=0.0, scale=1.0,
+                  grad=None, loss=None, stream=None):
+        B = rot.shape[0]
+        if grad is None:
+            grad = torch.empty_like(vol)
+        if loss is None:
+            loss = torch.empty((), dtype=torch.float64, device=vol.device)
+        self._check("cs_loss_grad", self.lib.cs_loss_grad(
+            self.h, geom.c, _ptr(vol, torch.complex64, "vol"),
+            _ptr(images, torch.complex64, "images"), _ptr(rot, torch.float32, "rot"),
+            _ptr(defocus, torch.float32, "defocus"), B, float(lam), float(scale),
+            _ptr(grad, torch.complex64, "grad"), _ptr(loss, torch.float64, "loss"),
+            _stream(stream)))
+        return loss, grad
+
+    def hvp(self, geom: Geometry, z, rot, defocus=None, lam=0.0, scale=1.0, out=None,
+            stream=None):
+        B = rot.shape[0]
+        if out is None:
+            out = torch.empty_like(z)
+        self._check("cs_hvp", self.lib.cs_hvp(
+            self.h, geom.c, _ptr(z, torch.float32, "z"), _ptr(rot, torch.float32, "rot"),
+            _ptr(defocus, torch.float32, "defocus"), B, float(lam), float(scale),
+            _ptr(out, torch.float32, "Hz"), _stream(stream)))
+        return out
+
+    def hutchinson_diag(self, geom: Geometry, rot, defocus=None, lam=0.0, scale=1.0,
+                        n_probes=32, seed=0, probe_block=0, out=None, stream=None):
+        B = rot.shape[0]
+        M = geom.M
+        if out is None:
+            out = torch.empty((M, M, M), dtype=torch.float32, device=rot.device)
+        self._check("cs_hutchinson_diag", self.lib.cs_hutchinson_diag(
+            self.h, geom.c, _ptr(rot, torch.float32, "rot"),
+            _ptr(defocus, torch.float32, "defocus"), B, float(lam), float(scale),
+            int(n_probes), int(seed), int(probe_block), _ptr(out, torch.float32, "diag"),
+            _stream(stream)))
+        return out
+
+    def exact_diag(self, geom: Geometry, rot, defocus=None, lam=0.0, scale=1.0,
+                   diag=True, coverage=False, ctf2w=False, stream=None):
+        B = rot.shape[0]
+        M = geom.M
+        mk = lambda want: (torch.empty((M, M, M), dtype=torch.float32, device=rot.device)
+                           if want is True else (want if want is not False else None))
+        d, cv, cw = mk(diag), mk(coverage), mk(ctf2w)
+        self._check("cs_exact_diag", self.lib.cs_exact_diag(
+            self.h, geom.c, _ptr(rot, torch.float32, "rot"),
+            _ptr(defocus, torch.float32, "defocus"), B, float(lam), float(scale),
+            _ptr(d, torch.float32, "diag"), _ptr(cv, torch.float32, "coverage"),
+            _ptr(cw, torch.float32, "ctf2w"), _stream(stream)))
+        return d, cv, cw
+
+    def threshold_alpha(self, geom: Geometry, defocus_all, N_images, lam, scale_alpha=1.0,
+                        out=None, stream=None):
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=torch.device("cuda", self.device))
+        self._check("cs_threshold_alpha", self.lib.cs_threshold_alpha(
+            self.h, geom.c, _ptr(defocus_all, torch.float32, "defocus_all"), int(N_images),
+            float(lam), float(scale_alpha), _ptr(out, torch.float64, "alpha"),
+            _stream(stream)))
+        return out
+
+    def precond_sgd_step(self, geom: Geometry, state: "SGDState", images, rot, defocus=None,
+                         lam=0.0, scale=1.0, stream=None):
+        B = rot.shape[0]
+        self._check("cs_precond_sgd_step", self.lib.cs_precond_sgd_step(
+            self.h, geom.c, ctypes.byref(state.cstruct()), _ptr(images, torch.complex64, "images"),
+            _ptr(rot, torch.float32, "rot"), _ptr(defocus, torch.float32, "defocus"), B,
+            float(lam), float(scale), _stream(stream)))
+
+    def profile_enable(self, enable=True, max_steps=4096):
+        self._check("cs_profile_enable", self.lib.cs_profile_enable(self.h, int(enable),
+                                                                    int(max_steps)))
+
+    def profile_read(self):
+        """{phase: (total ms, timed steps)} of cs_precond_sgd_step."""
+        ms = (ctypes.c_double * N.CS_NPHASES)()
+        cnt = (ctypes.c_int * N.CS_NPHASES)()
+        self._check("cs_profile_read", self.lib.cs_profile_read(self.h, ms, cnt))
+        return {n: (ms[i], cnt[i]) for i, n in enumerate(N.PHASE_NAMES)}
+
+    def rel_err(self, geom: Geometry, v, v_ref, out=None, stream=None):
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=v.device)
+        self._check("cs_rel_err", self.lib.cs_rel_err(
+            self.h, geom.c, _ptr(v, torch.complex64, "v"), _ptr(v_ref, torch.complex64, "v_ref"),
+            _ptr(out, torch.float64, "out"), _stream(stream)))
+        return out
+
+
+MODES = {"plain": N.CS_PLAIN, "hutchinson": N.CS_HUTCHINSON, "fixed": N.CS_FIXED}
+
+
+class SGDState:
+    """Algorithm 1 state on the device: v, D (init I), D_avg (init 0) and the
+    scalar block (eta, k, alpha, loss, G, Q, halvings, status)."""
+
+    def __init__(self, v0: torch.Tensor, mode="hutchinson", alpha=0.0, eta0=1.0, beta=0.9,
+                 armijo_c=0.5, n_probes=1, seed=0, max_halvings=64, D=None):
+        M = v0.shape[0]
+        dev = v0.device
+        self.v = v0.clone().contiguous()
+        self.mode = mode
+        self.D = (D.clone().contiguous() if D is not None
+                  else torch.ones((M, M, M), dtype=torch.float32, device=dev))
+        self.D_avg = torch.zeros((M, M, M), dtype=torch.float32, device=dev)
+        self.scalars = torch.zeros(N.CS_NSCALARS, dtype=torch.float64, device=dev)
+        self.scalars[N.CS_S_ETA] = eta0
+        if torch.is_tensor(alpha):
+            self.scalars[N.CS_S_ALPHA] = alpha.to(dev, torch.float64)
+        else:
+            self.scalars[N.CS_S_ALPHA] = float(alpha)
+        self.n_probes, self.seed, self.beta = n_probes, seed, beta
+        self.armijo_c = armijo_c
+        self.max_halvings = max_halvings
+        self._cs = None
+
+    def cstruct(self) -> N.CsSgdState:
+        s = N.CsSgdState()
+        s.v = self.v.data_ptr()
+        s.D = self.D.data_ptr()
+        s.D_avg = self.D_avg.data_ptr()
+        s.scalars = self.scalars.data_ptr()
+        s.mode = MODES[self.mode]
+        s.n_probes = self.n_probes
+        s.seed = self.seed
+        s.beta = self.beta
+        s.c = self.armijo_c
+        s.max_halvings = self.max_halvings
+        self._cs = s
+        return s
