@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=48,
                    help="images in the oracle's timed sample")
+    p.add_argument("--algo", choices=["tiled", "pixel"], default="tiled",
+                   help="scatter algorithm of the adjoint-type passes")
     p.add_argument("--images", type=int, default=0,
                    help="override the number of images held in HBM (profiling runs)")
     return p.parse_args()
@@ -209,6 +211,7 @@ def run_gpu(args, cfg, rank, world):
     from paper_2311_16100_gb300 import native as N
 
     h = ops.Handle(torch.cuda.current_device())
+    h.set_algo(args.algo)
     W = build_workload(cfg, rank, h, torch, ops, synth)
     M, B, nb = cfg["M"], cfg["B"], W["nb"]
     geom, images, quat, df, rot = W["geom"], W["images"], W["quat"], W["df"], W["rot"]
@@ -412,7 +415,7 @@ def config_json(args, cfg):
             "M": cfg["M"], "global_batch": cfg["B"] * args.gpus, "batch_per_gpu": cfg["B"],
             "interp": cfg["interp"], "n_probes": cfg["K"],
             "images_in_hbm_per_gpu": cfg["n_img"] // cfg["B"] * cfg["B"],
-            "parallelism": f"replicas{args.gpus}",
+            "parallelism": f"replicas{args.gpus}", "scatter": args.algo,
             "l2": "inputs larger than L2: consecutive steps read distinct 134 MB batches "
                   "from a 6.4 GB image set; the volume stays L2-resident by design"}
 

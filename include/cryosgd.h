@@ -108,6 +108,17 @@ int cs_reserve(cs_handle* h, int M, int max_batch);
 /* Bytes of device workspace currently held by h. */
 size_t cs_workspace_bytes(const cs_handle* h);
 
+/* Scatter algorithm of the adjoint-type passes (backproject_adjoint,
+ * loss_grad, hvp, hutchinson_diag and the SGD step):
+ *   CS_ALGO_TILED -- volume tiles binned by image, adjoint accumulated in
+ *                    shared memory and added to global memory once per tile
+ *                    and work item (default; CS_ALGO_AUTO selects it);
+ *   CS_ALGO_PIXEL -- one thread per pixel, FP32 reductions straight into
+ *                    global memory.
+ * Both compute the same sums (in different orders). */
+enum { CS_ALGO_AUTO = 0, CS_ALGO_PIXEL = 1, CS_ALGO_TILED = 2 };
+int cs_set_algo(cs_handle* h, int algo);
+
 /* Pose -> rotation.  quat float[B][4] unit quaternions (w, x, y, z),
  * Hamilton convention (R v = q (0, v) q*; normalised first); rot float[B][9]
  * row-major R.  The paper's pose carries R directly (Definition 2.1); this

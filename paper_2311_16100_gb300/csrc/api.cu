@@ -7,6 +7,7 @@
 #include <new>
 
 #include "internal.h"
+#include "tiles.h"
 
 namespace cs {
 
@@ -18,22 +19,35 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-size_t workspace_bytes(int M) {
+size_t workspace_bytes(int M, int B) {
   const size_t n = (size_t)M * M * M;
+  const size_t nt = (size_t)tile_count_for(M);
+  const size_t items = max_items_for(M, B > 0 ? B : 1);
   return align256(n * sizeof(float2)) * 2 + align256(n * sizeof(float)) * 2 +
-         align256(n * sizeof(uint32_t)) + align256(kPartSlots * sizeof(double));
+         align256(n * sizeof(uint32_t)) + align256(kPartSlots * sizeof(double)) +
+         align256(nt * sizeof(int)) + align256(nt * (size_t)(B > 0 ? B : 1) * sizeof(int)) +
+         align256((nt + 1) * sizeof(int)) + align256(sizeof(int)) +
+         2 * align256(items * sizeof(double));
 }
 
-Workspace carve(void* base, int M) {
+Workspace carve(void* base, int M, int B) {
   const size_t n = (size_t)M * M * M;
+  const size_t nt = (size_t)tile_count_for(M);
+  const size_t items = max_items_for(M, B > 0 ? B : 1);
   char* p = static_cast<char*>(base);
   Workspace w;
-  w.g = reinterpret_cast<float2*>(p);     p += align256(n * sizeof(float2));
-  w.d = reinterpret_cast<float2*>(p);     p += align256(n * sizeof(float2));
-  w.dhat = reinterpret_cast<float*>(p);   p += align256(n * sizeof(float));
-  w.dest = reinterpret_cast<float*>(p);   p += align256(n * sizeof(float));
+  w.g = reinterpret_cast<float2*>(p);      p += align256(n * sizeof(float2));
+  w.d = reinterpret_cast<float2*>(p);      p += align256(n * sizeof(float2));
+  w.dhat = reinterpret_cast<float*>(p);    p += align256(n * sizeof(float));
+  w.dest = reinterpret_cast<float*>(p);    p += align256(n * sizeof(float));
   w.bits = reinterpret_cast<uint32_t*>(p); p += align256(n * sizeof(uint32_t));
-  w.part = reinterpret_cast<double*>(p);
+  w.part = reinterpret_cast<double*>(p);   p += align256(kPartSlots * sizeof(double));
+  w.tile_count = reinterpret_cast<int*>(p); p += align256(nt * sizeof(int));
+  w.tile_list = reinterpret_cast<int*>(p);  p += align256(nt * (size_t)(B > 0 ? B : 1) * sizeof(int));
+  w.item_start = reinterpret_cast<int*>(p); p += align256((nt + 1) * sizeof(int));
+  w.queue = reinterpret_cast<int*>(p);      p += align256(sizeof(int));
+  w.part_items = reinterpret_cast<double*>(p); p += align256(items * sizeof(double));
+  w.part_items2 = reinterpret_cast<double*>(p);
   return w;
 }
 
@@ -135,8 +149,8 @@ int check_batch(cs_handle* h, const cs_geom* g, int B, const float* rot,
   return CS_OK;
 }
 
-int ensure_ws(cs_handle* h, int M, Workspace* w) {
-  const size_t need = workspace_bytes(M);
+int ensure_ws(cs_handle* h, int M, int B, Workspace* w) {
+  const size_t need = workspace_bytes(M, B);
   if (h->ws_bytes < need) {
     if (const char* f = getenv("CS_FAULT_INJECT_ALLOC"))
       if (f[0] == '1') return fail(h, CS_ERR_ALLOC, "workspace allocation failed (injected)");
@@ -156,8 +170,19 @@ int ensure_ws(cs_handle* h, int M, Workspace* w) {
     h->ws = p;
     h->ws_bytes = need;
   }
-  *w = carve(h->ws, M);
+  *w = carve(h->ws, M, B);
   return CS_OK;
+}
+
+bool use_tiles(const cs_handle* h) { return h->algo != CS_ALGO_PIXEL; }
+
+// Bins the batch for the tile engine and fills the common fields of A.
+cudaError_t bin_batch(cs_handle* h, const Geo& G, const Workspace& w, const float* rot,
+                      const float* df, int B, float scale, TileArgs& A, cudaStream_t s) {
+  A = TileArgs{};
+  A.df = df;
+  A.scale = scale;
+  return launch_bin(G, rot, B, A, w.tile_count, w.tile_list, w.item_start, w.queue, s);
 }
 
 inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
@@ -259,12 +284,20 @@ int cs_reserve(cs_handle* h, int M, int max_batch) {
   if (max_batch < 0) return fail(h, CS_ERR_SHAPE, "max_batch=%d is negative", max_batch);
   CS_SCOPE(h);
   Workspace w;
-  CS_TRY(ensure_ws(h, M, &w));
+  CS_TRY(ensure_ws(h, M, max_batch, &w));
   CS_CUDA(cudaDeviceSynchronize(), "cs_reserve");
   return CS_OK;
 }
 
 size_t cs_workspace_bytes(const cs_handle* h) { return h ? h->ws_bytes : 0; }
+
+int cs_set_algo(cs_handle* h, int algo) {
+  if (!h) return CS_ERR_ARG;
+  if (algo != CS_ALGO_AUTO && algo != CS_ALGO_PIXEL && algo != CS_ALGO_TILED)
+    return fail(h, CS_ERR_ARG, "algo=%d is not a CS_ALGO_* value", algo);
+  h->algo = algo;
+  return CS_OK;
+}
 
 int cs_quat_to_rot(cs_handle* h, const float* quat, int B, float* rot, void* stream) {
   if (!h) return CS_ERR_ARG;
@@ -303,10 +336,21 @@ int cs_backproject_adjoint(cs_handle* h, const cs_geom* g, const float* images,
   if (!images || !vol_accum) return fail(h, CS_ERR_ARG, "images or vol_accum is NULL");
   CS_SCOPE(h);
   Geo G = make_geo(*g);
-  CS_CUDA(launch_backproject(G, reinterpret_cast<const float2*>(images), rot, defocus, B,
-                             scale, reinterpret_cast<float2*>(vol_accum),
-                             pixel_grid(h->num_sms, B, g->M), S(stream)),
-          "backproject launch");
+  cudaStream_t s = S(stream);
+  if (!use_tiles(h)) {
+    CS_CUDA(launch_backproject(G, reinterpret_cast<const float2*>(images), rot, defocus, B,
+                               scale, reinterpret_cast<float2*>(vol_accum),
+                               pixel_grid(h->num_sms, B, g->M), s),
+            "backproject launch");
+    return CS_OK;
+  }
+  Workspace w;
+  CS_TRY(ensure_ws(h, g->M, B, &w));
+  TileArgs A;
+  CS_CUDA(bin_batch(h, G, w, rot, defocus, B, scale, A, s), "binning launch");
+  A.img = reinterpret_cast<const float2*>(images);
+  A.dst = vol_accum;
+  CS_CUDA(launch_tile_op(OP_ADJOINT, A, h->num_sms, s), "adjoint tile launch");
   return CS_OK;
 }
 
@@ -321,15 +365,35 @@ int cs_loss_grad(cs_handle* h, const cs_geom* g, const float* vol, const float* 
     return fail(h, CS_ERR_ARG, "vol, grad or images is NULL");
   CS_SCOPE(h);
   Workspace w;
-  CS_TRY(ensure_ws(h, g->M, &w));
+  CS_TRY(ensure_ws(h, g->M, B, &w));
   Geo G = make_geo(*g);
+  cudaStream_t s = S(stream);
   int nvv = 0;
-  CS_CUDA(launch_loss_grad(G, reinterpret_cast<const float2*>(vol),
-                           reinterpret_cast<const float2*>(images), rot, defocus, B,
-                           lambda, scale, reinterpret_cast<float2*>(grad), loss, w.part,
-                           w.part + kPartRegion, &nvv, pixel_grid(h->num_sms, B, g->M),
-                           h->num_sms, S(stream)),
-          "loss_grad launch");
+  if (!use_tiles(h) || B == 0) {
+    CS_CUDA(launch_loss_grad(G, reinterpret_cast<const float2*>(vol),
+                             reinterpret_cast<const float2*>(images), rot, defocus, B,
+                             lambda, scale, reinterpret_cast<float2*>(grad), loss, w.part,
+                             w.part + kPartRegion, &nvv, pixel_grid(h->num_sms, B, g->M),
+                             h->num_sms, s),
+            "loss_grad launch");
+    return CS_OK;
+  }
+  const int n = g->M * g->M * g->M;
+  CS_CUDA(launch_init_grad(n, reinterpret_cast<const float2*>(vol), lambda,
+                           reinterpret_cast<float2*>(grad), w.part + kPartRegion, &nvv,
+                           h->num_sms, s),
+          "init_grad launch");
+  TileArgs A;
+  CS_CUDA(bin_batch(h, G, w, rot, defocus, B, scale, A, s), "binning launch");
+  A.src = vol;
+  A.img = reinterpret_cast<const float2*>(images);
+  A.dst = grad;
+  A.part = w.part_items;
+  CS_CUDA(launch_tile_op(OP_LOSS_GRAD, A, h->num_sms, s), "loss_grad tile launch");
+  if (loss)
+    CS_CUDA(launch_finalize_loss(w.part_items, 0, w.item_start + A.n_tiles,
+                                 w.part + kPartRegion, nvv, lambda, scale, loss, s),
+            "finalize_loss launch");
   return CS_OK;
 }
 
@@ -344,9 +408,22 @@ int cs_hvp(cs_handle* h, const cs_geom* g, const float* z, const float* rot,
   if (z == Hz) return fail(h, CS_ERR_ARG, "z and Hz must not alias");
   CS_SCOPE(h);
   Geo G = make_geo(*g);
-  CS_CUDA(launch_hvp(G, z, rot, defocus, B, lambda, scale, Hz,
-                     pixel_grid(h->num_sms, B, g->M), h->num_sms, S(stream)),
-          "hvp launch");
+  cudaStream_t s = S(stream);
+  if (!use_tiles(h) || B == 0) {
+    CS_CUDA(launch_hvp(G, z, rot, defocus, B, lambda, scale, Hz,
+                       pixel_grid(h->num_sms, B, g->M), h->num_sms, s),
+            "hvp launch");
+    return CS_OK;
+  }
+  Workspace w;
+  CS_TRY(ensure_ws(h, g->M, B, &w));
+  CS_CUDA(launch_scale_copy(g->M * g->M * g->M, z, lambda, Hz, h->num_sms, s),
+          "scale_copy launch");
+  TileArgs A;
+  CS_CUDA(bin_batch(h, G, w, rot, defocus, B, scale, A, s), "binning launch");
+  A.src = z;
+  A.dst = Hz;
+  CS_CUDA(launch_tile_op(OP_HVP, A, h->num_sms, s), "hvp tile launch");
   return CS_OK;
 }
 
@@ -363,14 +440,25 @@ int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
   if (!diag_out) return fail(h, CS_ERR_ARG, "diag_out is NULL");
   CS_SCOPE(h);
   Workspace w;
-  CS_TRY(ensure_ws(h, g->M, &w));
+  CS_TRY(ensure_ws(h, g->M, B, &w));
   Geo G = make_geo(*g);
+  cudaStream_t s = S(stream);
   if (g->interp == CS_TRILINEAR)
-    CS_CUDA(launch_probe_bits(g->M, seed, probe_block, nullptr, w.bits, h->num_sms, S(stream)),
+    CS_CUDA(launch_probe_bits(g->M, seed, probe_block, nullptr, w.bits, h->num_sms, s),
             "probe_bits launch");
-  CS_CUDA(launch_hutchinson(G, w.bits, rot, defocus, B, lambda, scale, n_probes, diag_out,
-                            pixel_grid(h->num_sms, B, g->M), h->num_sms, S(stream)),
-          "hutchinson launch");
+  if (!use_tiles(h) || B == 0) {
+    CS_CUDA(launch_hutchinson(G, w.bits, rot, defocus, B, lambda, scale, n_probes, diag_out,
+                              pixel_grid(h->num_sms, B, g->M), h->num_sms, s),
+            "hutchinson launch");
+    return CS_OK;
+  }
+  CS_CUDA(launch_fill(g->M * g->M * g->M, lambda, diag_out, h->num_sms, s), "fill launch");
+  TileArgs A;
+  CS_CUDA(bin_batch(h, G, w, rot, defocus, B, scale, A, s), "binning launch");
+  A.src = w.bits;
+  A.dst = diag_out;
+  A.K = n_probes;
+  CS_CUDA(launch_tile_op(OP_HUTCH, A, h->num_sms, s), "hutchinson tile launch");
   return CS_OK;
 }
 
@@ -449,7 +537,7 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
   if (st->max_halvings < 0) return fail(h, CS_ERR_ARG, "max_halvings is negative");
   CS_SCOPE(h);
   Workspace w;
-  CS_TRY(ensure_ws(h, g->M, &w));
+  CS_TRY(ensure_ws(h, g->M, B, &w));
   const Geo G = make_geo(*g);
   const int n = g->M * g->M * g->M;
   const int grid = pixel_grid(h->num_sms, B, g->M);
@@ -459,14 +547,26 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
   double* pD = w.part + 2 * kPartRegion; // direction partials (G, |d|^2)
   double* pQ = w.part + 3 * kPartRegion; // curvature partials
   const float* dhat = nullptr;
+  const bool tiles = use_tiles(h) && B > 0;
+  TileArgs A;
   prof_mark(h, 0, s);
+  if (tiles) CS_CUDA(bin_batch(h, G, w, rot, defocus, B, scale, A, s), "binning launch");
   if (st->mode == CS_HUTCHINSON) {
     if (g->interp == CS_TRILINEAR)
       CS_CUDA(launch_probe_bits(g->M, st->seed, 0, st->scalars + CS_S_K, w.bits, h->num_sms, s),
               "probe_bits launch");
-    CS_CUDA(launch_hutchinson(G, w.bits, rot, defocus, B, lambda, scale, st->n_probes,
-                              w.dest, grid, h->num_sms, s),
-            "hutchinson launch");
+    if (tiles) {
+      CS_CUDA(launch_fill(n, lambda, w.dest, h->num_sms, s), "fill launch");
+      TileArgs T = A;
+      T.src = w.bits;
+      T.dst = w.dest;
+      T.K = st->n_probes;
+      CS_CUDA(launch_tile_op(OP_HUTCH, T, h->num_sms, s), "hutchinson tile launch");
+    } else {
+      CS_CUDA(launch_hutchinson(G, w.bits, rot, defocus, B, lambda, scale, st->n_probes,
+                                w.dest, grid, h->num_sms, s),
+              "hutchinson launch");
+    }
     CS_CUDA(launch_precond_update(n, w.dest, st->D, st->D_avg, w.dhat, st->scalars,
                                   st->beta, h->num_sms, s),
             "precond_update launch");
@@ -478,19 +578,42 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
   }
   int nvv = 0, nd = 0;
   prof_mark(h, CS_PH_LOSS_GRAD, s);
-  CS_CUDA(launch_loss_grad(G, reinterpret_cast<const float2*>(st->v),
-                           reinterpret_cast<const float2*>(images), rot, defocus, B, lambda,
-                           scale, w.g, nullptr, pL, pV, &nvv, grid, h->num_sms, s),
-          "loss_grad launch");
+  if (tiles) {
+    CS_CUDA(launch_init_grad(n, reinterpret_cast<const float2*>(st->v), lambda, w.g, pV, &nvv,
+                             h->num_sms, s),
+            "init_grad launch");
+    TileArgs T = A;
+    T.src = st->v;
+    T.img = reinterpret_cast<const float2*>(images);
+    T.dst = w.g;
+    T.part = w.part_items;
+    CS_CUDA(launch_tile_op(OP_LOSS_GRAD, T, h->num_sms, s), "loss_grad tile launch");
+  } else {
+    CS_CUDA(launch_loss_grad(G, reinterpret_cast<const float2*>(st->v),
+                             reinterpret_cast<const float2*>(images), rot, defocus, B, lambda,
+                             scale, w.g, nullptr, pL, pV, &nvv, grid, h->num_sms, s),
+            "loss_grad launch");
+  }
   prof_mark(h, CS_PH_DIRECTION, s);
   CS_CUDA(launch_direction(n, w.g, dhat, w.d, pD, &nd, h->num_sms, s), "direction launch");
   prof_mark(h, CS_PH_CURVATURE, s);
-  if (B > 0)
+  if (tiles) {
+    TileArgs T = A;
+    T.src = w.d;
+    T.part = w.part_items2;
+    CS_CUDA(launch_tile_op(OP_CURVATURE, T, h->num_sms, s), "curvature tile launch");
+  } else if (B > 0) {
     CS_CUDA(launch_curvature(G, w.d, rot, defocus, B, pQ, grid, s), "curvature launch");
+  }
   prof_mark(h, CS_PH_UPDATE, s);
-  CS_CUDA(launch_eta(st->scalars, pL, B > 0 ? grid : 0, pV, nvv, pD, pD + nd, nd, pQ,
-                     B > 0 ? grid : 0, lambda, scale, st->c, st->max_halvings, s),
-          "eta launch");
+  if (tiles)
+    CS_CUDA(launch_eta(st->scalars, w.part_items, 0, pV, nvv, pD, pD + nd, nd, w.part_items2, 0,
+                       w.item_start + A.n_tiles, lambda, scale, st->c, st->max_halvings, s),
+            "eta launch");
+  else
+    CS_CUDA(launch_eta(st->scalars, pL, B > 0 ? grid : 0, pV, nvv, pD, pD + nd, nd, pQ,
+                       B > 0 ? grid : 0, nullptr, lambda, scale, st->c, st->max_halvings, s),
+            "eta launch");
   CS_CUDA(launch_update(n, reinterpret_cast<float2*>(st->v), w.d, st->scalars, h->num_sms, s),
           "update launch");
   prof_mark(h, CS_NPHASES, s);
@@ -554,7 +677,7 @@ int cs_rel_err(cs_handle* h, const cs_geom* g, const float* v, const float* v_re
   if (!v || !v_ref || !out) return fail(h, CS_ERR_ARG, "v, v_ref or out is NULL");
   CS_SCOPE(h);
   Workspace w;
-  CS_TRY(ensure_ws(h, g->M, &w));
+  CS_TRY(ensure_ws(h, g->M, 1, &w));
   Geo G = make_geo(*g);
   CS_CUDA(launch_rel_err(G, reinterpret_cast<const float2*>(v),
                          reinterpret_cast<const float2*>(v_ref), w.part, out, h->num_sms,

@@ -20,6 +20,7 @@ struct cs_handle {
   // workspace (grown on demand, released in cs_destroy)
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  int algo = 0;            // CS_ALGO_*
   // profiler: CS_NPHASES + 1 boundary events per timed step
   bool prof = false;
   int prof_max_steps = 0;
@@ -33,7 +34,8 @@ namespace cs {
 extern std::atomic<uint64_t> g_launches;
 inline void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
-// Workspace layout for a grid of side M: offsets are 256-byte aligned.
+// Workspace layout for a grid of side M and batches of up to B images:
+// offsets are 256-byte aligned.
 struct Workspace {
   float2* g;         // gradient, complex [M^3]
   float2* d;         // step direction, complex [M^3]
@@ -41,14 +43,21 @@ struct Workspace {
   float* dest;       // Hutchinson estimate of the batch [M^3]
   uint32_t* bits;    // probe words [M^3]
   double* part;      // block partial sums [kPartSlots]
+  // tile engine
+  int* tile_count;   // [n_tiles]
+  int* tile_list;    // [n_tiles][B]
+  int* item_start;   // [n_tiles + 1]
+  int* queue;        // [1]
+  double* part_items;   // [max items]: loss partials
+  double* part_items2;  // [max items]: curvature partials
 };
 
 constexpr int kPartRegion = 8192;           // doubles per partial-sum region
 constexpr int kPartSlots = 4 * kPartRegion; // four regions
 constexpr int kBlock = 256;            // threads per block of the pixel kernels
 
-size_t workspace_bytes(int M);
-Workspace carve(void* base, int M);
+size_t workspace_bytes(int M, int B);
+Workspace carve(void* base, int M, int B);
 
 // Geometry for the kernels; FP64 CTF constants folded on the host.
 Geo make_geo(const cs_geom& g);
@@ -72,6 +81,16 @@ cudaError_t launch_loss_grad(const Geo& G, const float2* vol, const float2* img,
                              float scale, float2* grad, double* loss, double* part_loss,
                              double* part_vv, int* n_vv, int grid, int num_sms,
                              cudaStream_t s);
+// grad = lambda v and |v|^2 partials (part_vv[0..*n_vv)).
+cudaError_t launch_init_grad(int n, const float2* vol, float lambda, float2* grad,
+                             double* part_vv, int* n_vv, int num_sms, cudaStream_t s);
+// loss = scale/2 sum(pl[0..n)) + lambda/2 sum(pv[0..nv)), n = *n_dev if n_dev.
+cudaError_t launch_finalize_loss(const double* pl, int n, const int* n_dev, const double* pv,
+                                 int nv, float lambda, float scale, double* loss,
+                                 cudaStream_t s);
+cudaError_t launch_fill(int n, float value, float* out, int num_sms, cudaStream_t s);
+cudaError_t launch_scale_copy(int n, const float* z, float lambda, float* out, int num_sms,
+                              cudaStream_t s);
 cudaError_t launch_hvp(const Geo& G, const float* z, const float* rot, const float* df,
                        int B, float lambda, float scale, float* Hz, int grid,
                        int num_sms, cudaStream_t s);
@@ -102,11 +121,12 @@ cudaError_t launch_direction(int n, const float2* g, const float* dhat, float2* 
 cudaError_t launch_curvature(const Geo& G, const float2* d, const float* rot,
                              const float* df, int B, double* part, int grid,
                              cudaStream_t s);
+// n_loss / n_Q are read from *n_dev when n_dev is not NULL (tile items).
 cudaError_t launch_eta(double* scalars, const double* part_loss, int n_loss,
                        const double* part_vv, int n_vv, const double* part_G,
                        const double* part_dd, int n_dir, const double* part_Q,
-                       int n_Q, float lambda, float scale, float c, int max_halvings,
-                       cudaStream_t s);
+                       int n_Q, const int* n_dev, float lambda, float scale, float c,
+                       int max_halvings, cudaStream_t s);
 cudaError_t launch_update(int n, float2* v, const float2* d, const double* scalars,
                           int num_sms, cudaStream_t s);
 cudaError_t launch_rel_err(const Geo& G, const float2* v, const float2* vref,

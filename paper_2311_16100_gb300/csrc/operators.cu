@@ -163,8 +163,10 @@ k_loss_grad(Geo G, const float2* __restrict__ vol, const float2* __restrict__ im
 
 // loss = scale/2 * sum(pl) + lambda/2 * sum(pv), fixed summation order
 __global__ void __launch_bounds__(1024)
-k_finalize_loss(const double* __restrict__ pl, int nl, const double* __restrict__ pv,
-                int nv, float lambda, float scale, double* loss) {
+k_finalize_loss(const double* __restrict__ pl, int nl, const int* __restrict__ nl_dev,
+                const double* __restrict__ pv, int nv, float lambda, float scale,
+                double* loss) {
+  if (nl_dev) nl = *nl_dev;
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < nl; i += blockDim.x) a += pl[i];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) b += pv[i];
@@ -339,8 +341,8 @@ cudaError_t launch_loss_grad(const Geo& G, const float2* vol, const float2* img,
   count_launches(1);
   if (B > 0) { CS_DISPATCH(G, k_loss_grad, G, vol, img, rot, df, B, scale, grad, part_loss); count_launches(1); }
   if (loss) {
-    k_finalize_loss<<<1, 1024, 0, s>>>(part_loss, B > 0 ? grid : 0, part_vv, gi, lambda,
-                                       scale, loss);
+    k_finalize_loss<<<1, 1024, 0, s>>>(part_loss, B > 0 ? grid : 0, nullptr, part_vv, gi,
+                                       lambda, scale, loss);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -395,6 +397,36 @@ cudaError_t launch_curvature(const Geo& G, const float2* d, const float* rot,
                              const float* df, int B, double* part, int grid,
                              cudaStream_t s) {
   CS_DISPATCH(G, k_curvature, G, d, rot, df, B, part);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_grad(int n, const float2* vol, float lambda, float2* grad,
+                             double* part_vv, int* n_vv, int num_sms, cudaStream_t s) {
+  const int gi = elem_grid(n, num_sms);
+  *n_vv = gi;
+  k_init_grad<<<gi, kBlock, 0, s>>>(n, vol, lambda, grad, part_vv);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_loss(const double* pl, int n, const int* n_dev, const double* pv,
+                                 int nv, float lambda, float scale, double* loss,
+                                 cudaStream_t s) {
+  k_finalize_loss<<<1, 1024, 0, s>>>(pl, n, n_dev, pv, nv, lambda, scale, loss);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(int n, float value, float* out, int num_sms, cudaStream_t s) {
+  k_fill<<<elem_grid(n, num_sms), kBlock, 0, s>>>(n, value, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(int n, const float* z, float lambda, float* out, int num_sms,
+                              cudaStream_t s) {
+  k_scale_copy<<<elem_grid(n, num_sms), kBlock, 0, s>>>(n, z, lambda, out);
   count_launches(1);
   return cudaGetLastError();
 }

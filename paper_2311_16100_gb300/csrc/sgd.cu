@@ -89,8 +89,12 @@ __device__ double sum_fixed(const double* p, int n) {
 // eta = eta_prev 2^-m with eta <= 2 (1 - c) G / Q.
 __global__ void __launch_bounds__(1024)
 k_eta(double* sc, const double* pl, int nl, const double* pv, int nv, const double* pG,
-      const double* pD, int nd, const double* pQ, int nq, float lambda, float scale,
-      float c, int max_halvings) {
+      const double* pD, int nd, const double* pQ, int nq, const int* n_dev, float lambda,
+      float scale, float c, int max_halvings) {
+  if (n_dev) {
+    nl = *n_dev;
+    nq = *n_dev;
+  }
   double L = sum_fixed(pl, nl);
   double V = sum_fixed(pv, nv);
   double G = sum_fixed(pG, nd);
@@ -211,10 +215,10 @@ cudaError_t launch_direction(int n, const float2* g, const float* dhat, float2* 
 cudaError_t launch_eta(double* scalars, const double* part_loss, int n_loss,
                        const double* part_vv, int n_vv, const double* part_G,
                        const double* part_dd, int n_dir, const double* part_Q, int n_Q,
-                       float lambda, float scale, float c, int max_halvings,
-                       cudaStream_t s) {
+                       const int* n_dev, float lambda, float scale, float c,
+                       int max_halvings, cudaStream_t s) {
   k_eta<<<1, 1024, 0, s>>>(scalars, part_loss, n_loss, part_vv, n_vv, part_G, part_dd,
-                           n_dir, part_Q, n_Q, lambda, scale, c, max_halvings);
+                           n_dir, part_Q, n_Q, n_dev, lambda, scale, c, max_halvings);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(PKG, "libcryosgd.so")
 CS_OK, CS_ERR_ARG, CS_ERR_SHAPE, CS_ERR_CUDA, CS_ERR_TIMEOUT, CS_ERR_INTERNAL, CS_ERR_ALLOC = range(7)
 CS_NEAREST, CS_TRILINEAR = 0, 1
 CS_PLAIN, CS_HUTCHINSON, CS_FIXED = 0, 1, 2
+CS_ALGO_AUTO, CS_ALGO_PIXEL, CS_ALGO_TILED = 0, 1, 2
 (CS_S_ETA, CS_S_K, CS_S_ALPHA, CS_S_LOSS, CS_S_G, CS_S_Q, CS_S_HALVINGS,
  CS_S_STATUS, CS_NSCALARS) = range(9)
 CS_MAX_M = 512
@@ -50,6 +51,7 @@ SIGNATURES = {
     "cs_status_string": (c_char_p, [c_int]),
     "cs_reserve": (c_int, [P, c_int, c_int]),
     "cs_workspace_bytes": (c_size_t, [P]),
+    "cs_set_algo": (c_int, [P, c_int]),
     "cs_quat_to_rot": (c_int, [P, P, c_int, P, P]),
     "cs_slice_project": (c_int, [P, G, P, P, P, c_int, P, P]),
     "cs_backproject_adjoint": (c_int, [P, G, P, P, P, c_int, c_float, P, P]),

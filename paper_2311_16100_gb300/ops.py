@@ -117,6 +117,11 @@ class Handle:
     def reserve(self, M: int, max_batch: int = 0):
         self._check("cs_reserve", self.lib.cs_reserve(self.h, M, max_batch))
 
+    def set_algo(self, algo: str):
+        """"tiled" (default) or "pixel" scatter for the adjoint-type passes."""
+        code = {"auto": N.CS_ALGO_AUTO, "pixel": N.CS_ALGO_PIXEL, "tiled": N.CS_ALGO_TILED}[algo]
+        self._check("cs_set_algo", self.lib.cs_set_algo(self.h, code))
+
     def workspace_bytes(self) -> int:
         return int(self.lib.cs_workspace_bytes(self.h))
 

@@ -17,12 +17,14 @@ TOL_SLICE = 1e-5
 TOL_GRAD = 1e-4
 
 
-@pytest.fixture(scope="module")
-def h():
+@pytest.fixture(scope="module", params=["tiled", "pixel"])
+def h(request):
+    """A handle per scatter algorithm: every parity test runs on both."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2311_16100_gb300.ops import Handle
     hd = Handle(0)
+    hd.set_algo(request.param)
     yield hd
     hd.close()
 
