@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=48,
                    help="images in the oracle's timed sample")
-    p.add_argument("--algo", choices=["tiled", "pixel"], default="tiled",
+    p.add_argument("--algo", choices=["auto", "vector", "tiled", "pixel"], default="auto",
                    help="scatter algorithm of the adjoint-type passes")
     p.add_argument("--images", type=int, default=0,
                    help="override the number of images held in HBM (profiling runs)")

@@ -110,13 +110,19 @@ size_t cs_workspace_bytes(const cs_handle* h);
 
 /* Scatter algorithm of the adjoint-type passes (backproject_adjoint,
  * loss_grad, hvp, hutchinson_diag and the SGD step):
- *   CS_ALGO_TILED -- volume tiles binned by image, adjoint accumulated in
- *                    shared memory and added to global memory once per tile
- *                    and work item (default; CS_ALGO_AUTO selects it);
- *   CS_ALGO_PIXEL -- one thread per pixel, FP32 reductions straight into
- *                    global memory.
- * Both compute the same sums (in different orders). */
-enum { CS_ALGO_AUTO = 0, CS_ALGO_PIXEL = 1, CS_ALGO_TILED = 2 };
+ *   CS_ALGO_VECTOR -- one thread per disc pixel; the trilinear adjoint is
+ *                     packed into 16-byte vector reductions into
+ *                     parity-split accumulators, then folded back (default
+ *                     for trilinear interpolation; CS_ALGO_AUTO selects it);
+ *                     in the SGD step the Hutchinson estimate shares the
+ *                     gradient's traversal;
+ *   CS_ALGO_PIXEL  -- one thread per pixel, one FP32 reduction per corner
+ *                     into global memory (AUTO's choice for nearest);
+ *   CS_ALGO_TILED  -- volume tiles binned by image, adjoint accumulated in
+ *                     shared memory and added to global memory once per tile
+ *                     and work item.
+ * All compute the same sums (in different orders). */
+enum { CS_ALGO_AUTO = 0, CS_ALGO_PIXEL = 1, CS_ALGO_TILED = 2, CS_ALGO_VECTOR = 3 };
 int cs_set_algo(cs_handle* h, int algo);
 
 /* Pose -> rotation.  quat float[B][4] unit quaternions (w, x, y, z),
@@ -239,9 +245,13 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
 
 /* Phases of cs_precond_sgd_step timed by the profiler. */
 enum {
-  CS_PH_PRECOND = 0,   /* probe words, Hutchinson estimate, D update (or D-hat) */
-  CS_PH_LOSS_GRAD = 1, /* fused forward, residual, loss and adjoint scatter */
-  CS_PH_DIRECTION = 2, /* d = g / D-hat and its norms */
+  CS_PH_PRECOND = 0,   /* probe words, Hutchinson estimate, D update (vector
+                          algorithm: probe words and accumulator reset only) */
+  CS_PH_LOSS_GRAD = 1, /* forward, residual, loss and adjoint scatter (vector
+                          algorithm: the one traversal that also accumulates
+                          Hutchinson's estimate) */
+  CS_PH_DIRECTION = 2, /* d = g / D-hat and its norms (vector algorithm: also
+                          the accumulator folds and the D update) */
   CS_PH_CURVATURE = 3, /* |C P d|^2 for the Armijo step */
   CS_PH_UPDATE = 4,    /* eta and v -= eta d */
   CS_NPHASES = 5

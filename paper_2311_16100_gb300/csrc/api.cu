@@ -8,6 +8,7 @@
 
 #include "internal.h"
 #include "tiles.h"
+#include "fused.h"
 
 namespace cs {
 
@@ -27,7 +28,7 @@ size_t workspace_bytes(int M, int B) {
          align256(n * sizeof(uint32_t)) + align256(kPartSlots * sizeof(double)) +
          align256(nt * sizeof(int)) + align256(nt * (size_t)(B > 0 ? B : 1) * sizeof(int)) +
          align256((nt + 1) * sizeof(int)) + align256(sizeof(int)) +
-         2 * align256(items * sizeof(double));
+         2 * align256(items * sizeof(double)) + align256(fused_ws_bytes(M));
 }
 
 Workspace carve(void* base, int M, int B) {
@@ -47,7 +48,8 @@ Workspace carve(void* base, int M, int B) {
   w.item_start = reinterpret_cast<int*>(p); p += align256((nt + 1) * sizeof(int));
   w.queue = reinterpret_cast<int*>(p);      p += align256(sizeof(int));
   w.part_items = reinterpret_cast<double*>(p); p += align256(items * sizeof(double));
-  w.part_items2 = reinterpret_cast<double*>(p);
+  w.part_items2 = reinterpret_cast<double*>(p); p += align256(items * sizeof(double));
+  w.fw = fused_carve(p, M);
   return w;
 }
 
@@ -174,7 +176,11 @@ int ensure_ws(cs_handle* h, int M, int B, Workspace* w) {
   return CS_OK;
 }
 
-bool use_tiles(const cs_handle* h) { return h->algo != CS_ALGO_PIXEL; }
+bool use_tiles(const cs_handle* h) { return h->algo == CS_ALGO_TILED; }
+// Vector-reduction passes: the default for trilinear interpolation.
+bool use_vector(const cs_handle* h, const cs_geom* g) {
+  return (h->algo == CS_ALGO_AUTO || h->algo == CS_ALGO_VECTOR) && g->interp == CS_TRILINEAR;
+}
 
 // Bins the batch for the tile engine and fills the common fields of A.
 cudaError_t bin_batch(cs_handle* h, const Geo& G, const Workspace& w, const float* rot,
@@ -293,7 +299,8 @@ size_t cs_workspace_bytes(const cs_handle* h) { return h ? h->ws_bytes : 0; }
 
 int cs_set_algo(cs_handle* h, int algo) {
   if (!h) return CS_ERR_ARG;
-  if (algo != CS_ALGO_AUTO && algo != CS_ALGO_PIXEL && algo != CS_ALGO_TILED)
+  if (algo != CS_ALGO_AUTO && algo != CS_ALGO_PIXEL && algo != CS_ALGO_TILED &&
+      algo != CS_ALGO_VECTOR)
     return fail(h, CS_ERR_ARG, "algo=%d is not a CS_ALGO_* value", algo);
   h->algo = algo;
   return CS_OK;
@@ -337,6 +344,21 @@ int cs_backproject_adjoint(cs_handle* h, const cs_geom* g, const float* images,
   CS_SCOPE(h);
   Geo G = make_geo(*g);
   cudaStream_t s = S(stream);
+  if (use_vector(h, g)) {
+    Workspace w;
+    CS_TRY(ensure_ws(h, g->M, B, &w));
+    const int grid = pixel_grid(h->num_sms, B, g->M);
+    CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
+    CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(launch_fused(F_ADJ, G, w.fw, rot, defocus, B, scale, nullptr, nullptr,
+                         reinterpret_cast<const float2*>(images), nullptr, nullptr, 1, grid, s),
+            "adjoint launch");
+    CS_CUDA(launch_combine_c2(g->M, reinterpret_cast<const float2*>(vol_accum), 1.0f, w.fw,
+                              reinterpret_cast<float2*>(vol_accum), nullptr, nullptr,
+                              h->num_sms, s),
+            "combine launch");
+    return CS_OK;
+  }
   if (!use_tiles(h)) {
     CS_CUDA(launch_backproject(G, reinterpret_cast<const float2*>(images), rot, defocus, B,
                                scale, reinterpret_cast<float2*>(vol_accum),
@@ -369,6 +391,24 @@ int cs_loss_grad(cs_handle* h, const cs_geom* g, const float* vol, const float* 
   Geo G = make_geo(*g);
   cudaStream_t s = S(stream);
   int nvv = 0;
+  if (use_vector(h, g) && B > 0) {
+    const int grid = pixel_grid(h->num_sms, B, g->M);
+    CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
+    CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(launch_fused(F_GRAD, G, w.fw, rot, defocus, B, scale,
+                         reinterpret_cast<const float2*>(vol), nullptr,
+                         reinterpret_cast<const float2*>(images), w.part, nullptr, 1, grid, s),
+            "loss_grad launch");
+    CS_CUDA(launch_combine_c2(g->M, reinterpret_cast<const float2*>(vol), lambda, w.fw,
+                              reinterpret_cast<float2*>(grad), w.part + kPartRegion, &nvv,
+                              h->num_sms, s),
+            "combine launch");
+    if (loss)
+      CS_CUDA(launch_finalize_loss(w.part, grid, nullptr, w.part + kPartRegion, nvv, lambda,
+                                   scale, loss, s),
+              "finalize_loss launch");
+    return CS_OK;
+  }
   if (!use_tiles(h) || B == 0) {
     CS_CUDA(launch_loss_grad(G, reinterpret_cast<const float2*>(vol),
                              reinterpret_cast<const float2*>(images), rot, defocus, B,
@@ -409,6 +449,18 @@ int cs_hvp(cs_handle* h, const cs_geom* g, const float* z, const float* rot,
   CS_SCOPE(h);
   Geo G = make_geo(*g);
   cudaStream_t s = S(stream);
+  if (use_vector(h, g) && B > 0) {
+    Workspace w;
+    CS_TRY(ensure_ws(h, g->M, B, &w));
+    const int grid = pixel_grid(h->num_sms, B, g->M);
+    CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
+    CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(launch_fused(F_HVP, G, w.fw, rot, defocus, B, scale, nullptr, z, nullptr, nullptr,
+                         nullptr, 1, grid, s),
+            "hvp launch");
+    CS_CUDA(launch_combine_r4(g->M, w.fw, 0.0f, lambda, z, Hz, h->num_sms, s), "combine launch");
+    return CS_OK;
+  }
   if (!use_tiles(h) || B == 0) {
     CS_CUDA(launch_hvp(G, z, rot, defocus, B, lambda, scale, Hz,
                        pixel_grid(h->num_sms, B, g->M), h->num_sms, s),
@@ -446,6 +498,17 @@ int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
   if (g->interp == CS_TRILINEAR)
     CS_CUDA(launch_probe_bits(g->M, seed, probe_block, nullptr, w.bits, h->num_sms, s),
             "probe_bits launch");
+  if (use_vector(h, g) && B > 0) {
+    const int grid = pixel_grid(h->num_sms, B, g->M);
+    CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
+    CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(launch_fused(F_HUTCH, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
+                         nullptr, w.bits, n_probes, grid, s),
+            "hutchinson launch");
+    CS_CUDA(launch_combine_r4(g->M, w.fw, lambda, 0.0f, nullptr, diag_out, h->num_sms, s),
+            "combine launch");
+    return CS_OK;
+  }
   if (!use_tiles(h) || B == 0) {
     CS_CUDA(launch_hutchinson(G, w.bits, rot, defocus, B, lambda, scale, n_probes, diag_out,
                               pixel_grid(h->num_sms, B, g->M), h->num_sms, s),
@@ -547,6 +610,54 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
   double* pD = w.part + 2 * kPartRegion; // direction partials (G, |d|^2)
   double* pQ = w.part + 3 * kPartRegion; // curvature partials
   const float* dhat = nullptr;
+  if (use_vector(h, g) && B > 0) {
+    // one traversal computes loss, gradient and (Hutchinson) the estimate
+    const bool hutch = st->mode == CS_HUTCHINSON;
+    int nvv = 0, nd = 0;
+    prof_mark(h, 0, s);
+    CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
+    if (hutch) {
+      CS_CUDA(launch_probe_bits(g->M, st->seed, 0, st->scalars + CS_S_K, w.bits, h->num_sms, s),
+              "probe_bits launch");
+      CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
+    }
+    CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
+    prof_mark(h, CS_PH_LOSS_GRAD, s);
+    CS_CUDA(launch_fused(hutch ? (F_GRAD | F_HUTCH) : F_GRAD, G, w.fw, rot, defocus, B, scale,
+                         reinterpret_cast<const float2*>(st->v), nullptr,
+                         reinterpret_cast<const float2*>(images), pL, w.bits, st->n_probes,
+                         grid, s),
+            "fused loss_grad launch");
+    prof_mark(h, CS_PH_DIRECTION, s);
+    if (hutch) {
+      CS_CUDA(launch_combine_r4(g->M, w.fw, lambda, 0.0f, nullptr, w.dest, h->num_sms, s),
+              "combine launch");
+      CS_CUDA(launch_precond_update(n, w.dest, st->D, st->D_avg, w.dhat, st->scalars,
+                                    st->beta, h->num_sms, s),
+              "precond_update launch");
+      dhat = w.dhat;
+    } else if (st->mode == CS_FIXED) {
+      CS_CUDA(launch_fixed_dhat(n, st->D, w.dhat, st->scalars, h->num_sms, s),
+              "fixed_dhat launch");
+      dhat = w.dhat;
+    }
+    CS_CUDA(launch_combine_c2(g->M, reinterpret_cast<const float2*>(st->v), lambda, w.fw, w.g,
+                              pV, &nvv, h->num_sms, s),
+            "combine launch");
+    CS_CUDA(launch_direction(n, w.g, dhat, w.d, pD, &nd, h->num_sms, s), "direction launch");
+    prof_mark(h, CS_PH_CURVATURE, s);
+    CS_CUDA(launch_fused(F_CURV, G, w.fw, rot, defocus, B, scale, w.d, nullptr, nullptr, pQ,
+                         nullptr, 1, grid, s),
+            "curvature launch");
+    prof_mark(h, CS_PH_UPDATE, s);
+    CS_CUDA(launch_eta(st->scalars, pL, grid, pV, nvv, pD, pD + nd, nd, pQ, grid, nullptr,
+                       lambda, scale, st->c, st->max_halvings, s),
+            "eta launch");
+    CS_CUDA(launch_update(n, reinterpret_cast<float2*>(st->v), w.d, st->scalars, h->num_sms, s),
+            "update launch");
+    prof_mark(h, CS_NPHASES, s);
+    return CS_OK;
+  }
   const bool tiles = use_tiles(h) && B > 0;
   TileArgs A;
   prof_mark(h, 0, s);

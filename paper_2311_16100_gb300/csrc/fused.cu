@@ -1,0 +1,449 @@
+// Pixel-parallel adjoint passes with vector reductions into parity-split
+// accumulators.
+//
+// Global floating-point reductions are executed in L2 at a fixed rate of
+// operations, whatever their width (measured on GB300: ~211 G reductions/s
+// for f32, v2.f32 and v4.f32 alike, with or without lanes sharing an
+// address).  The adjoint of trilinear interpolation (Definition 2.1) adds to
+// the 8 corners of each pixel's cell; the passes here pack those additions
+// into 16-byte reductions:
+//   * complex accumulators: corners (x0, x0+1) of a cell row are 16
+//     contiguous bytes, aligned when x0 is even.  Two buffers are kept, E
+//     (natural layout) and O (shifted by one voxel along x), so that every
+//     pair is one aligned v4 reduction into E (x0 even) or O (x0 odd):
+//     4 reductions per pixel instead of 8;
+//   * real accumulators: four buffers P[px][py] hold the grid as 2x2 (x, y)
+//     patches whose origin has parity (px, py); each z-plane of a cell is one
+//     patch in exactly one buffer: 2 reductions per pixel instead of 8.
+// A combine pass folds the buffers into the natural layout.  Pixels are
+// enumerated from a table of the disc's pixels (no idle lanes outside the
+// disc); images are read once with an evict-first policy so that the
+// accumulators and the volume stay in L2.
+//
+// The fused pass of the SGD step computes, for one mini-batch and one
+// traversal of its pixels, the loss, the gradient (Eq. optim cp) and
+// Hutchinson's estimate (Eq. hutch) from bit-packed probes.
+#include "internal.h"
+#include "fused.h"
+
+namespace cs {
+
+namespace {
+
+// pixel table: entry p = (kx + half) | (ky + half) << 16 for the disc's
+// pixels in row-major order
+__global__ void k_disc_table(int M, int r, int* __restrict__ table, int* __restrict__ n_out) {
+  // one block; rows handled in order with a running offset
+  __shared__ int row_off[CS_MAX_M + 1];
+  const int half = M / 2;
+  for (int ky = -r + (int)threadIdx.x; ky <= r; ky += blockDim.x) {
+    int xr = (int)sqrtf((float)(r * r - ky * ky));
+    while (xr * xr > r * r - ky * ky) --xr;
+    while ((xr + 1) * (xr + 1) <= r * r - ky * ky) ++xr;
+    row_off[ky + r + 1] = 2 * xr + 1;
+  }
+  if (threadIdx.x == 0) row_off[0] = 0;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 1; i <= 2 * r + 1; ++i) row_off[i] += row_off[i - 1];
+  __syncthreads();
+  for (int ky = -r + (int)threadIdx.x; ky <= r; ky += blockDim.x) {
+    const int o = row_off[ky + r], n = row_off[ky + r + 1] - o, xr = (n - 1) / 2;
+    for (int i = 0; i < n; ++i)
+      table[o + i] = ((i - xr) + half) | ((ky + half) << 16);
+  }
+  if (threadIdx.x == 0) *n_out = row_off[2 * r + 1];
+}
+
+struct Cell {
+  int x0, y0, z0;
+  float tx, ty, tz;
+};
+
+__device__ __forceinline__ Cell cell_of(const Geo& G, const Rot& R, int kx, int ky) {
+  const float fx = (float)kx, fy = (float)ky;
+  const float sx = fmaf(R.r1x, fy, R.r0x * fx) + (float)G.half;
+  const float sy = fmaf(R.r1y, fy, R.r0y * fx) + (float)G.half;
+  const float sz = fmaf(R.r1z, fy, R.r0z * fx) + (float)G.half;
+  const float flx = floorf(sx), fly = floorf(sy), flz = floorf(sz);
+  Cell c;
+  c.x0 = (int)flx; c.y0 = (int)fly; c.z0 = (int)flz;
+  c.tx = sx - flx; c.ty = sy - fly; c.tz = sz - flz;
+  return c;
+}
+
+// trilinear gather of a complex volume at a cell (corners outside the grid read 0)
+__device__ __forceinline__ float2 gather_cell(const Geo& G, const Cell& c,
+                                              const float2* __restrict__ v) {
+  const int M = G.M;
+  float re = 0.f, im = 0.f;
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz) {
+    const int z = c.z0 + dz;
+    const float wz = dz ? c.tz : 1.f - c.tz;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const int y = c.y0 + dy;
+      const float wzy = wz * (dy ? c.ty : 1.f - c.ty);
+      if ((unsigned)z >= (unsigned)M || (unsigned)y >= (unsigned)M) continue;
+      const float2* row = v + ((size_t)z * M + y) * M;
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const int x = c.x0 + dx;
+        if ((unsigned)x >= (unsigned)M) continue;
+        const float w = wzy * (dx ? c.tx : 1.f - c.tx);
+        const float2 a = __ldg(row + x);
+        re = fmaf(w, a.x, re);
+        im = fmaf(w, a.y, im);
+      }
+    }
+  }
+  return make_float2(re, im);
+}
+
+__device__ __forceinline__ float corner_w(const Cell& c, int k) {
+  const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+  return (dx ? c.tx : 1.f - c.tx) * (dy ? c.ty : 1.f - c.ty) * (dz ? c.tz : 1.f - c.tz);
+}
+
+__device__ __forceinline__ bool corner_in(const Geo& G, const Cell& c, int k) {
+  const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+  return (unsigned)(c.x0 + dx) < (unsigned)G.M && (unsigned)(c.y0 + dy) < (unsigned)G.M &&
+         (unsigned)(c.z0 + dz) < (unsigned)G.M;
+}
+
+// A cell whose base corner lies inside the grid (always the case for
+// rotations and r_max <= M/2 - 1); other cells take the per-corner path.
+__device__ __forceinline__ bool base_in(const Geo& G, const Cell& c) {
+  return (unsigned)c.x0 < (unsigned)G.M && (unsigned)c.y0 < (unsigned)G.M &&
+         (unsigned)c.z0 < (unsigned)G.M;
+}
+
+// adds val * w(corner) to the 8 corners of a cell: one v4 reduction per
+// (y, z) corner row, into E (x0 even) or O (x0 odd, shifted by one voxel)
+__device__ __forceinline__ void scatter_cell_c2(const Geo& G, const Cell& c, float2 val,
+                                                float2* __restrict__ E, float2* __restrict__ O) {
+  const int M = G.M;
+  if (!base_in(G, c)) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (!corner_in(G, c, k)) continue;
+      const float w = corner_w(c, k);
+      const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+      atomicAdd(E + ((size_t)(c.z0 + dz) * M + (c.y0 + dy)) * M + (c.x0 + dx),
+                make_float2(w * val.x, w * val.y));
+    }
+    return;
+  }
+  const bool odd = c.x0 & 1;
+  float2* base = odd ? O : E;
+  const int xb = odd ? c.x0 - 1 : c.x0;      // even slot of the pair
+  const float w0x = 1.f - c.tx, w1x = c.tx;
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz) {
+    const int z = c.z0 + dz;
+    const float wz = dz ? c.tz : 1.f - c.tz;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const int y = c.y0 + dy;
+      if (z >= M || y >= M) continue;
+      const float wzy = wz * (dy ? c.ty : 1.f - c.ty);
+      const float a0 = wzy * w0x, a1 = wzy * w1x;
+      float4* p = reinterpret_cast<float4*>(base + ((size_t)z * M + y) * M + xb);
+      atomicAdd(p, make_float4(a0 * val.x, a0 * val.y, a1 * val.x, a1 * val.y));
+    }
+  }
+}
+
+// adds per-corner real values to the 2x2 (x, y) patch buffers, one v4
+// reduction per z-plane.  vals[k] for corner k = dx + 2 dy + 4 dz.
+__device__ __forceinline__ void scatter_cell_r4(const Geo& G, const Cell& c, const float* vals,
+                                                float* __restrict__ P) {
+  const int M = G.M, Mh = G.M / 2;
+  const size_t nb = (size_t)M * M * M;
+  if (!base_in(G, c)) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (!corner_in(G, c, k)) continue;
+      const int x = c.x0 + (k & 1), y = c.y0 + ((k >> 1) & 1), z = c.z0 + (k >> 2);
+      float* buf = P + (size_t)((y & 1) * 2 + (x & 1)) * nb;
+      atomicAdd(buf + 4 * (((size_t)z * Mh + (y >> 1)) * Mh + (x >> 1)), vals[k]);
+    }
+    return;
+  }
+  const int px = c.x0 & 1, py = c.y0 & 1;
+  float* buf = P + (size_t)(py * 2 + px) * nb;
+  const int X = (c.x0 - px) >> 1, Y = (c.y0 - py) >> 1;
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz) {
+    const int z = c.z0 + dz;
+    if (z >= M) continue;
+    float4* p = reinterpret_cast<float4*>(buf + 4 * (((size_t)z * Mh + Y) * Mh + X));
+    atomicAdd(p, make_float4(vals[4 * dz + 0], vals[4 * dz + 1], vals[4 * dz + 2],
+                             vals[4 * dz + 3]));
+  }
+}
+
+__device__ __forceinline__ uint32_t bits_at(const Geo& G, const Cell& c, int k,
+                                            const uint32_t* __restrict__ bits) {
+  const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+  if (!corner_in(G, c, k)) return 0u;
+  return __ldg(bits + ((size_t)(c.z0 + dz) * G.M + (c.y0 + dy)) * G.M + (c.x0 + dx));
+}
+
+// real trilinear gather (corners outside the grid read 0)
+__device__ __forceinline__ float gather_cell_r(const Geo& G, const Cell& c,
+                                               const float* __restrict__ z) {
+  float a = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (!corner_in(G, c, k)) continue;
+    const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+    a = fmaf(corner_w(c, k),
+             __ldg(z + ((size_t)(c.z0 + dz) * G.M + (c.y0 + dy)) * G.M + (c.x0 + dx)), a);
+  }
+  return a;
+}
+
+struct FusedArgs {
+  Geo G;
+  const int* table;
+  const int* n_px_dev;
+  const float* rot;
+  const float* df;
+  int B;
+  float scale;
+  const float2* vol;    // F_GRAD: volume; F_CURV: direction d
+  const float* zr;      // F_HVP: real vector z
+  const float2* img;    // F_ADJ, F_GRAD
+  float2* E;
+  float2* O;
+  double* part;         // F_GRAD: data-term partials; F_CURV: curvature partials
+  const uint32_t* bits; // F_HUTCH
+  float* P;             // F_HUTCH, F_HVP
+  int K;
+};
+
+// One traversal of the batch's disc pixels (trilinear).  Work item =
+// (image, 256 consecutive disc pixels); a fixed grid walks the items, so
+// the per-block partial sums are deterministic.
+//   F_ADJ   : E/O += scale C y                    (adjoint of the forward model)
+//   F_GRAD  : r = C P v - x; loss += |r|^2; E/O += scale C r     (Eq. optim cp)
+//   F_HUTCH : P4 += scale C^2 w_j sum_l w_l Z_jl  (Eq. hutch, bit-packed probes)
+//   F_HVP   : P4 += scale C^2 w_j (P z)           (Eq. hessian)
+//   F_CURV  : part += C^2 |P d|^2                 (curvature of the Armijo step)
+template <int FL>
+__global__ void __launch_bounds__(256)
+k_fused(FusedArgs A) {
+  const Geo& G = A.G;
+  const int n_px = *A.n_px_dev;
+  const int nch = (n_px + 255) >> 8;
+  const int total = A.B * nch;
+  const int MM = G.M * G.M;
+  const uint32_t pmask = A.K >= 32 ? 0xffffffffu : ((1u << A.K) - 1u);
+  const float invK = 1.0f / (float)(A.K > 0 ? A.K : 1);
+  float acc = 0.f;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int b = w / nch;
+    const int p = (w - b * nch) * 256 + threadIdx.x;
+    if (p >= n_px) continue;
+    const int e = __ldg(A.table + p);
+    const int ix = e & 0xffff, iy = e >> 16;
+    const int kx = ix - G.half, ky = iy - G.half;
+    const Rot R = load_rot(A.rot, b);
+    const Cell c = cell_of(G, R, kx, ky);
+    float C = 1.f;
+    if (G.ctf_on) {
+      float a_hi, a_lo;
+      ctf_coeff(G, __ldg(A.df + b), a_hi, a_lo);
+      C = ctf_value(G, a_hi, a_lo, kx * kx + ky * ky);
+    }
+    if (FL & (F_ADJ | F_GRAD)) {
+      float2 r = __ldcs(A.img + (size_t)b * MM + (size_t)iy * G.M + ix);
+      if (FL & F_GRAD) {
+        const float2 a = gather_cell(G, c, A.vol);
+        r = make_float2(fmaf(C, a.x, -r.x), fmaf(C, a.y, -r.y));
+        acc = fmaf(r.x, r.x, fmaf(r.y, r.y, acc));
+      }
+      const float sc = A.scale * C;
+      scatter_cell_c2(G, c, make_float2(sc * r.x, sc * r.y), A.E, A.O);
+    }
+    if (FL & F_CURV) {
+      const float2 a = gather_cell(G, c, A.vol);
+      acc = fmaf(C * C, fmaf(a.x, a.x, a.y * a.y), acc);
+    }
+    if (FL & F_HVP) {
+      const float y = A.scale * C * C * gather_cell_r(G, c, A.zr);
+      float vals[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) vals[k] = corner_in(G, c, k) ? corner_w(c, k) * y : 0.f;
+      scatter_cell_r4(G, c, vals, A.P);
+    }
+    if (FL & F_HUTCH) {
+      uint32_t bw[8];
+      float w8[8], wsum = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        w8[k] = corner_in(G, c, k) ? corner_w(c, k) : 0.f;
+        bw[k] = bits_at(G, c, k, A.bits);
+        wsum += w8[k];
+      }
+      const float sc = A.scale * C * C;
+      float vals[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float pc = 0.f;
+#pragma unroll
+        for (int l = 0; l < 8; ++l)
+          if (l != j) pc = fmaf(w8[l], (float)__popc((bw[j] ^ bw[l]) & pmask), pc);
+        vals[j] = sc * w8[j] * fmaf(-2.0f * invK, pc, wsum);
+      }
+      scatter_cell_r4(G, c, vals, A.P);
+    }
+  }
+  if (FL & (F_GRAD | F_CURV)) {
+    const double t = block_sum((double)acc);
+    if (threadIdx.x == 0) A.part[blockIdx.x] = t;
+  }
+}
+
+// g = lambda v + E + shift(O), and |v|^2 partials
+__global__ void __launch_bounds__(256)
+k_combine_c2(int M, const float2* __restrict__ v, float lambda, const float2* __restrict__ E,
+             const float2* __restrict__ O, float2* __restrict__ g, double* __restrict__ part) {
+  const int n = M * M * M;
+  double accv = 0.0;
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
+    const int x = j % M;
+    float2 a = v ? v[j] : make_float2(0.f, 0.f);
+    float2 r = E[j];
+    if (x >= 1) {
+      const float2 o = O[j - 1];
+      r.x += o.x;
+      r.y += o.y;
+    }
+    g[j] = make_float2(fmaf(lambda, a.x, r.x), fmaf(lambda, a.y, r.y));
+    accv += (double)fmaf(a.x, a.x, a.y * a.y);
+  }
+  if (part) {
+    const double t = block_sum(accv);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+  }
+}
+
+// out = base + coef * add + sum over the four patch buffers
+__global__ void __launch_bounds__(256)
+k_combine_r4(int M, const float* __restrict__ P, float base, float coef,
+             const float* __restrict__ add, float* __restrict__ out) {
+  const int n = M * M * M, Mh = M / 2;
+  const size_t nb = (size_t)n;
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
+    const int x = j % M, y = (j / M) % M, z = j / (M * M);
+    float s = add ? fmaf(coef, add[j], base) : base;
+#pragma unroll
+    for (int py = 0; py < 2; ++py) {
+#pragma unroll
+      for (int px = 0; px < 2; ++px) {
+        const int xx = x - px, yy = y - py;
+        if (xx < 0 || yy < 0) continue;
+        const float* buf = P + (size_t)(py * 2 + px) * nb;
+        s += buf[4 * (((size_t)z * Mh + (yy >> 1)) * Mh + (xx >> 1)) + 2 * (yy & 1) + (xx & 1)];
+      }
+    }
+    out[j] = s;
+  }
+}
+
+int elem_grid(int n, int num_sms) {
+  int g = (n + 255) / 256;
+  return g < num_sms * 4 ? (g > 0 ? g : 1) : num_sms * 4;
+}
+
+}  // namespace
+
+size_t fused_ws_bytes(int M) {
+  const size_t n = (size_t)M * M * M;
+  // E, O (complex), P (4 real buffers), disc table, count
+  return 2 * n * sizeof(float2) + 4 * n * sizeof(float) + (size_t)M * M * sizeof(int) + 256;
+}
+
+FusedWs fused_carve(void* base, int M) {
+  const size_t n = (size_t)M * M * M;
+  char* p = static_cast<char*>(base);
+  FusedWs w;
+  w.E = reinterpret_cast<float2*>(p);   p += n * sizeof(float2);
+  w.O = reinterpret_cast<float2*>(p);   p += n * sizeof(float2);
+  w.P = reinterpret_cast<float*>(p);    p += 4 * n * sizeof(float);
+  w.table = reinterpret_cast<int*>(p);  p += (size_t)M * M * sizeof(int);
+  w.n_px = reinterpret_cast<int*>(p);
+  return w;
+}
+
+cudaError_t launch_disc_table(int M, int r, const FusedWs& w, cudaStream_t s) {
+  k_disc_table<<<1, 256, 0, s>>>(M, r, w.table, w.n_px);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float* rot,
+                         const float* df, int B, float scale, const float2* vol,
+                         const float* zr, const float2* img, double* part,
+                         const uint32_t* bits, int K, int grid, cudaStream_t s) {
+  FusedArgs A;
+  A.G = G;
+  A.table = w.table;
+  A.n_px_dev = w.n_px;
+  A.rot = rot;
+  A.df = df;
+  A.B = B;
+  A.scale = scale;
+  A.vol = vol;
+  A.zr = zr;
+  A.img = img;
+  A.E = w.E;
+  A.O = w.O;
+  A.part = part;
+  A.bits = bits;
+  A.P = w.P;
+  A.K = K;
+  switch (flags) {
+    case F_ADJ: k_fused<F_ADJ><<<grid, 256, 0, s>>>(A); break;
+    case F_GRAD: k_fused<F_GRAD><<<grid, 256, 0, s>>>(A); break;
+    case F_GRAD | F_HUTCH: k_fused<F_GRAD | F_HUTCH><<<grid, 256, 0, s>>>(A); break;
+    case F_HUTCH: k_fused<F_HUTCH><<<grid, 256, 0, s>>>(A); break;
+    case F_HVP: k_fused<F_HVP><<<grid, 256, 0, s>>>(A); break;
+    case F_CURV: k_fused<F_CURV><<<grid, 256, 0, s>>>(A); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_c2(int M, const FusedWs& w, cudaStream_t s) {
+  const size_t n = (size_t)M * M * M;
+  return cudaMemsetAsync(w.E, 0, 2 * n * sizeof(float2), s);
+}
+
+cudaError_t launch_zero_r4(int M, const FusedWs& w, cudaStream_t s) {
+  const size_t n = (size_t)M * M * M;
+  return cudaMemsetAsync(w.P, 0, 4 * n * sizeof(float), s);
+}
+
+cudaError_t launch_combine_c2(int M, const float2* v, float lambda, const FusedWs& w,
+                              float2* g, double* part_vv, int* n_vv, int num_sms,
+                              cudaStream_t s) {
+  const int gb = elem_grid(M * M * M, num_sms);
+  if (n_vv) *n_vv = gb;
+  k_combine_c2<<<gb, 256, 0, s>>>(M, v, lambda, w.E, w.O, g, part_vv);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_r4(int M, const FusedWs& w, float base, float coef,
+                              const float* add, float* out, int num_sms, cudaStream_t s) {
+  k_combine_r4<<<elem_grid(M * M * M, num_sms), 256, 0, s>>>(M, w.P, base, coef, add, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace cs

@@ -1,0 +1,31 @@
+// Vector-reduction pixel passes (see fused.cu).
+#pragma once
+
+#include "internal.h"
+
+namespace cs {
+
+enum FusedFlags { F_ADJ = 1, F_GRAD = 2, F_HUTCH = 4, F_HVP = 8, F_CURV = 16 };
+
+
+
+size_t fused_ws_bytes(int M);
+FusedWs fused_carve(void* base, int M);
+
+cudaError_t launch_disc_table(int M, int r, const FusedWs& w, cudaStream_t s);
+// One trilinear traversal with the given flags (partials: one per block).
+cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float* rot,
+                         const float* df, int B, float scale, const float2* vol,
+                         const float* zr, const float2* img, double* part,
+                         const uint32_t* bits, int K, int grid, cudaStream_t s);
+cudaError_t launch_zero_c2(int M, const FusedWs& w, cudaStream_t s);
+cudaError_t launch_zero_r4(int M, const FusedWs& w, cudaStream_t s);
+// g = lambda v + E + shift(O) (v may be NULL); |v|^2 partials if part_vv.
+cudaError_t launch_combine_c2(int M, const float2* v, float lambda, const FusedWs& w,
+                              float2* g, double* part_vv, int* n_vv, int num_sms,
+                              cudaStream_t s);
+// out = base + coef * add + (patch buffers); add may be NULL.
+cudaError_t launch_combine_r4(int M, const FusedWs& w, float base, float coef,
+                              const float* add, float* out, int num_sms, cudaStream_t s);
+
+}  // namespace cs

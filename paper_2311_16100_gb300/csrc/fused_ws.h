@@ -1,0 +1,16 @@
+// Workspace of the vector-reduction passes (see fused.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace cs {
+
+struct FusedWs {
+  float2* E;      // complex accumulator, natural layout [M^3]
+  float2* O;      // complex accumulator shifted by one voxel along x [M^3]
+  float* P;       // four real 2x2-patch accumulators [4][M^3]
+  int* table;     // disc pixel table [M*M]
+  int* n_px;      // number of disc pixels
+};
+
+}  // namespace cs

@@ -12,6 +12,7 @@
 
 #include "../../include/cryosgd.h"
 #include "device.cuh"
+#include "fused_ws.h"
 
 struct cs_handle {
   int device = 0;
@@ -50,6 +51,7 @@ struct Workspace {
   int* queue;        // [1]
   double* part_items;   // [max items]: loss partials
   double* part_items2;  // [max items]: curvature partials
+  FusedWs fw;           // vector-reduction accumulators and disc table
 };
 
 constexpr int kPartRegion = 8192;           // doubles per partial-sum region

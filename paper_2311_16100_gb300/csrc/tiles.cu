@@ -315,8 +315,12 @@ k_tile(TileArgs A) {
           if (lane >= o) incl += v;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        for (int fb = 0; fb < total; fb += 32) {
-          const int f = fb + lane;
+        // lane l takes the contiguous candidate run [l*per, (l+1)*per): lanes of
+        // one instruction then sit ~per pixels apart, so their cells (and the
+        // shared-memory words they accumulate into) rarely coincide
+        const int per = (total + 31) >> 5;
+        for (int j = 0; j < per; ++j) {
+          const int f = lane * per + j;
           int pos = 0;
 #pragma unroll
           for (int s = 16; s >= 1; s >>= 1) {

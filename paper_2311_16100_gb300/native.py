@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(PKG, "libcryosgd.so")
 CS_OK, CS_ERR_ARG, CS_ERR_SHAPE, CS_ERR_CUDA, CS_ERR_TIMEOUT, CS_ERR_INTERNAL, CS_ERR_ALLOC = range(7)
 CS_NEAREST, CS_TRILINEAR = 0, 1
 CS_PLAIN, CS_HUTCHINSON, CS_FIXED = 0, 1, 2
-CS_ALGO_AUTO, CS_ALGO_PIXEL, CS_ALGO_TILED = 0, 1, 2
+CS_ALGO_AUTO, CS_ALGO_PIXEL, CS_ALGO_TILED, CS_ALGO_VECTOR = 0, 1, 2, 3
 (CS_S_ETA, CS_S_K, CS_S_ALPHA, CS_S_LOSS, CS_S_G, CS_S_Q, CS_S_HALVINGS,
  CS_S_STATUS, CS_NSCALARS) = range(9)
 CS_MAX_M = 512

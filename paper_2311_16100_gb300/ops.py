@@ -118,8 +118,10 @@ class Handle:
         self._check("cs_reserve", self.lib.cs_reserve(self.h, M, max_batch))
 
     def set_algo(self, algo: str):
-        """"tiled" (default) or "pixel" scatter for the adjoint-type passes."""
-        code = {"auto": N.CS_ALGO_AUTO, "pixel": N.CS_ALGO_PIXEL, "tiled": N.CS_ALGO_TILED}[algo]
+        """Scatter algorithm of the adjoint-type passes: "auto" (default),
+        "vector", "pixel" or "tiled"."""
+        code = {"auto": N.CS_ALGO_AUTO, "pixel": N.CS_ALGO_PIXEL, "tiled": N.CS_ALGO_TILED,
+                "vector": N.CS_ALGO_VECTOR}[algo]
         self._check("cs_set_algo", self.lib.cs_set_algo(self.h, code))
 
     def workspace_bytes(self) -> int:

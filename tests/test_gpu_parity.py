@@ -17,7 +17,7 @@ TOL_SLICE = 1e-5
 TOL_GRAD = 1e-4
 
 
-@pytest.fixture(scope="module", params=["tiled", "pixel"])
+@pytest.fixture(scope="module", params=["vector", "tiled", "pixel"])
 def h(request):
     """A handle per scatter algorithm: every parity test runs on both."""
     if not torch.cuda.is_available():
