@@ -168,9 +168,9 @@ int cs_hvp(cs_handle* h, const cs_geom* g, const float* z, const float* rot,
 /* Hutchinson's diagonal estimate (Eq. hutch) with K = n_probes (1..32)
  * Rademacher probes on the mini-batch Hessian:
  *   diag_out = (1/K) sum_k z_k (.) H z_k   (float[M^3], overwritten).
- * Probe k of voxel j is -1 if bit k of W_j is set, +1 otherwise, where W_j
- * is the low 32 bits of output number probe_block*M^3 + j of a SplitMix64
- * stream seeded with `seed`.  Computed exactly (up to rounding) without
+ * Probe k of voxel j is -1 if bit k of W_j is set, +1 otherwise, where the
+ * words of voxels 2i and 2i+1 are the low and high 32 bits of output number
+ * probe_block*M^3/2 + i of a SplitMix64 stream seeded with `seed`.  Computed exactly (up to rounding) without
  * forming the K products separately. */
 int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
                        const float* defocus, int B, float lambda, float scale,

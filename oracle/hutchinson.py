@@ -32,11 +32,16 @@ def splitmix64(seed: int, counters: np.ndarray) -> np.ndarray:
 def probe_words(seed: int, block: int, n_vox: int) -> np.ndarray:
     """32 probe bits per voxel for probe block ``block``: uint32 [n_vox].
 
-    Word of voxel j = low 32 bits of SplitMix64 output number block*n_vox + j.
+    Voxels are taken in pairs (2i, 2i+1): both words come from SplitMix64
+    output number block*ceil(n_vox/2) + i, the low 32 bits for voxel 2i and
+    the high 32 bits for voxel 2i+1.
     """
+    n_pairs = (n_vox + 1) // 2
     j = np.arange(n_vox, dtype=np.uint64)
-    c = np.uint64(block) * np.uint64(n_vox) + j
-    return (splitmix64(seed, c) & _MASK32).astype(np.uint32)
+    c = np.uint64(block) * np.uint64(n_pairs) + (j >> np.uint64(1))
+    out = splitmix64(seed, c)
+    half = (j & np.uint64(1)) * np.uint64(32)
+    return ((out >> half) & _MASK32).astype(np.uint32)
 
 
 def rademacher_probes(seed: int, block: int, n_vox: int, n_probes: int) -> np.ndarray:

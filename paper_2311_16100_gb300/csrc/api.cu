@@ -350,8 +350,9 @@ int cs_backproject_adjoint(cs_handle* h, const cs_geom* g, const float* images,
     const int grid = pixel_grid(h->num_sms, B, g->M);
     CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
     CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
-    CS_CUDA(launch_fused(F_ADJ, G, w.fw, rot, defocus, B, scale, nullptr, nullptr,
-                         reinterpret_cast<const float2*>(images), nullptr, nullptr, 1, grid, s),
+    CS_CUDA(launch_fused(F_ADJ, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
+                         reinterpret_cast<const float2*>(images), nullptr, 0, 0, nullptr, 1,
+                         grid, s),
             "adjoint launch");
     CS_CUDA(launch_combine_c2(g->M, reinterpret_cast<const float2*>(vol_accum), 1.0f, w.fw,
                               reinterpret_cast<float2*>(vol_accum), nullptr, nullptr,
@@ -395,9 +396,12 @@ int cs_loss_grad(cs_handle* h, const cs_geom* g, const float* vol, const float* 
     const int grid = pixel_grid(h->num_sms, B, g->M);
     CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
     CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(launch_pairs(g->M, reinterpret_cast<const float2*>(vol), w.fw.pairs, h->num_sms, s),
+            "pairs launch");
     CS_CUDA(launch_fused(F_GRAD, G, w.fw, rot, defocus, B, scale,
-                         reinterpret_cast<const float2*>(vol), nullptr,
-                         reinterpret_cast<const float2*>(images), w.part, nullptr, 1, grid, s),
+                         reinterpret_cast<const float2*>(vol), w.fw.pairs, nullptr,
+                         reinterpret_cast<const float2*>(images), w.part, 0, 0, nullptr, 1,
+                         grid, s),
             "loss_grad launch");
     CS_CUDA(launch_combine_c2(g->M, reinterpret_cast<const float2*>(vol), lambda, w.fw,
                               reinterpret_cast<float2*>(grad), w.part + kPartRegion, &nvv,
@@ -455,8 +459,8 @@ int cs_hvp(cs_handle* h, const cs_geom* g, const float* z, const float* rot,
     const int grid = pixel_grid(h->num_sms, B, g->M);
     CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
     CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
-    CS_CUDA(launch_fused(F_HVP, G, w.fw, rot, defocus, B, scale, nullptr, z, nullptr, nullptr,
-                         nullptr, 1, grid, s),
+    CS_CUDA(launch_fused(F_HVP, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, z, nullptr,
+                         nullptr, 0, 0, nullptr, 1, grid, s),
             "hvp launch");
     CS_CUDA(launch_combine_r4(g->M, w.fw, 0.0f, lambda, z, Hz, h->num_sms, s), "combine launch");
     return CS_OK;
@@ -495,20 +499,20 @@ int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
   CS_TRY(ensure_ws(h, g->M, B, &w));
   Geo G = make_geo(*g);
   cudaStream_t s = S(stream);
-  if (g->interp == CS_TRILINEAR)
-    CS_CUDA(launch_probe_bits(g->M, seed, probe_block, nullptr, w.bits, h->num_sms, s),
-            "probe_bits launch");
   if (use_vector(h, g) && B > 0) {
     const int grid = pixel_grid(h->num_sms, B, g->M);
     CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
     CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_HUTCH, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
-                         nullptr, w.bits, n_probes, grid, s),
+                         nullptr, nullptr, seed, probe_block, nullptr, n_probes, grid, s),
             "hutchinson launch");
     CS_CUDA(launch_combine_r4(g->M, w.fw, lambda, 0.0f, nullptr, diag_out, h->num_sms, s),
             "combine launch");
     return CS_OK;
   }
+  if (g->interp == CS_TRILINEAR)
+    CS_CUDA(launch_probe_bits(g->M, seed, probe_block, nullptr, w.bits, h->num_sms, s),
+            "probe_bits launch");
   if (!use_tiles(h) || B == 0) {
     CS_CUDA(launch_hutchinson(G, w.bits, rot, defocus, B, lambda, scale, n_probes, diag_out,
                               pixel_grid(h->num_sms, B, g->M), h->num_sms, s),
@@ -616,17 +620,15 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
     int nvv = 0, nd = 0;
     prof_mark(h, 0, s);
     CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
-    if (hutch) {
-      CS_CUDA(launch_probe_bits(g->M, st->seed, 0, st->scalars + CS_S_K, w.bits, h->num_sms, s),
-              "probe_bits launch");
-      CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
-    }
+    if (hutch) CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(launch_pairs(g->M, reinterpret_cast<const float2*>(st->v), w.fw.pairs, h->num_sms, s),
+            "pairs launch");
     prof_mark(h, CS_PH_LOSS_GRAD, s);
     CS_CUDA(launch_fused(hutch ? (F_GRAD | F_HUTCH) : F_GRAD, G, w.fw, rot, defocus, B, scale,
-                         reinterpret_cast<const float2*>(st->v), nullptr,
-                         reinterpret_cast<const float2*>(images), pL, w.bits, st->n_probes,
-                         grid, s),
+                         reinterpret_cast<const float2*>(st->v), w.fw.pairs, nullptr,
+                         reinterpret_cast<const float2*>(images), pL, st->seed, 0,
+                         st->scalars + CS_S_K, st->n_probes, grid, s),
             "fused loss_grad launch");
     prof_mark(h, CS_PH_DIRECTION, s);
     if (hutch) {
@@ -645,9 +647,10 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
                               pV, &nvv, h->num_sms, s),
             "combine launch");
     CS_CUDA(launch_direction(n, w.g, dhat, w.d, pD, &nd, h->num_sms, s), "direction launch");
+    CS_CUDA(launch_pairs(g->M, w.d, w.fw.pairs, h->num_sms, s), "pairs launch");
     prof_mark(h, CS_PH_CURVATURE, s);
-    CS_CUDA(launch_fused(F_CURV, G, w.fw, rot, defocus, B, scale, w.d, nullptr, nullptr, pQ,
-                         nullptr, 1, grid, s),
+    CS_CUDA(launch_fused(F_CURV, G, w.fw, rot, defocus, B, scale, w.d, w.fw.pairs, nullptr,
+                         nullptr, pQ, 0, 0, nullptr, 1, grid, s),
             "curvature launch");
     prof_mark(h, CS_PH_UPDATE, s);
     CS_CUDA(launch_eta(st->scalars, pL, grid, pV, nvv, pD, pD + nd, nd, pQ, grid, nullptr,

@@ -130,6 +130,12 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t c) {
   return z ^ (z >> 31);
 }
 
+// Probe words: voxels (2i, 2i+1) take the low / high 32 bits of SplitMix64
+// output number block * (n_vox / 2) + i (n_vox = M^3 is even).
+__device__ __forceinline__ uint64_t probe_pair(uint64_t seed, uint64_t pair_base, uint64_t i) {
+  return splitmix64(seed, pair_base + i);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -101,6 +101,31 @@ __device__ __forceinline__ float2 gather_cell(const Geo& G, const Cell& c,
   return make_float2(re, im);
 }
 
+// trilinear gather from the pair layout vp[j] = (v[j], v[j+1]): one aligned
+// 16-byte load per (y, z) corner row.  Only for cells with base_in().
+__device__ __forceinline__ float2 gather_cell_pairs(const Geo& G, const Cell& c,
+                                                    const float4* __restrict__ vp) {
+  const int M = G.M;
+  const float w0x = 1.f - c.tx, w1x = c.tx;
+  float re = 0.f, im = 0.f;
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz) {
+    const int z = c.z0 + dz;
+    const float wz = dz ? c.tz : 1.f - c.tz;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const int y = c.y0 + dy;
+      if (z >= M || y >= M) continue;
+      const float wzy = wz * (dy ? c.ty : 1.f - c.ty);
+      const float4 a = __ldg(vp + ((size_t)z * M + y) * M + c.x0);
+      const float a0 = wzy * w0x, a1 = wzy * w1x;
+      re = fmaf(a0, a.x, fmaf(a1, a.z, re));
+      im = fmaf(a0, a.y, fmaf(a1, a.w, im));
+    }
+  }
+  return make_float2(re, im);
+}
+
 __device__ __forceinline__ float corner_w(const Cell& c, int k) {
   const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
   return (dx ? c.tx : 1.f - c.tx) * (dy ? c.ty : 1.f - c.ty) * (dz ? c.tz : 1.f - c.tz);
@@ -184,12 +209,6 @@ __device__ __forceinline__ void scatter_cell_r4(const Geo& G, const Cell& c, con
   }
 }
 
-__device__ __forceinline__ uint32_t bits_at(const Geo& G, const Cell& c, int k,
-                                            const uint32_t* __restrict__ bits) {
-  const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-  if (!corner_in(G, c, k)) return 0u;
-  return __ldg(bits + ((size_t)(c.z0 + dz) * G.M + (c.y0 + dy)) * G.M + (c.x0 + dx));
-}
 
 // real trilinear gather (corners outside the grid read 0)
 __device__ __forceinline__ float gather_cell_r(const Geo& G, const Cell& c,
@@ -219,10 +238,28 @@ struct FusedArgs {
   float2* E;
   float2* O;
   double* part;         // F_GRAD: data-term partials; F_CURV: curvature partials
-  const uint32_t* bits; // F_HUTCH
+  const uint32_t* bits; // unused (probe words are generated in place)
   float* P;             // F_HUTCH, F_HVP
   int K;
+  const float4* vp;     // pair layout of vol (F_GRAD, F_CURV)
+  uint64_t seed;        // F_HUTCH: probe stream
+  uint64_t block_host;  // F_HUTCH: probe block, or
+  const double* k_dev;  //   (iterations done + 1) read from the SGD state
 };
+
+// Probe words of the corners (x0, x0+1) of one cell row starting at linear
+// index j = row + x0: voxels (2i, 2i+1) share SplitMix64 output i.
+__device__ __forceinline__ void row_words(uint64_t seed, uint64_t base, size_t j, uint32_t& b0,
+                                          uint32_t& b1) {
+  if ((j & 1) == 0) {
+    const uint64_t w = probe_pair(seed, base, (uint64_t)(j >> 1));
+    b0 = (uint32_t)w;
+    b1 = (uint32_t)(w >> 32);
+  } else {
+    b0 = (uint32_t)(probe_pair(seed, base, (uint64_t)(j >> 1)) >> 32);
+    b1 = (uint32_t)probe_pair(seed, base, (uint64_t)((j + 1) >> 1));
+  }
+}
 
 // One traversal of the batch's disc pixels (trilinear).  Work item =
 // (image, 256 consecutive disc pixels); a fixed grid walks the items, so
@@ -242,6 +279,11 @@ k_fused(FusedArgs A) {
   const int MM = G.M * G.M;
   const uint32_t pmask = A.K >= 32 ? 0xffffffffu : ((1u << A.K) - 1u);
   const float invK = 1.0f / (float)(A.K > 0 ? A.K : 1);
+  uint64_t pbase = 0;
+  if (FL & F_HUTCH) {
+    const uint64_t blk = A.k_dev ? (uint64_t)(*A.k_dev) + 1ull : A.block_host;
+    pbase = blk * (((uint64_t)G.M * G.M * G.M) >> 1);
+  }
   float acc = 0.f;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const int b = w / nch;
@@ -258,10 +300,11 @@ k_fused(FusedArgs A) {
       ctf_coeff(G, __ldg(A.df + b), a_hi, a_lo);
       C = ctf_value(G, a_hi, a_lo, kx * kx + ky * ky);
     }
+    const bool inb = base_in(G, c);
     if (FL & (F_ADJ | F_GRAD)) {
       float2 r = __ldcs(A.img + (size_t)b * MM + (size_t)iy * G.M + ix);
       if (FL & F_GRAD) {
-        const float2 a = gather_cell(G, c, A.vol);
+        const float2 a = inb ? gather_cell_pairs(G, c, A.vp) : gather_cell(G, c, A.vol);
         r = make_float2(fmaf(C, a.x, -r.x), fmaf(C, a.y, -r.y));
         acc = fmaf(r.x, r.x, fmaf(r.y, r.y, acc));
       }
@@ -269,7 +312,7 @@ k_fused(FusedArgs A) {
       scatter_cell_c2(G, c, make_float2(sc * r.x, sc * r.y), A.E, A.O);
     }
     if (FL & F_CURV) {
-      const float2 a = gather_cell(G, c, A.vol);
+      const float2 a = inb ? gather_cell_pairs(G, c, A.vp) : gather_cell(G, c, A.vol);
       acc = fmaf(C * C, fmaf(a.x, a.x, a.y * a.y), acc);
     }
     if (FL & F_HVP) {
@@ -285,8 +328,28 @@ k_fused(FusedArgs A) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         w8[k] = corner_in(G, c, k) ? corner_w(c, k) : 0.f;
-        bw[k] = bits_at(G, c, k, A.bits);
         wsum += w8[k];
+      }
+      if (inb) {
+#pragma unroll
+        for (int r2 = 0; r2 < 4; ++r2) {
+          const int dy = r2 & 1, dz = r2 >> 1;
+          const int y = c.y0 + dy, z = c.z0 + dz;
+          uint32_t b0 = 0u, b1 = 0u;
+          if (y < G.M && z < G.M)
+            row_words(A.seed, pbase, ((size_t)z * G.M + y) * G.M + c.x0, b0, b1);
+          bw[2 * r2] = b0;
+          bw[2 * r2 + 1] = b1;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          bw[k] = 0u;
+          if (!corner_in(G, c, k)) continue;
+          const size_t j = ((size_t)(c.z0 + (k >> 2)) * G.M + (c.y0 + ((k >> 1) & 1))) * G.M +
+                           (c.x0 + (k & 1));
+          bw[k] = (uint32_t)(probe_pair(A.seed, pbase, (uint64_t)(j >> 1)) >> (32 * (j & 1)));
+        }
       }
       const float sc = A.scale * C * C;
       float vals[8];
@@ -304,6 +367,17 @@ k_fused(FusedArgs A) {
   if (FL & (F_GRAD | F_CURV)) {
     const double t = block_sum((double)acc);
     if (threadIdx.x == 0) A.part[blockIdx.x] = t;
+  }
+}
+
+// vp[j] = (v[j], v[j+1]) with 0 past the end of each x row
+__global__ void __launch_bounds__(256)
+k_pairs(int M, const float2* __restrict__ v, float4* __restrict__ vp) {
+  const int n = M * M * M;
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
+    const float2 a = v[j];
+    const float2 b = (j % M) != M - 1 ? v[j + 1] : make_float2(0.f, 0.f);
+    vp[j] = make_float4(a.x, a.y, b.x, b.y);
   }
 }
 
@@ -363,8 +437,9 @@ int elem_grid(int n, int num_sms) {
 
 size_t fused_ws_bytes(int M) {
   const size_t n = (size_t)M * M * M;
-  // E, O (complex), P (4 real buffers), disc table, count
-  return 2 * n * sizeof(float2) + 4 * n * sizeof(float) + (size_t)M * M * sizeof(int) + 256;
+  // E, O (complex), P (4 real buffers), pair layout, disc table, count
+  return 2 * n * sizeof(float2) + 4 * n * sizeof(float) + n * sizeof(float4) +
+         (size_t)M * M * sizeof(int) + 256;
 }
 
 FusedWs fused_carve(void* base, int M) {
@@ -374,6 +449,7 @@ FusedWs fused_carve(void* base, int M) {
   w.E = reinterpret_cast<float2*>(p);   p += n * sizeof(float2);
   w.O = reinterpret_cast<float2*>(p);   p += n * sizeof(float2);
   w.P = reinterpret_cast<float*>(p);    p += 4 * n * sizeof(float);
+  w.pairs = reinterpret_cast<float4*>(p); p += n * sizeof(float4);
   w.table = reinterpret_cast<int*>(p);  p += (size_t)M * M * sizeof(int);
   w.n_px = reinterpret_cast<int*>(p);
   return w;
@@ -387,8 +463,9 @@ cudaError_t launch_disc_table(int M, int r, const FusedWs& w, cudaStream_t s) {
 
 cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float* rot,
                          const float* df, int B, float scale, const float2* vol,
-                         const float* zr, const float2* img, double* part,
-                         const uint32_t* bits, int K, int grid, cudaStream_t s) {
+                         const float4* vp, const float* zr, const float2* img, double* part,
+                         uint64_t seed, uint64_t block_host, const double* k_dev, int K,
+                         int grid, cudaStream_t s) {
   FusedArgs A;
   A.G = G;
   A.table = w.table;
@@ -403,9 +480,13 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
   A.E = w.E;
   A.O = w.O;
   A.part = part;
-  A.bits = bits;
+  A.bits = nullptr;
   A.P = w.P;
   A.K = K;
+  A.vp = vp;
+  A.seed = seed;
+  A.block_host = block_host;
+  A.k_dev = k_dev;
   switch (flags) {
     case F_ADJ: k_fused<F_ADJ><<<grid, 256, 0, s>>>(A); break;
     case F_GRAD: k_fused<F_GRAD><<<grid, 256, 0, s>>>(A); break;
@@ -415,6 +496,12 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
     case F_CURV: k_fused<F_CURV><<<grid, 256, 0, s>>>(A); break;
     default: return cudaErrorInvalidValue;
   }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pairs(int M, const float2* v, float4* vp, int num_sms, cudaStream_t s) {
+  k_pairs<<<elem_grid(M * M * M, num_sms), 256, 0, s>>>(M, v, vp);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -14,10 +14,15 @@ FusedWs fused_carve(void* base, int M);
 
 cudaError_t launch_disc_table(int M, int r, const FusedWs& w, cudaStream_t s);
 // One trilinear traversal with the given flags (partials: one per block).
+// vol: natural layout, vp: its pair layout (F_GRAD, F_CURV); probe words
+// (F_HUTCH) come from (seed, block), block = *k_dev + 1 when k_dev != NULL.
 cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float* rot,
                          const float* df, int B, float scale, const float2* vol,
-                         const float* zr, const float2* img, double* part,
-                         const uint32_t* bits, int K, int grid, cudaStream_t s);
+                         const float4* vp, const float* zr, const float2* img, double* part,
+                         uint64_t seed, uint64_t block_host, const double* k_dev, int K,
+                         int grid, cudaStream_t s);
+// vp[j] = (v[j], v[j+1]), 0 past each row's end.
+cudaError_t launch_pairs(int M, const float2* v, float4* vp, int num_sms, cudaStream_t s);
 cudaError_t launch_zero_c2(int M, const FusedWs& w, cudaStream_t s);
 cudaError_t launch_zero_r4(int M, const FusedWs& w, cudaStream_t s);
 // g = lambda v + E + shift(O) (v may be NULL); |v|^2 partials if part_vv.

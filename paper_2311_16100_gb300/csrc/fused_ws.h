@@ -9,6 +9,7 @@ struct FusedWs {
   float2* E;      // complex accumulator, natural layout [M^3]
   float2* O;      // complex accumulator shifted by one voxel along x [M^3]
   float* P;       // four real 2x2-patch accumulators [4][M^3]
+  float4* pairs;  // pair layout (v[j], v[j+1]) of the gathered volume [M^3]
   int* table;     // disc pixel table [M*M]
   int* n_px;      // number of disc pixels
 };

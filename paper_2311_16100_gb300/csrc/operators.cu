@@ -209,9 +209,12 @@ k_probe_bits(int n, uint64_t seed, uint64_t block_host, const double* __restrict
              uint32_t* __restrict__ bits) {
   // probe block: block_host, or (iterations done + 1) read from the SGD state
   const uint64_t blk = k_dev ? (uint64_t)(*k_dev) + 1ull : block_host;
-  const uint64_t base = blk * (uint64_t)n;
-  for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock)
-    bits[j] = (uint32_t)splitmix64(seed, base + (uint64_t)j);
+  const int np = n >> 1;
+  const uint64_t base = blk * (uint64_t)np;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < np; i += gridDim.x * kBlock) {
+    const uint64_t w = probe_pair(seed, base, (uint64_t)i);
+    reinterpret_cast<uint2*>(bits)[i] = make_uint2((uint32_t)w, (uint32_t)(w >> 32));
+  }
 }
 
 // D_j += scale C^2 w_j sum_l w_l Z_jl with Z_jl = (K - 2 popc((b_j ^ b_l) & mask)) / K,
