@@ -120,7 +120,8 @@ size_t cs_workspace_bytes(const cs_handle* h);
  *                     into global memory (AUTO's choice for nearest);
  *   CS_ALGO_TILED  -- volume tiles binned by image, adjoint accumulated in
  *                     shared memory and added to global memory once per tile
- *                     and work item.
+ *                     and work item (requires orthonormal rotations: the
+ *                     binning assumes |R^T r| = |r|).
  * All compute the same sums (in different orders). */
 enum { CS_ALGO_AUTO = 0, CS_ALGO_PIXEL = 1, CS_ALGO_TILED = 2, CS_ALGO_VECTOR = 3 };
 int cs_set_algo(cs_handle* h, int algo);

@@ -37,6 +37,8 @@ Workspace carve(void* base, int M, int B) {
   const size_t items = max_items_for(M, B > 0 ? B : 1);
   char* p = static_cast<char*>(base);
   Workspace w;
+  // vector-pass region first: its layout depends on M only
+  w.fw = fused_carve(p, M);                p += align256(fused_ws_bytes(M));
   w.g = reinterpret_cast<float2*>(p);      p += align256(n * sizeof(float2));
   w.d = reinterpret_cast<float2*>(p);      p += align256(n * sizeof(float2));
   w.dhat = reinterpret_cast<float*>(p);    p += align256(n * sizeof(float));
@@ -48,8 +50,7 @@ Workspace carve(void* base, int M, int B) {
   w.item_start = reinterpret_cast<int*>(p); p += align256((nt + 1) * sizeof(int));
   w.queue = reinterpret_cast<int*>(p);      p += align256(sizeof(int));
   w.part_items = reinterpret_cast<double*>(p); p += align256(items * sizeof(double));
-  w.part_items2 = reinterpret_cast<double*>(p); p += align256(items * sizeof(double));
-  w.fw = fused_carve(p, M);
+  w.part_items2 = reinterpret_cast<double*>(p);
   return w;
 }
 
@@ -171,9 +172,28 @@ int ensure_ws(cs_handle* h, int M, int B, Workspace* w) {
     }
     h->ws = p;
     h->ws_bytes = need;
+    h->acc_M = -1;
+    h->table_key = -1;
   }
   *w = carve(h->ws, M, B);
   return CS_OK;
+}
+
+// Zeroed accumulators and the disc table for the vector passes of grid M,
+// disc r (enqueued on s when the layout or the disc changed).
+cudaError_t prepare_vector(cs_handle* h, const Workspace& w, int M, int r, cudaStream_t s) {
+  if (h->acc_M != M) {
+    cudaError_t e = zero_accumulators(M, w.fw, s);
+    if (e != cudaSuccess) return e;
+    h->acc_M = M;
+  }
+  const int key = M * 1024 + r;
+  if (h->table_key != key) {
+    cudaError_t e = launch_disc_table(M, r, w.fw, s);
+    if (e != cudaSuccess) return e;
+    h->table_key = key;
+  }
+  return cudaSuccess;
 }
 
 bool use_tiles(const cs_handle* h) { return h->algo == CS_ALGO_TILED; }
@@ -348,8 +368,7 @@ int cs_backproject_adjoint(cs_handle* h, const cs_geom* g, const float* images,
     Workspace w;
     CS_TRY(ensure_ws(h, g->M, B, &w));
     const int grid = pixel_grid(h->num_sms, B, g->M);
-    CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
-    CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
     CS_CUDA(launch_fused(F_ADJ, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
                          reinterpret_cast<const float2*>(images), nullptr, 0, 0, nullptr, 1,
                          grid, s),
@@ -394,8 +413,7 @@ int cs_loss_grad(cs_handle* h, const cs_geom* g, const float* vol, const float* 
   int nvv = 0;
   if (use_vector(h, g) && B > 0) {
     const int grid = pixel_grid(h->num_sms, B, g->M);
-    CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
-    CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
     CS_CUDA(launch_pairs(g->M, reinterpret_cast<const float2*>(vol), w.fw.pairs, h->num_sms, s),
             "pairs launch");
     CS_CUDA(launch_fused(F_GRAD, G, w.fw, rot, defocus, B, scale,
@@ -457,8 +475,7 @@ int cs_hvp(cs_handle* h, const cs_geom* g, const float* z, const float* rot,
     Workspace w;
     CS_TRY(ensure_ws(h, g->M, B, &w));
     const int grid = pixel_grid(h->num_sms, B, g->M);
-    CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
-    CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
     CS_CUDA(launch_fused(F_HVP, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, z, nullptr,
                          nullptr, 0, 0, nullptr, 1, grid, s),
             "hvp launch");
@@ -501,8 +518,7 @@ int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
   cudaStream_t s = S(stream);
   if (use_vector(h, g) && B > 0) {
     const int grid = pixel_grid(h->num_sms, B, g->M);
-    CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
-    CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
     CS_CUDA(launch_fused(F_HUTCH, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
                          nullptr, nullptr, seed, probe_block, nullptr, n_probes, grid, s),
             "hutchinson launch");
@@ -619,9 +635,7 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
     const bool hutch = st->mode == CS_HUTCHINSON;
     int nvv = 0, nd = 0;
     prof_mark(h, 0, s);
-    CS_CUDA(launch_disc_table(g->M, g->r_max, w.fw, s), "disc_table launch");
-    if (hutch) CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
-    CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
     CS_CUDA(launch_pairs(g->M, reinterpret_cast<const float2*>(st->v), w.fw.pairs, h->num_sms, s),
             "pairs launch");
     prof_mark(h, CS_PH_LOSS_GRAD, s);
@@ -631,23 +645,11 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
                          st->scalars + CS_S_K, st->n_probes, grid, s),
             "fused loss_grad launch");
     prof_mark(h, CS_PH_DIRECTION, s);
-    if (hutch) {
-      CS_CUDA(launch_combine_r4(g->M, w.fw, lambda, 0.0f, nullptr, w.dest, h->num_sms, s),
-              "combine launch");
-      CS_CUDA(launch_precond_update(n, w.dest, st->D, st->D_avg, w.dhat, st->scalars,
-                                    st->beta, h->num_sms, s),
-              "precond_update launch");
-      dhat = w.dhat;
-    } else if (st->mode == CS_FIXED) {
-      CS_CUDA(launch_fixed_dhat(n, st->D, w.dhat, st->scalars, h->num_sms, s),
-              "fixed_dhat launch");
-      dhat = w.dhat;
-    }
-    CS_CUDA(launch_combine_c2(g->M, reinterpret_cast<const float2*>(st->v), lambda, w.fw, w.g,
-                              pV, &nvv, h->num_sms, s),
-            "combine launch");
-    CS_CUDA(launch_direction(n, w.g, dhat, w.d, pD, &nd, h->num_sms, s), "direction launch");
-    CS_CUDA(launch_pairs(g->M, w.d, w.fw.pairs, h->num_sms, s), "pairs launch");
+    CS_CUDA(launch_step_post(g->M, st->mode, reinterpret_cast<const float2*>(st->v), lambda,
+                             st->beta, st->scalars, w.fw, st->D, st->D_avg, pD, pV, &nd,
+                             h->num_sms, s),
+            "step_post launch");
+    nvv = nd;
     prof_mark(h, CS_PH_CURVATURE, s);
     CS_CUDA(launch_fused(F_CURV, G, w.fw, rot, defocus, B, scale, w.d, w.fw.pairs, nullptr,
                          nullptr, pQ, 0, 0, nullptr, 1, grid, s),
@@ -656,7 +658,8 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
     CS_CUDA(launch_eta(st->scalars, pL, grid, pV, nvv, pD, pD + nd, nd, pQ, grid, nullptr,
                        lambda, scale, st->c, st->max_halvings, s),
             "eta launch");
-    CS_CUDA(launch_update(n, reinterpret_cast<float2*>(st->v), w.d, st->scalars, h->num_sms, s),
+    CS_CUDA(launch_update_pairs(g->M, reinterpret_cast<float2*>(st->v), w.fw, st->scalars,
+                                h->num_sms, s),
             "update launch");
     prof_mark(h, CS_NPHASES, s);
     return CS_OK;

@@ -126,6 +126,26 @@ __device__ __forceinline__ float2 gather_cell_pairs(const Geo& G, const Cell& c,
   return make_float2(re, im);
 }
 
+__device__ __forceinline__ float corner_w(const Cell& c, int k);
+__device__ __forceinline__ bool corner_in(const Geo& G, const Cell& c, int k);
+
+// per-corner gather from the pair layout (element j's first half is v[j]);
+// used for cells whose base corner is outside the grid
+__device__ __forceinline__ float2 gather_cell_pairs_slow(const Geo& G, const Cell& c,
+                                                         const float4* __restrict__ vp) {
+  float re = 0.f, im = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (!corner_in(G, c, k)) continue;
+    const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+    const float4 a = __ldg(vp + ((size_t)(c.z0 + dz) * G.M + (c.y0 + dy)) * G.M + (c.x0 + dx));
+    const float w = corner_w(c, k);
+    re = fmaf(w, a.x, re);
+    im = fmaf(w, a.y, im);
+  }
+  return make_float2(re, im);
+}
+
 __device__ __forceinline__ float corner_w(const Cell& c, int k) {
   const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
   return (dx ? c.tx : 1.f - c.tx) * (dy ? c.ty : 1.f - c.ty) * (dz ? c.tz : 1.f - c.tz);
@@ -304,7 +324,7 @@ k_fused(FusedArgs A) {
     if (FL & (F_ADJ | F_GRAD)) {
       float2 r = __ldcs(A.img + (size_t)b * MM + (size_t)iy * G.M + ix);
       if (FL & F_GRAD) {
-        const float2 a = inb ? gather_cell_pairs(G, c, A.vp) : gather_cell(G, c, A.vol);
+        const float2 a = inb ? gather_cell_pairs(G, c, A.vp) : gather_cell_pairs_slow(G, c, A.vp);
         r = make_float2(fmaf(C, a.x, -r.x), fmaf(C, a.y, -r.y));
         acc = fmaf(r.x, r.x, fmaf(r.y, r.y, acc));
       }
@@ -312,7 +332,7 @@ k_fused(FusedArgs A) {
       scatter_cell_c2(G, c, make_float2(sc * r.x, sc * r.y), A.E, A.O);
     }
     if (FL & F_CURV) {
-      const float2 a = inb ? gather_cell_pairs(G, c, A.vp) : gather_cell(G, c, A.vol);
+      const float2 a = inb ? gather_cell_pairs(G, c, A.vp) : gather_cell_pairs_slow(G, c, A.vp);
       acc = fmaf(C * C, fmaf(a.x, a.x, a.y * a.y), acc);
     }
     if (FL & F_HVP) {
@@ -383,16 +403,18 @@ k_pairs(int M, const float2* __restrict__ v, float4* __restrict__ vp) {
 
 // g = lambda v + E + shift(O), and |v|^2 partials
 __global__ void __launch_bounds__(256)
-k_combine_c2(int M, const float2* __restrict__ v, float lambda, const float2* __restrict__ E,
-             const float2* __restrict__ O, float2* __restrict__ g, double* __restrict__ part) {
+k_combine_c2(int M, const float2* v, float lambda, float2* __restrict__ E,
+             float2* __restrict__ O, float2* g, double* __restrict__ part) {
   const int n = M * M * M;
   double accv = 0.0;
   for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
     const int x = j % M;
     float2 a = v ? v[j] : make_float2(0.f, 0.f);
     float2 r = E[j];
+    E[j] = make_float2(0.f, 0.f);
     if (x >= 1) {
       const float2 o = O[j - 1];
+      O[j - 1] = make_float2(0.f, 0.f);
       r.x += o.x;
       r.y += o.y;
     }
@@ -407,7 +429,7 @@ k_combine_c2(int M, const float2* __restrict__ v, float lambda, const float2* __
 
 // out = base + coef * add + sum over the four patch buffers
 __global__ void __launch_bounds__(256)
-k_combine_r4(int M, const float* __restrict__ P, float base, float coef,
+k_combine_r4(int M, float* __restrict__ P, float base, float coef,
              const float* __restrict__ add, float* __restrict__ out) {
   const int n = M * M * M, Mh = M / 2;
   const size_t nb = (size_t)n;
@@ -420,11 +442,103 @@ k_combine_r4(int M, const float* __restrict__ P, float base, float coef,
       for (int px = 0; px < 2; ++px) {
         const int xx = x - px, yy = y - py;
         if (xx < 0 || yy < 0) continue;
-        const float* buf = P + (size_t)(py * 2 + px) * nb;
-        s += buf[4 * (((size_t)z * Mh + (yy >> 1)) * Mh + (xx >> 1)) + 2 * (yy & 1) + (xx & 1)];
+        float* buf = P + (size_t)(py * 2 + px) * nb;
+        const size_t slot =
+            4 * (((size_t)z * Mh + (yy >> 1)) * Mh + (xx >> 1)) + 2 * (yy & 1) + (xx & 1);
+        s += buf[slot];
+        buf[slot] = 0.f;
       }
     }
     out[j] = s;
+  }
+}
+
+// Everything element-wise between the fused traversal and the curvature
+// pass of one Algorithm 1 step, per voxel j:
+//   HUTCH: D_est = lambda + patches; D_avg = ((k-1)/k) D_avg + D_est/k;
+//          D = beta D + (1-beta) D_avg; D-hat = max(|D|, alpha)
+//   FIXED: D-hat = max(|D|, alpha);  PLAIN: D-hat = 1
+//   g = lambda v + E + shift(O);  d = g / D-hat, written in pair layout;
+//   partials of |g|^2/D-hat, |d|^2 and |v|^2.
+// Consumed accumulator slots are reset to zero for the next pass.
+__global__ void __launch_bounds__(256)
+k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float beta,
+            const double* __restrict__ sc, float2* __restrict__ E, float2* __restrict__ O,
+            float* __restrict__ P, float* __restrict__ D, float* __restrict__ Davg,
+            float4* __restrict__ dp, double* __restrict__ partG, double* __restrict__ partV,
+            int nb) {
+  const int n = M * M * M, Mh = M / 2;
+  const size_t nbuf = (size_t)n;
+  const double k = sc[CS_S_K] + 1.0;
+  const float wold = (float)((k - 1.0) / k), wnew = (float)(1.0 / k);
+  const float alpha = (float)sc[CS_S_ALPHA];
+  double aG = 0.0, aD = 0.0, aV = 0.0;
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
+    const int x = j % M, y = (j / M) % M, z = j / (M * M);
+    float dh = 1.0f;
+    if (mode == CS_HUTCHINSON) {
+      float e = lambda;
+#pragma unroll
+      for (int py = 0; py < 2; ++py) {
+#pragma unroll
+        for (int px = 0; px < 2; ++px) {
+          const int xx = x - px, yy = y - py;
+          if (xx < 0 || yy < 0) continue;
+          float* buf = P + (size_t)(py * 2 + px) * nbuf;
+          const size_t slot =
+              4 * (((size_t)z * Mh + (yy >> 1)) * Mh + (xx >> 1)) + 2 * (yy & 1) + (xx & 1);
+          e += buf[slot];
+          buf[slot] = 0.f;
+        }
+      }
+      const float a = fmaf(wold, Davg[j], wnew * e);
+      const float d = fmaf(beta, D[j], (1.0f - beta) * a);
+      Davg[j] = a;
+      D[j] = d;
+      dh = fmaxf(fabsf(d), alpha);
+    } else if (mode == CS_FIXED) {
+      dh = fmaxf(fabsf(D[j]), alpha);
+    }
+    const float2 vv = v[j];
+    float2 g = E[j];
+    E[j] = make_float2(0.f, 0.f);
+    if (x >= 1) {
+      const float2 o = O[j - 1];
+      O[j - 1] = make_float2(0.f, 0.f);
+      g.x += o.x;
+      g.y += o.y;
+    }
+    g.x = fmaf(lambda, vv.x, g.x);
+    g.y = fmaf(lambda, vv.y, g.y);
+    const float inv = 1.0f / dh;
+    const float2 d = make_float2(g.x * inv, g.y * inv);
+    float2* dp2 = reinterpret_cast<float2*>(dp);
+    dp2[2 * (size_t)j] = d;
+    if (x >= 1) dp2[2 * (size_t)j - 1] = d;
+    if (x == M - 1) dp2[2 * (size_t)j + 1] = make_float2(0.f, 0.f);
+    aG += (double)(fmaf(g.x, g.x, g.y * g.y) * inv);
+    aD += (double)fmaf(d.x, d.x, d.y * d.y);
+    aV += (double)fmaf(vv.x, vv.x, vv.y * vv.y);
+  }
+  const double tG = block_sum(aG);
+  const double tD = block_sum(aD);
+  const double tV = block_sum(aV);
+  if (threadIdx.x == 0) {
+    partG[blockIdx.x] = tG;
+    partG[nb + blockIdx.x] = tD;
+    partV[blockIdx.x] = tV;
+  }
+}
+
+// v -= eta d, with d read from its pair layout
+__global__ void __launch_bounds__(256)
+k_update_pairs(int n, float2* __restrict__ v, const float4* __restrict__ dp,
+               const double* __restrict__ sc) {
+  const float eta = (float)sc[CS_S_ETA];
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
+    const float4 d = dp[j];
+    const float2 a = v[j];
+    v[j] = make_float2(fmaf(-eta, d.x, a.x), fmaf(-eta, d.y, a.y));
   }
 }
 
@@ -500,10 +614,37 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
   return cudaGetLastError();
 }
 
+cudaError_t launch_step_post(int M, int mode, const float2* v, float lambda, float beta,
+                             const double* scalars, const FusedWs& w, float* D, float* Davg,
+                             double* partG, double* partV, int* nb, int num_sms,
+                             cudaStream_t s) {
+  const int g = elem_grid(M * M * M, num_sms);
+  *nb = g;
+  k_step_post<<<g, 256, 0, s>>>(M, mode, v, lambda, beta, scalars, w.E, w.O, w.P, D, Davg,
+                                w.pairs, partG, partV, g);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_pairs(int M, float2* v, const FusedWs& w, const double* scalars,
+                                int num_sms, cudaStream_t s) {
+  const int n = M * M * M;
+  k_update_pairs<<<elem_grid(n, num_sms), 256, 0, s>>>(n, v, w.pairs, scalars);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pairs(int M, const float2* v, float4* vp, int num_sms, cudaStream_t s) {
   k_pairs<<<elem_grid(M * M * M, num_sms), 256, 0, s>>>(M, v, vp);
   count_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t zero_accumulators(int M, const FusedWs& w, cudaStream_t s) {
+  const size_t n = (size_t)M * M * M;
+  cudaError_t e = cudaMemsetAsync(w.E, 0, 2 * n * sizeof(float2), s);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(w.P, 0, 4 * n * sizeof(float), s);
 }
 
 cudaError_t launch_zero_c2(int M, const FusedWs& w, cudaStream_t s) {

@@ -25,6 +25,7 @@ def h(request):
     from paper_2311_16100_gb300.ops import Handle
     hd = Handle(0)
     hd.set_algo(request.param)
+    hd.algo_name = request.param
     yield hd
     hd.close()
 
@@ -243,6 +244,26 @@ def test_rel_err(h):
     e = float(h.rel_err(c.gpu_geometry(), torch.from_numpy(b).cuda(), torch.from_numpy(a).cuda()))
     # FP32 differences against FP64 ones: a few float ulps of relative error
     assert abs(e - O.rel_err(b, a, 32, 15)) <= 2e-5 * e
+
+
+def test_cells_outside_the_grid(h, request):
+    """A scaled rotation sends outer pixels' cells past the grid edge: those
+    corners contribute nothing (both sides), exercising the guarded paths."""
+    if h.algo_name == "tiled":
+        pytest.skip("the tiled algorithm bins with orthonormal rotations")
+    c = Case(32, 9, interp="trilinear", ctf=True, seed=41)
+    R = (1.08 * c.R).astype(np.float32)
+    g = c.to_gpu()
+    Rg = torch.from_numpy(R).cuda()
+    geom = c.gpu_geometry()
+    y = cpu(h.slice_project(geom, g["vol"], Rg, g["df"]))
+    assert rel_l2(y, O.slice_project(c.vol, R, c.df, **c.geo())) <= TOL_SLICE
+    loss, grad = h.loss_grad(geom, g["vol"], g["images"], Rg, g["df"], 0.1, 2.0)
+    f, gw = O.loss_grad(c.vol, c.images, R, c.df, lam=0.1, scale=2.0, **c.geo())
+    assert rel_l2(cpu(grad), gw) <= TOL_GRAD and abs(float(loss) - f) <= 1e-6 * abs(f)
+    d = cpu(h.hutchinson_diag(geom, Rg, g["df"], 0.1, 2.0, n_probes=8, seed=3, probe_block=2))
+    dw = O.hutchinson_diag(R, c.df, lam=0.1, scale=2.0, n_probes=8, seed=3, block=2, **c.geo())
+    assert rel_l2(d, dw) <= TOL_GRAD
 
 
 # ------------------------------------------------------------ validation
