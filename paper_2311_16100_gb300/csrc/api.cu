@@ -172,21 +172,15 @@ int ensure_ws(cs_handle* h, int M, int B, Workspace* w) {
     }
     h->ws = p;
     h->ws_bytes = need;
-    h->acc_M = -1;
     h->table_key = -1;
   }
   *w = carve(h->ws, M, B);
   return CS_OK;
 }
 
-// Zeroed accumulators and the disc table for the vector passes of grid M,
-// disc r (enqueued on s when the layout or the disc changed).
+// Disc pixel table of the vector passes for grid M, disc r (rebuilt on the
+// stream when the grid, the disc or the workspace changed).
 cudaError_t prepare_vector(cs_handle* h, const Workspace& w, int M, int r, cudaStream_t s) {
-  if (h->acc_M != M) {
-    cudaError_t e = zero_accumulators(M, w.fw, s);
-    if (e != cudaSuccess) return e;
-    h->acc_M = M;
-  }
   const int key = M * 1024 + r;
   if (h->table_key != key) {
     cudaError_t e = launch_disc_table(M, r, w.fw, s);
@@ -369,6 +363,7 @@ int cs_backproject_adjoint(cs_handle* h, const cs_geom* g, const float* images,
     CS_TRY(ensure_ws(h, g->M, B, &w));
     const int grid = pixel_grid(h->num_sms, B, g->M);
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
+    CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_ADJ, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
                          reinterpret_cast<const float2*>(images), nullptr, 0, 0, nullptr, 1,
                          grid, s),
@@ -414,6 +409,7 @@ int cs_loss_grad(cs_handle* h, const cs_geom* g, const float* vol, const float* 
   if (use_vector(h, g) && B > 0) {
     const int grid = pixel_grid(h->num_sms, B, g->M);
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
+    CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_pairs(g->M, reinterpret_cast<const float2*>(vol), w.fw.pairs, h->num_sms, s),
             "pairs launch");
     CS_CUDA(launch_fused(F_GRAD, G, w.fw, rot, defocus, B, scale,
@@ -476,6 +472,7 @@ int cs_hvp(cs_handle* h, const cs_geom* g, const float* z, const float* rot,
     CS_TRY(ensure_ws(h, g->M, B, &w));
     const int grid = pixel_grid(h->num_sms, B, g->M);
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
+    CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_HVP, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, z, nullptr,
                          nullptr, 0, 0, nullptr, 1, grid, s),
             "hvp launch");
@@ -519,6 +516,7 @@ int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
   if (use_vector(h, g) && B > 0) {
     const int grid = pixel_grid(h->num_sms, B, g->M);
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
+    CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_HUTCH, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
                          nullptr, nullptr, seed, probe_block, nullptr, n_probes, grid, s),
             "hutchinson launch");
@@ -636,6 +634,8 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
     int nvv = 0, nd = 0;
     prof_mark(h, 0, s);
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
+    if (hutch) CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_pairs(g->M, reinterpret_cast<const float2*>(st->v), w.fw.pairs, h->num_sms, s),
             "pairs launch");
     prof_mark(h, CS_PH_LOSS_GRAD, s);

@@ -411,10 +411,8 @@ k_combine_c2(int M, const float2* v, float lambda, float2* __restrict__ E,
     const int x = j % M;
     float2 a = v ? v[j] : make_float2(0.f, 0.f);
     float2 r = E[j];
-    E[j] = make_float2(0.f, 0.f);
     if (x >= 1) {
       const float2 o = O[j - 1];
-      O[j - 1] = make_float2(0.f, 0.f);
       r.x += o.x;
       r.y += o.y;
     }
@@ -446,7 +444,6 @@ k_combine_r4(int M, float* __restrict__ P, float base, float coef,
         const size_t slot =
             4 * (((size_t)z * Mh + (yy >> 1)) * Mh + (xx >> 1)) + 2 * (yy & 1) + (xx & 1);
         s += buf[slot];
-        buf[slot] = 0.f;
       }
     }
     out[j] = s;
@@ -460,7 +457,6 @@ k_combine_r4(int M, float* __restrict__ P, float base, float coef,
 //   FIXED: D-hat = max(|D|, alpha);  PLAIN: D-hat = 1
 //   g = lambda v + E + shift(O);  d = g / D-hat, written in pair layout;
 //   partials of |g|^2/D-hat, |d|^2 and |v|^2.
-// Consumed accumulator slots are reset to zero for the next pass.
 __global__ void __launch_bounds__(256)
 k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float beta,
             const double* __restrict__ sc, float2* __restrict__ E, float2* __restrict__ O,
@@ -488,7 +484,6 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
           const size_t slot =
               4 * (((size_t)z * Mh + (yy >> 1)) * Mh + (xx >> 1)) + 2 * (yy & 1) + (xx & 1);
           e += buf[slot];
-          buf[slot] = 0.f;
         }
       }
       const float a = fmaf(wold, Davg[j], wnew * e);
@@ -501,10 +496,8 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
     }
     const float2 vv = v[j];
     float2 g = E[j];
-    E[j] = make_float2(0.f, 0.f);
     if (x >= 1) {
       const float2 o = O[j - 1];
-      O[j - 1] = make_float2(0.f, 0.f);
       g.x += o.x;
       g.y += o.y;
     }
@@ -542,9 +535,10 @@ k_update_pairs(int n, float2* __restrict__ v, const float4* __restrict__ dp,
   }
 }
 
+// element-wise kernels: up to 8 blocks of 256 threads per SM (full occupancy)
 int elem_grid(int n, int num_sms) {
   int g = (n + 255) / 256;
-  return g < num_sms * 4 ? (g > 0 ? g : 1) : num_sms * 4;
+  return g < num_sms * 8 ? (g > 0 ? g : 1) : num_sms * 8;
 }
 
 }  // namespace
@@ -638,13 +632,6 @@ cudaError_t launch_pairs(int M, const float2* v, float4* vp, int num_sms, cudaSt
   k_pairs<<<elem_grid(M * M * M, num_sms), 256, 0, s>>>(M, v, vp);
   count_launches(1);
   return cudaGetLastError();
-}
-
-cudaError_t zero_accumulators(int M, const FusedWs& w, cudaStream_t s) {
-  const size_t n = (size_t)M * M * M;
-  cudaError_t e = cudaMemsetAsync(w.E, 0, 2 * n * sizeof(float2), s);
-  if (e != cudaSuccess) return e;
-  return cudaMemsetAsync(w.P, 0, 4 * n * sizeof(float), s);
 }
 
 cudaError_t launch_zero_c2(int M, const FusedWs& w, cudaStream_t s) {

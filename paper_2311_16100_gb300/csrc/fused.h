@@ -21,10 +21,7 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
                          const float4* vp, const float* zr, const float2* img, double* part,
                          uint64_t seed, uint64_t block_host, const double* k_dev, int K,
                          int grid, cudaStream_t s);
-// The accumulators E, O and P are kept zero between passes: every combine
-// (and the step's post pass) resets the slots it consumes.  zero_accumulators
-// establishes the invariant when the workspace layout changes.
-cudaError_t zero_accumulators(int M, const FusedWs& w, cudaStream_t s);
+
 // Element-wise work of one step between the fused traversal and the
 // curvature pass (see fused.cu); partG holds the |g|^2/D-hat partials then
 // the |d|^2 partials (*nb each), partV the |v|^2 partials.

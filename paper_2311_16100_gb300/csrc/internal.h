@@ -22,7 +22,6 @@ struct cs_handle {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int algo = 0;            // CS_ALGO_*
-  int acc_M = -1;          // grid side of the zeroed vector-pass accumulators
   int table_key = -1;      // (M, r_max) of the cached disc pixel table
   // profiler: CS_NPHASES + 1 boundary events per timed step
   bool prof = false;

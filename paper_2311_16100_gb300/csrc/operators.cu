@@ -305,7 +305,7 @@ k_curvature(Geo G, const float2* __restrict__ d, const float* __restrict__ rot,
 
 int elem_grid(int n, int num_sms) {
   int g = (n + kBlock - 1) / kBlock;
-  return g < num_sms * 4 ? (g > 0 ? g : 1) : num_sms * 4;
+  return g < num_sms * 8 ? (g > 0 ? g : 1) : num_sms * 8;
 }
 
 }  // namespace

@@ -11,7 +11,7 @@ namespace {
 
 int elem_grid(int n, int num_sms) {
   int g = (n + kBlock - 1) / kBlock;
-  return g < num_sms * 4 ? (g > 0 ? g : 1) : num_sms * 4;
+  return g < num_sms * 8 ? (g > 0 ? g : 1) : num_sms * 8;
 }
 
 __global__ void k_quat_to_rot(const float* __restrict__ q, int B, float* __restrict__ R) {
