@@ -270,6 +270,12 @@ int cs_profile_read(cs_handle* h, double* ms, int* counts);
 /* Kernels launched by this library in this process so far (all handles). */
 uint64_t cs_kernel_launches(void);
 
+/* Calibration: the rate, in G operations/s, at which this device executes
+ * 16-byte floating-point reductions into global memory (random addresses in
+ * a 16 MiB L2-resident buffer) -- the ceiling of the adjoint passes.
+ * Synchronous; allocates and frees a 16 MiB buffer. */
+int cs_measure_reduction_rate(cs_handle* h, double* gops);
+
 /* Relative error over the ball |k| <= r_max:
  *   |v - v_ref| / |v_ref| -> *out (device double). */
 int cs_rel_err(cs_handle* h, const cs_geom* g, const float* v, const float* v_ref,

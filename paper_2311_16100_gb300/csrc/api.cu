@@ -787,6 +787,23 @@ int cs_profile_read(cs_handle* h, double* ms, int* counts) {
 
 uint64_t cs_kernel_launches(void) { return g_launches.load(); }
 
+int cs_measure_reduction_rate(cs_handle* h, double* gops) {
+  if (!h) return CS_ERR_ARG;
+  if (!gops) return fail(h, CS_ERR_ARG, "gops is NULL");
+  CS_SCOPE(h);
+  const size_t bytes = (size_t)16 << 20;
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, CS_ERR_ALLOC, "calibration buffer: %s", cudaGetErrorString(e));
+  }
+  e = measure_red_rate(buf, bytes, h->num_sms, nullptr, gops);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(h, e, "reduction-rate calibration");
+  return CS_OK;
+}
+
 int cs_rel_err(cs_handle* h, const cs_geom* g, const float* v, const float* v_ref,
                double* out, void* stream) {
   if (!h) return CS_ERR_ARG;

@@ -371,16 +371,24 @@ k_fused(FusedArgs A) {
           bw[k] = (uint32_t)(probe_pair(A.seed, pbase, (uint64_t)(j >> 1)) >> (32 * (j & 1)));
         }
       }
+      // S_j = sum_l w_l popc(b_j ^ b_l): each of the 28 unordered pairs is
+      // counted once and feeds both of its corners
       const float sc = A.scale * C * C;
-      float vals[8];
+      float S[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) S[j] = 0.f;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        float pc = 0.f;
 #pragma unroll
-        for (int l = 0; l < 8; ++l)
-          if (l != j) pc = fmaf(w8[l], (float)__popc((bw[j] ^ bw[l]) & pmask), pc);
-        vals[j] = sc * w8[j] * fmaf(-2.0f * invK, pc, wsum);
+        for (int l = j + 1; l < 8; ++l) {
+          const float pc = (float)__popc((bw[j] ^ bw[l]) & pmask);
+          S[j] = fmaf(w8[l], pc, S[j]);
+          S[l] = fmaf(w8[j], pc, S[l]);
+        }
       }
+      float vals[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) vals[j] = sc * w8[j] * fmaf(-2.0f * invK, S[j], wsum);
       scatter_cell_r4(G, c, vals, A.P);
     }
   }

@@ -132,6 +132,9 @@ cudaError_t launch_eta(double* scalars, const double* part_loss, int n_loss,
                        int max_halvings, cudaStream_t s);
 cudaError_t launch_update(int n, float2* v, const float2* d, const double* scalars,
                           int num_sms, cudaStream_t s);
+// Rate of 16-byte global reductions (G ops/s) measured on a scratch buffer.
+cudaError_t measure_red_rate(void* scratch, size_t bytes, int num_sms, cudaStream_t s,
+                             double* gops);
 cudaError_t launch_rel_err(const Geo& G, const float2* v, const float2* vref,
                            double* part, double* out, int num_sms, cudaStream_t s);
 

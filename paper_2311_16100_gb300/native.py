@@ -67,6 +67,7 @@ SIGNATURES = {
     "cs_profile_enable": (c_int, [P, c_int, c_int]),
     "cs_profile_read": (c_int, [P, POINTER(c_double), POINTER(c_int)]),
     "cs_kernel_launches": (c_uint64, []),
+    "cs_measure_reduction_rate": (c_int, [P, POINTER(c_double)]),
 }
 
 _lib = None

@@ -241,6 +241,13 @@ class Handle:
         self._check("cs_profile_read", self.lib.cs_profile_read(self.h, ms, cnt))
         return {n: (ms[i], cnt[i]) for i, n in enumerate(N.PHASE_NAMES)}
 
+    def measure_reduction_rate(self) -> float:
+        """G 16-byte reductions per second into L2-resident memory (synchronous)."""
+        g = ctypes.c_double()
+        self._check("cs_measure_reduction_rate",
+                    self.lib.cs_measure_reduction_rate(self.h, ctypes.byref(g)))
+        return g.value
+
     def rel_err(self, geom: Geometry, v, v_ref, out=None, stream=None):
         if out is None:
             out = torch.empty((), dtype=torch.float64, device=v.device)
