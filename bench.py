@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--config", choices=sorted(CONFIGS), default="m128")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample", type=int, default=48,
+    p.add_argument("--cpu-sample", type=int, default=128,
                    help="images in the oracle's timed sample")
     p.add_argument("--algo", choices=["auto", "vector", "tiled", "pixel"], default="auto",
                    help="scatter algorithm of the adjoint-type passes")
@@ -76,12 +76,21 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_source_hash():
+# sources that define the kernel of each timed phase (for the validity of
+# recorded ncu counters)
+KERNEL_SOURCES = {
+    "loss_grad": ["fused.cu", "fused.h", "fused_ws.h", "device.cuh"],
+    "curvature": ["fused.cu", "fused.h", "fused_ws.h", "device.cuh"],
+}
+
+
+def kernel_source_hash(kernel="loss_grad"):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2311_16100_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    files = KERNEL_SOURCES.get(kernel) or sorted(
+        f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -94,7 +103,7 @@ def recorded_traffic(config, kernel):
     except (OSError, ValueError):
         return None
     e = rec.get(f"{kernel}:{config}")
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
