@@ -178,6 +178,28 @@ int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
                        int n_probes, uint64_t seed, uint64_t probe_block,
                        float* diag_out, void* stream);
 
+/* Hutchinson's diagonal estimate without device allocation.  The paper has
+ * no counterpart: this is a deployment variant of cs_hutchinson_diag for
+ * callers that cannot allocate device memory when they need the estimate
+ * (inside another application's stream capture, under a caching allocator
+ * that must not be bypassed, or after a start-up-only allocation phase).
+ * Same arguments and result as cs_hutchinson_diag (per-pixel algorithm), on
+ * the current CUDA device, without a handle.  Its only scratch, one probe
+ * word per voxel, is a fixed 8 MiB device array inside the library that
+ * every GPU loading the library holds until exit, so M is limited to 128:
+ * larger grids return CS_ERR_SHAPE and enqueue nothing.  Other argument
+ * errors return CS_ERR_ARG / CS_ERR_SHAPE as in cs_hutchinson_diag (no
+ * message is recorded: there is no handle).  No cudaMalloc or cudaFree is
+ * made.  The first call on a device looks up the array's device address
+ * (make it before any stream capture).  All calls share the array, so calls
+ * that overlap on the GPU (different streams, or devices sharing nothing but
+ * the process) race on it: serialise them on one stream per device. */
+int cs_hutchinson_diag_noalloc(const cs_geom* g, const float* rot,
+                               const float* defocus, int B, float lambda,
+                               float scale, int n_probes, uint64_t seed,
+                               uint64_t probe_block, float* diag_out,
+                               void* stream);
+
 /* Exact diagonal of the mini-batch Hessian (Eq. hessian; under nearest
  * interpolation without CTF it is |Omega_j| + lambda, Eq. H diag):
  *   diag_out_j = lambda + scale sum_i sum_p C_ip^2 w_pj^2,

@@ -59,6 +59,8 @@ SIGNATURES = {
     "cs_hvp": (c_int, [P, G, P, P, P, c_int, c_float, c_float, P, P]),
     "cs_hutchinson_diag": (c_int, [P, G, P, P, c_int, c_float, c_float, c_int, c_uint64,
                                    c_uint64, P, P]),
+    "cs_hutchinson_diag_noalloc": (c_int, [G, P, P, c_int, c_float, c_float, c_int, c_uint64,
+                                           c_uint64, P, P]),
     "cs_exact_diag": (c_int, [P, G, P, P, c_int, c_float, c_float, P, P, P, P]),
     "cs_threshold_alpha": (c_int, [P, G, P, c_int, c_double, c_double, P, P]),
     "cs_precond_sgd_step": (c_int, [P, G, POINTER(CsSgdState), P, P, P, c_int, c_float,
