@@ -298,6 +298,63 @@ uint64_t cs_kernel_launches(void);
  * Synchronous; allocates and frees a 16 MiB buffer. */
 int cs_measure_reduction_rate(cs_handle* h, double* gops);
 
+/* ------------------------------------------------------------------------
+ * Several volumes in one launch, CUDA graphs and launch-shape autotuning.
+ * None of this is in the paper: it batches independent refinements (for
+ * example volumes of different box sizes) so that the dominant traversal of
+ * all of them is one kernel launch, and makes a whole step replayable as a
+ * CUDA graph.
+ * ------------------------------------------------------------------------ */
+#define CS_MAX_PROBLEMS 8
+
+/* One refinement problem of a multi-volume step.  Its images, quaternions
+ * and defocus values for all n_batches batches of B images stay in device
+ * memory; step k (state.scalars[CS_S_K] = iterations done) uses batch
+ * (k mod n_batches), chosen on the device, so a captured step replays over
+ * the batches without host involvement. */
+typedef struct {
+  cs_geom geom;          /* trilinear interpolation only */
+  cs_sgd_state state;    /* as for cs_precond_sgd_step */
+  const float* images;   /* complex64 [n_batches*B][M][M] */
+  const float* quat;     /* float [n_batches*B][4] unit quaternions (w,x,y,z) */
+  const float* defocus;  /* float [n_batches*B] (NULL if the CTF is off) */
+  int B;                 /* images per step (>= 1) */
+  int n_batches;         /* >= 1 */
+  float lambda;
+  float scale;           /* N/|I| of this problem */
+} cs_problem;
+
+/* One Algorithm 1 iteration for each of n (1..CS_MAX_PROBLEMS) problems:
+ * pose conversion of the selected batch, then the same computation as
+ * cs_precond_sgd_step per problem, with the fused loss / gradient /
+ * Hutchinson traversal of all problems in one kernel launch and the Armijo
+ * curvature traversal in another.  All problems must use the same
+ * cs_sgd_mode.  Stream ordered; grows the handle's multi-volume workspace on
+ * first use (synchronous then). */
+int cs_multi_step(cs_handle* h, const cs_problem* probs, int n, void* stream);
+
+typedef struct cs_graph cs_graph;
+/* Captures one cs_multi_step of these problems into an executable CUDA
+ * graph (workspace and pixel tables prepared first, synchronously).  Each
+ * cs_graph_launch replays one step: batches advance on the device.  The
+ * graph keeps the problems' device pointers and the handle's workspace; it
+ * is invalid once the handle is destroyed, and cs_graph_launch returns
+ * CS_ERR_ARG if the handle's multi-volume workspace was reallocated since
+ * the capture. */
+int cs_multi_step_graph(cs_handle* h, const cs_problem* probs, int n, cs_graph** graph);
+int cs_graph_launch(cs_graph* graph, void* stream);
+int cs_graph_destroy(cs_graph* graph);
+
+/* Launch shape of the trilinear traversal kernels: threads per block
+ * (128 or 256) and blocks per SM (1..32 for 256 threads, 1..64 for 128).
+ * Default 256 x 8. */
+int cs_set_launch_shape(cs_handle* h, int block_threads, int blocks_per_sm);
+/* Autotuner: times the fused traversal of these problems (without changing
+ * their state) for a set of launch shapes, keeps the fastest on the handle
+ * and returns it.  Synchronous. */
+int cs_autotune(cs_handle* h, const cs_problem* probs, int n, int* block_threads,
+                int* blocks_per_sm);
+
 /* Relative error over the ball |k| <= r_max:
  *   |v - v_ref| / |v_ref| -> *out (device double). */
 int cs_rel_err(cs_handle* h, const cs_geom* g, const float* v, const float* v_ref,

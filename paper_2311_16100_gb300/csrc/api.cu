@@ -3,6 +3,7 @@
 // kernels into the calls of the paper's problem statement.
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <new>
 
@@ -191,6 +192,14 @@ cudaError_t prepare_vector(cs_handle* h, const Workspace& w, int M, int r, cudaS
 }
 
 bool use_tiles(const cs_handle* h) { return h->algo == CS_ALGO_TILED; }
+
+// grid of the single-problem trilinear traversals (launch shape of the handle)
+int vec_grid(const cs_handle* h, int B, int M) {
+  const long items = (long)B * (((long)M * M + h->block - 1) / h->block);
+  const long cap = (long)h->num_sms * h->blocks_per_sm;
+  const long g = items < cap ? items : cap;
+  return (int)(g > 0 ? (g < kPartRegion ? g : kPartRegion) : 1);
+}
 // Vector-reduction passes: the default for trilinear interpolation.
 bool use_vector(const cs_handle* h, const cs_geom* g) {
   return (h->algo == CS_ALGO_AUTO || h->algo == CS_ALGO_VECTOR) && g->interp == CS_TRILINEAR;
@@ -361,12 +370,12 @@ int cs_backproject_adjoint(cs_handle* h, const cs_geom* g, const float* images,
   if (use_vector(h, g)) {
     Workspace w;
     CS_TRY(ensure_ws(h, g->M, B, &w));
-    const int grid = pixel_grid(h->num_sms, B, g->M);
+    const int grid = vec_grid(h, B, g->M);
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
     CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_ADJ, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
                          reinterpret_cast<const float2*>(images), nullptr, 0, 0, nullptr, 1,
-                         grid, s),
+                         grid, s, h->block),
             "adjoint launch");
     CS_CUDA(launch_combine_c2(g->M, reinterpret_cast<const float2*>(vol_accum), 1.0f, w.fw,
                               reinterpret_cast<float2*>(vol_accum), nullptr, nullptr,
@@ -407,7 +416,7 @@ int cs_loss_grad(cs_handle* h, const cs_geom* g, const float* vol, const float* 
   cudaStream_t s = S(stream);
   int nvv = 0;
   if (use_vector(h, g) && B > 0) {
-    const int grid = pixel_grid(h->num_sms, B, g->M);
+    const int grid = vec_grid(h, B, g->M);
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
     CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_pairs(g->M, reinterpret_cast<const float2*>(vol), w.fw.pairs, h->num_sms, s),
@@ -415,7 +424,7 @@ int cs_loss_grad(cs_handle* h, const cs_geom* g, const float* vol, const float* 
     CS_CUDA(launch_fused(F_GRAD, G, w.fw, rot, defocus, B, scale,
                          reinterpret_cast<const float2*>(vol), w.fw.pairs, nullptr,
                          reinterpret_cast<const float2*>(images), w.part, 0, 0, nullptr, 1,
-                         grid, s),
+                         grid, s, h->block),
             "loss_grad launch");
     CS_CUDA(launch_combine_c2(g->M, reinterpret_cast<const float2*>(vol), lambda, w.fw,
                               reinterpret_cast<float2*>(grad), w.part + kPartRegion, &nvv,
@@ -470,11 +479,11 @@ int cs_hvp(cs_handle* h, const cs_geom* g, const float* z, const float* rot,
   if (use_vector(h, g) && B > 0) {
     Workspace w;
     CS_TRY(ensure_ws(h, g->M, B, &w));
-    const int grid = pixel_grid(h->num_sms, B, g->M);
+    const int grid = vec_grid(h, B, g->M);
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
     CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_HVP, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, z, nullptr,
-                         nullptr, 0, 0, nullptr, 1, grid, s),
+                         nullptr, 0, 0, nullptr, 1, grid, s, h->block),
             "hvp launch");
     CS_CUDA(launch_combine_r4(g->M, w.fw, 0.0f, lambda, z, Hz, h->num_sms, s), "combine launch");
     return CS_OK;
@@ -514,11 +523,11 @@ int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
   Geo G = make_geo(*g);
   cudaStream_t s = S(stream);
   if (use_vector(h, g) && B > 0) {
-    const int grid = pixel_grid(h->num_sms, B, g->M);
+    const int grid = vec_grid(h, B, g->M);
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
     CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_HUTCH, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
-                         nullptr, nullptr, seed, probe_block, nullptr, n_probes, grid, s),
+                         nullptr, nullptr, seed, probe_block, nullptr, n_probes, grid, s, h->block),
             "hutchinson launch");
     CS_CUDA(launch_combine_r4(g->M, w.fw, lambda, 0.0f, nullptr, diag_out, h->num_sms, s),
             "combine launch");
@@ -631,6 +640,7 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
   if (use_vector(h, g) && B > 0) {
     // one traversal computes loss, gradient and (Hutchinson) the estimate
     const bool hutch = st->mode == CS_HUTCHINSON;
+    const int vgrid = vec_grid(h, B, g->M);
     int nvv = 0, nd = 0;
     prof_mark(h, 0, s);
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
@@ -642,7 +652,7 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
     CS_CUDA(launch_fused(hutch ? (F_GRAD | F_HUTCH) : F_GRAD, G, w.fw, rot, defocus, B, scale,
                          reinterpret_cast<const float2*>(st->v), w.fw.pairs, nullptr,
                          reinterpret_cast<const float2*>(images), pL, st->seed, 0,
-                         st->scalars + CS_S_K, st->n_probes, grid, s),
+                         st->scalars + CS_S_K, st->n_probes, vgrid, s, h->block),
             "fused loss_grad launch");
     prof_mark(h, CS_PH_DIRECTION, s);
     CS_CUDA(launch_step_post(g->M, st->mode, reinterpret_cast<const float2*>(st->v), lambda,
@@ -652,10 +662,10 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
     nvv = nd;
     prof_mark(h, CS_PH_CURVATURE, s);
     CS_CUDA(launch_fused(F_CURV, G, w.fw, rot, defocus, B, scale, w.d, w.fw.pairs, nullptr,
-                         nullptr, pQ, 0, 0, nullptr, 1, grid, s),
+                         nullptr, pQ, 0, 0, nullptr, 1, vgrid, s, h->block),
             "curvature launch");
     prof_mark(h, CS_PH_UPDATE, s);
-    CS_CUDA(launch_eta(st->scalars, pL, grid, pV, nvv, pD, pD + nd, nd, pQ, grid, nullptr,
+    CS_CUDA(launch_eta(st->scalars, pL, vgrid, pV, nvv, pD, pD + nd, nd, pQ, vgrid, nullptr,
                        lambda, scale, st->c, st->max_halvings, s),
             "eta launch");
     CS_CUDA(launch_update_pairs(g->M, reinterpret_cast<float2*>(st->v), w.fw, st->scalars,
@@ -801,6 +811,382 @@ int cs_measure_reduction_rate(cs_handle* h, double* gops) {
   e = measure_red_rate(buf, bytes, h->num_sms, nullptr, gops);
   cudaFree(buf);
   if (e != cudaSuccess) return cuda_fail(h, e, "reduction-rate calibration");
+  return CS_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------- multi-volume
+
+namespace {
+
+constexpr int kMultiParts = 4 * kPartRegion;   // partial slots per problem
+
+struct ProblemWs {
+  FusedWs fw;
+  float* rot;       // [B][9]
+  double* part;     // kMultiParts doubles: loss | |v|^2 | (G, |d|^2) | Q
+};
+
+size_t problem_ws_bytes(int M, int B) {
+  return align256(fused_ws_bytes(M)) + align256((size_t)B * 9 * sizeof(float)) +
+         align256((size_t)kMultiParts * sizeof(double));
+}
+
+int check_problems(cs_handle* h, const cs_problem* P, int n) {
+  if (!P) return fail(h, CS_ERR_ARG, "problems pointer is NULL");
+  if (n < 1 || n > CS_MAX_PROBLEMS)
+    return fail(h, CS_ERR_SHAPE, "n=%d problems must be in [1, %d]", n, CS_MAX_PROBLEMS);
+  for (int p = 0; p < n; ++p) {
+    const cs_problem& q = P[p];
+    CS_TRY(check_geom(h, &q.geom));
+    if (q.geom.interp != CS_TRILINEAR)
+      return fail(h, CS_ERR_ARG, "problem %d: the multi-volume step needs trilinear interpolation", p);
+    if (q.B < 1 || q.n_batches < 1)
+      return fail(h, CS_ERR_SHAPE, "problem %d: B=%d and n_batches=%d must be >= 1", p, q.B, q.n_batches);
+    const long nch = ((long)q.geom.M * q.geom.M + 127) / 128;
+    if ((long)q.B * nch > 0x7fffffffL || (long)q.B * q.n_batches > 0x7fffffffL)
+      return fail(h, CS_ERR_SHAPE, "problem %d: batch too large", p);
+    if (!q.images || !q.quat || (q.geom.ctf.enabled && !q.defocus))
+      return fail(h, CS_ERR_ARG, "problem %d: images, quat or defocus is NULL", p);
+    const cs_sgd_state& st = q.state;
+    if (!st.v || !st.scalars) return fail(h, CS_ERR_ARG, "problem %d: state.v or scalars is NULL", p);
+    if (st.mode != P[0].state.mode)
+      return fail(h, CS_ERR_ARG, "problem %d: all problems must share the SGD mode", p);
+    if (st.mode != CS_PLAIN && st.mode != CS_HUTCHINSON && st.mode != CS_FIXED)
+      return fail(h, CS_ERR_ARG, "problem %d: mode=%d is not a cs_sgd_mode", p, st.mode);
+    if (st.mode != CS_PLAIN && !st.D) return fail(h, CS_ERR_ARG, "problem %d: state.D is NULL", p);
+    if (st.mode == CS_HUTCHINSON &&
+        (!st.D_avg || st.n_probes < 1 || st.n_probes > 32 || !(st.beta > 0.f && st.beta < 1.f)))
+      return fail(h, CS_ERR_ARG, "problem %d: Hutchinson state (D_avg, n_probes, beta) invalid", p);
+    if (!(st.c > 0.f && st.c < 1.f) || st.max_halvings < 0)
+      return fail(h, CS_ERR_ARG, "problem %d: c or max_halvings invalid", p);
+    if (!is_finite(q.lambda) || !is_finite(q.scale))
+      return fail(h, CS_ERR_ARG, "problem %d: lambda/scale not finite", p);
+  }
+  return CS_OK;
+}
+
+int ensure_mws(cs_handle* h, const cs_problem* P, int n, ProblemWs* W) {
+  size_t need = 0;
+  for (int p = 0; p < n; ++p) need += problem_ws_bytes(P[p].geom.M, P[p].B);
+  if (h->mws_bytes < need) {
+    if (h->mws) {
+      cudaError_t e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return cuda_fail(h, e, "synchronise before workspace growth");
+      cudaFree(h->mws);
+      h->mws = nullptr;
+      h->mws_bytes = 0;
+    }
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, CS_ERR_ALLOC, "multi-volume workspace of %zu bytes: %s", need,
+                  cudaGetErrorString(e));
+    }
+    h->mws = ptr;
+    h->mws_bytes = need;
+    ++h->mws_generation;
+    for (int i = 0; i < 8; ++i) h->mtable_key[i] = -1;
+  }
+  char* c = static_cast<char*>(h->mws);
+  for (int p = 0; p < n; ++p) {
+    const int M = P[p].geom.M;
+    W[p].fw = fused_carve(c, M);                c += align256(fused_ws_bytes(M));
+    W[p].rot = reinterpret_cast<float*>(c);     c += align256((size_t)P[p].B * 9 * sizeof(float));
+    W[p].part = reinterpret_cast<double*>(c);   c += align256((size_t)kMultiParts * sizeof(double));
+  }
+  return CS_OK;
+}
+
+long disc_pixels(int M, int r) {
+  long n = 0;
+  for (int y = -r; y <= r; ++y) {
+    int xr = (int)std::floor(std::sqrt((double)(r * r - y * y)));
+    n += 2 * xr + 1;
+  }
+  (void)M;
+  return n;
+}
+
+// blocks of the multi-volume traversal, split in proportion to each
+// problem's pixel count
+void split_blocks(const cs_handle* h, const cs_problem* P, int n, int* start, int* total) {
+  const int G = h->num_sms * h->blocks_per_sm;
+  double work[CS_MAX_PROBLEMS], sum = 0;
+  for (int p = 0; p < n; ++p) {
+    work[p] = (double)P[p].B * (double)disc_pixels(P[p].geom.M, P[p].geom.r_max);
+    sum += work[p];
+  }
+  int acc = 0;
+  start[0] = 0;
+  for (int p = 0; p < n; ++p) {
+    int b = (int)std::lround(G * work[p] / sum);
+    if (b < 1) b = 1;
+    acc += b;
+    start[p + 1] = acc;
+  }
+  *total = acc;
+}
+
+cudaError_t prepare_tables(cs_handle* h, const cs_problem* P, int n, const ProblemWs* W,
+                           cudaStream_t s) {
+  for (int p = 0; p < n; ++p) {
+    const int key = P[p].geom.M * 1024 + P[p].geom.r_max;
+    if (h->mtable_key[p] != key) {
+      cudaError_t e = launch_disc_table(P[p].geom.M, P[p].geom.r_max, W[p].fw, s);
+      if (e != cudaSuccess) return e;
+      h->mtable_key[p] = key;
+    }
+  }
+  return cudaSuccess;
+}
+
+FusedArgs problem_args(const cs_problem& q, const ProblemWs& w, const Geo& G) {
+  FusedArgs A{};
+  A.G = G;
+  A.table = w.fw.table;
+  A.n_px_dev = w.fw.n_px;
+  A.rot = w.rot;
+  A.df = q.defocus;
+  A.B = q.B;
+  A.scale = q.scale;
+  A.vol = reinterpret_cast<const float2*>(q.state.v);
+  A.img = reinterpret_cast<const float2*>(q.images);
+  A.E = w.fw.E;
+  A.O = w.fw.O;
+  A.P = w.fw.P;
+  A.K = q.state.n_probes;
+  A.vp = w.fw.pairs;
+  A.seed = q.state.seed;
+  A.k_dev = q.state.scalars + CS_S_K;
+  A.cursor = q.state.scalars + CS_S_K;
+  A.n_batches = q.n_batches;
+  return A;
+}
+
+// Everything of one multi-volume step, enqueued on s (no allocation, no
+// host synchronisation: capturable).
+int multi_step_enqueue(cs_handle* h, const cs_problem* P, int n, const ProblemWs* W,
+                       cudaStream_t s) {
+  const bool hutch = P[0].state.mode == CS_HUTCHINSON;
+  MultiFusedArgs MA{};
+  MA.n = n;
+  int total = 0;
+  split_blocks(h, P, n, MA.start, &total);
+  for (int p = 0; p < n; ++p) {
+    const cs_problem& q = P[p];
+    const int M = q.geom.M;
+    CS_CUDA(launch_quat_to_rot_cursor(q.quat, q.B, q.n_batches, q.state.scalars + CS_S_K,
+                                      W[p].rot, s),
+            "quat_to_rot launch");
+    if (hutch) CS_CUDA(launch_zero_r4(M, W[p].fw, s), "zero accumulators");
+    CS_CUDA(launch_zero_c2(M, W[p].fw, s), "zero accumulators");
+    CS_CUDA(launch_pairs(M, reinterpret_cast<const float2*>(q.state.v), W[p].fw.pairs,
+                         h->num_sms, s),
+            "pairs launch");
+    MA.a[p] = problem_args(q, W[p], make_geo(q.geom));
+    MA.a[p].part = W[p].part;                   // loss partials
+  }
+  CS_CUDA(launch_fused_multi(hutch ? (F_GRAD | F_HUTCH) : F_GRAD, MA, total, h->block, s),
+          "multi-volume traversal launch");
+  int nd[CS_MAX_PROBLEMS];
+  for (int p = 0; p < n; ++p) {
+    const cs_problem& q = P[p];
+    CS_CUDA(launch_step_post(q.geom.M, q.state.mode, reinterpret_cast<const float2*>(q.state.v),
+                             q.lambda, q.state.beta, q.state.scalars, W[p].fw, q.state.D,
+                             q.state.D_avg, W[p].part + 2 * kPartRegion, W[p].part + kPartRegion,
+                             &nd[p], h->num_sms, s),
+            "step_post launch");
+    MA.a[p].img = nullptr;
+    MA.a[p].part = W[p].part + 3 * kPartRegion;   // curvature partials
+  }
+  CS_CUDA(launch_fused_multi(F_CURV, MA, total, h->block, s), "multi-volume curvature launch");
+  for (int p = 0; p < n; ++p) {
+    const cs_problem& q = P[p];
+    const int nb = MA.start[p + 1] - MA.start[p];
+    double* pD = W[p].part + 2 * kPartRegion;
+    CS_CUDA(launch_eta(q.state.scalars, W[p].part, nb, W[p].part + kPartRegion, nd[p], pD,
+                       pD + nd[p], nd[p], W[p].part + 3 * kPartRegion, nb, nullptr, q.lambda,
+                       q.scale, q.state.c, q.state.max_halvings, s),
+            "eta launch");
+    CS_CUDA(launch_update_pairs(q.geom.M, reinterpret_cast<float2*>(q.state.v), W[p].fw,
+                                q.state.scalars, h->num_sms, s),
+            "update launch");
+  }
+  return CS_OK;
+}
+
+}  // namespace
+
+struct cs_graph {
+  cs_handle* h = nullptr;
+  int device = 0;
+  int generation = 0;
+  uint64_t n_kernels = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+int cs_multi_step(cs_handle* h, const cs_problem* probs, int n, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_problems(h, probs, n));
+  CS_SCOPE(h);
+  ProblemWs W[CS_MAX_PROBLEMS];
+  CS_TRY(ensure_mws(h, probs, n, W));
+  cudaStream_t s = S(stream);
+  CS_CUDA(prepare_tables(h, probs, n, W, s), "pixel table launch");
+  return multi_step_enqueue(h, probs, n, W, s);
+}
+
+int cs_multi_step_graph(cs_handle* h, const cs_problem* probs, int n, cs_graph** out) {
+  if (!h || !out) return CS_ERR_ARG;
+  *out = nullptr;
+  CS_TRY(check_problems(h, probs, n));
+  CS_SCOPE(h);
+  ProblemWs W[CS_MAX_PROBLEMS];
+  CS_TRY(ensure_mws(h, probs, n, W));
+  cudaStream_t cs_stream = nullptr;
+  CS_CUDA(cudaStreamCreateWithFlags(&cs_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  cudaError_t e = prepare_tables(h, probs, n, W, cs_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs_stream);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs_stream);
+    return cuda_fail(h, e, "pixel tables before capture");
+  }
+  cs_graph* g = new (std::nothrow) cs_graph();
+  if (!g) {
+    cudaStreamDestroy(cs_stream);
+    return fail(h, CS_ERR_ALLOC, "graph object");
+  }
+  const uint64_t l0 = g_launches.load();
+  e = cudaStreamBeginCapture(cs_stream, cudaStreamCaptureModeThreadLocal);
+  int rc = CS_OK;
+  if (e == cudaSuccess) rc = multi_step_enqueue(h, probs, n, W, cs_stream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cs_stream, &graph) : e;
+  const uint64_t captured = g_launches.load() - l0;
+  g_launches.fetch_sub(captured);   // captured, not executed
+  cudaStreamDestroy(cs_stream);
+  if (rc != CS_OK || e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    delete g;
+    if (rc != CS_OK) return rc;
+    return cuda_fail(h, e != cudaSuccess ? e : e2, "stream capture");
+  }
+  e = cudaGraphInstantiate(&g->exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    delete g;
+    return cuda_fail(h, e, "cudaGraphInstantiate");
+  }
+  g->graph = graph;
+  g->h = h;
+  g->device = h->device;
+  g->generation = h->mws_generation;
+  g->n_kernels = captured;
+  *out = g;
+  return CS_OK;
+}
+
+int cs_graph_launch(cs_graph* g, void* stream) {
+  if (!g || !g->exec) return CS_ERR_ARG;
+  cs_handle* h = g->h;
+  if (g->generation != h->mws_generation)
+    return fail(h, CS_ERR_ARG, "the handle's multi-volume workspace changed since the capture");
+  CS_SCOPE(h);
+  CS_CUDA(cudaGraphLaunch(g->exec, S(stream)), "cudaGraphLaunch");
+  count_launches((int)g->n_kernels);
+  return CS_OK;
+}
+
+int cs_graph_destroy(cs_graph* g) {
+  if (!g) return CS_OK;
+  {
+    DeviceScope scope(g->device);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+  }
+  delete g;
+  return CS_OK;
+}
+
+int cs_set_launch_shape(cs_handle* h, int block, int bps) {
+  if (!h) return CS_ERR_ARG;
+  if (block != 128 && block != 256)
+    return fail(h, CS_ERR_ARG, "block_threads=%d must be 128 or 256", block);
+  if (bps < 1 || bps > (block == 256 ? 32 : 64))
+    return fail(h, CS_ERR_ARG, "blocks_per_sm=%d out of range", bps);
+  h->block = block;
+  h->blocks_per_sm = bps;
+  return CS_OK;
+}
+
+int cs_autotune(cs_handle* h, const cs_problem* probs, int n, int* block_out, int* bps_out) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_problems(h, probs, n));
+  CS_SCOPE(h);
+  ProblemWs W[CS_MAX_PROBLEMS];
+  CS_TRY(ensure_mws(h, probs, n, W));
+  cudaStream_t s = nullptr;
+  CS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
+  const bool hutch = probs[0].state.mode == CS_HUTCHINSON;
+  cudaError_t e = prepare_tables(h, probs, n, W, s);
+  MultiFusedArgs MA{};
+  MA.n = n;
+  for (int p = 0; p < n && e == cudaSuccess; ++p) {
+    const cs_problem& q = probs[p];
+    e = launch_quat_to_rot_cursor(q.quat, q.B, q.n_batches, q.state.scalars + CS_S_K, W[p].rot, s);
+    if (e == cudaSuccess) e = launch_pairs(q.geom.M, reinterpret_cast<const float2*>(q.state.v),
+                                           W[p].fw.pairs, h->num_sms, s);
+    MA.a[p] = problem_args(q, W[p], make_geo(q.geom));
+    MA.a[p].part = W[p].part;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  const int old_block = h->block, old_bps = h->blocks_per_sm;
+  struct Shape { int block, bps; };
+  const Shape cands[] = {{256, 4}, {256, 6}, {256, 8}, {128, 8}, {128, 12}, {128, 16}};
+  float best = 1e30f;
+  Shape pick = {old_block, old_bps};
+  for (const Shape& c : cands) {
+    if (e != cudaSuccess) break;
+    h->block = c.block;
+    h->blocks_per_sm = c.bps;
+    int total = 0;
+    split_blocks(h, probs, n, MA.start, &total);
+    if (total > kPartRegion) continue;
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      cudaEventRecord(a, s);
+      e = launch_fused_multi(hutch ? (F_GRAD | F_HUTCH) : F_GRAD, MA, total, c.block, s);
+      cudaEventRecord(b, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e == cudaSuccess && ms < tmin) tmin = ms;
+    }
+    if (e == cudaSuccess && tmin < best) {
+      best = tmin;
+      pick = c;
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) {
+    h->block = old_block;
+    h->blocks_per_sm = old_bps;
+    return cuda_fail(h, e, "autotune");
+  }
+  h->block = pick.block;
+  h->blocks_per_sm = pick.bps;
+  if (block_out) *block_out = pick.block;
+  if (bps_out) *bps_out = pick.bps;
   return CS_OK;
 }
 

@@ -244,28 +244,7 @@ __device__ __forceinline__ float gather_cell_r(const Geo& G, const Cell& c,
   return a;
 }
 
-struct FusedArgs {
-  Geo G;
-  const int* table;
-  const int* n_px_dev;
-  const float* rot;
-  const float* df;
-  int B;
-  float scale;
-  const float2* vol;    // F_GRAD: volume; F_CURV: direction d
-  const float* zr;      // F_HVP: real vector z
-  const float2* img;    // F_ADJ, F_GRAD
-  float2* E;
-  float2* O;
-  double* part;         // F_GRAD: data-term partials; F_CURV: curvature partials
-  const uint32_t* bits; // unused (probe words are generated in place)
-  float* P;             // F_HUTCH, F_HVP
-  int K;
-  const float4* vp;     // pair layout of vol (F_GRAD, F_CURV)
-  uint64_t seed;        // F_HUTCH: probe stream
-  uint64_t block_host;  // F_HUTCH: probe block, or
-  const double* k_dev;  //   (iterations done + 1) read from the SGD state
-};
+
 
 // Probe words of the corners (x0, x0+1) of one cell row starting at linear
 // index j = row + x0: voxels (2i, 2i+1) share SplitMix64 output i.
@@ -290,13 +269,20 @@ __device__ __forceinline__ void row_words(uint64_t seed, uint64_t base, size_t j
 //   F_HVP   : P4 += scale C^2 w_j (P z)           (Eq. hessian)
 //   F_CURV  : part += C^2 |P d|^2                 (curvature of the Armijo step)
 template <int FL>
-__global__ void __launch_bounds__(256)
-k_fused(FusedArgs A) {
+__device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int nblk) {
   const Geo& G = A.G;
   const int n_px = *A.n_px_dev;
-  const int nch = (n_px + 255) >> 8;
+  const int bd = blockDim.x;
+  const int nch = (n_px + bd - 1) / bd;
   const int total = A.B * nch;
   const int MM = G.M * G.M;
+  const float2* img = A.img;
+  const float* dfp = A.df;
+  if (A.cursor) {
+    const long long bsel = (long long)(*A.cursor) % (long long)A.n_batches;
+    if (img) img += (size_t)bsel * A.B * MM;
+    if (dfp) dfp += (size_t)bsel * A.B;
+  }
   const uint32_t pmask = A.K >= 32 ? 0xffffffffu : ((1u << A.K) - 1u);
   const float invK = 1.0f / (float)(A.K > 0 ? A.K : 1);
   uint64_t pbase = 0;
@@ -305,9 +291,9 @@ k_fused(FusedArgs A) {
     pbase = blk * (((uint64_t)G.M * G.M * G.M) >> 1);
   }
   float acc = 0.f;
-  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+  for (int w = blk; w < total; w += nblk) {
     const int b = w / nch;
-    const int p = (w - b * nch) * 256 + threadIdx.x;
+    const int p = (w - b * nch) * bd + threadIdx.x;
     if (p >= n_px) continue;
     const int e = __ldg(A.table + p);
     const int ix = e & 0xffff, iy = e >> 16;
@@ -317,12 +303,12 @@ k_fused(FusedArgs A) {
     float C = 1.f;
     if (G.ctf_on) {
       float a_hi, a_lo;
-      ctf_coeff(G, __ldg(A.df + b), a_hi, a_lo);
+      ctf_coeff(G, __ldg(dfp + b), a_hi, a_lo);
       C = ctf_value(G, a_hi, a_lo, kx * kx + ky * ky);
     }
     const bool inb = base_in(G, c);
     if (FL & (F_ADJ | F_GRAD)) {
-      float2 r = __ldcs(A.img + (size_t)b * MM + (size_t)iy * G.M + ix);
+      float2 r = __ldcs(img + (size_t)b * MM + (size_t)iy * G.M + ix);
       if (FL & F_GRAD) {
         const float2 a = inb ? gather_cell_pairs(G, c, A.vp) : gather_cell_pairs_slow(G, c, A.vp);
         r = make_float2(fmaf(C, a.x, -r.x), fmaf(C, a.y, -r.y));
@@ -392,9 +378,33 @@ k_fused(FusedArgs A) {
       scatter_cell_r4(G, c, vals, A.P);
     }
   }
+  return acc;
+}
+
+template <int FL>
+__global__ void __launch_bounds__(256)
+k_fused(FusedArgs A) {
+  const float acc = fused_traverse<FL>(A, blockIdx.x, gridDim.x);
   if (FL & (F_GRAD | F_CURV)) {
     const double t = block_sum((double)acc);
     if (threadIdx.x == 0) A.part[blockIdx.x] = t;
+  }
+}
+
+// Several independent problems (volumes of different grid sizes) in one
+// launch: blocks [start[p], start[p+1]) walk problem p's items, so each
+// block's partial sum belongs to one problem and stays deterministic.
+template <int FL>
+__global__ void __launch_bounds__(256)
+k_fused_multi(MultiFusedArgs MA) {
+  int p = 0;
+  while (p + 1 < MA.n && (int)blockIdx.x >= MA.start[p + 1]) ++p;
+  const int lb = blockIdx.x - MA.start[p];
+  const int nb = MA.start[p + 1] - MA.start[p];
+  const float acc = fused_traverse<FL>(MA.a[p], lb, nb);
+  if (FL & (F_GRAD | F_CURV)) {
+    const double t = block_sum((double)acc);
+    if (threadIdx.x == 0) MA.a[p].part[lb] = t;
   }
 }
 
@@ -581,7 +591,7 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
                          const float* df, int B, float scale, const float2* vol,
                          const float4* vp, const float* zr, const float2* img, double* part,
                          uint64_t seed, uint64_t block_host, const double* k_dev, int K,
-                         int grid, cudaStream_t s) {
+                         int grid, cudaStream_t s, int block) {
   FusedArgs A;
   A.G = G;
   A.table = w.table;
@@ -603,13 +613,29 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
   A.seed = seed;
   A.block_host = block_host;
   A.k_dev = k_dev;
+  A.cursor = nullptr;
+  A.n_batches = 1;
+  if (block != 128 && block != 256) return cudaErrorInvalidValue;
   switch (flags) {
-    case F_ADJ: k_fused<F_ADJ><<<grid, 256, 0, s>>>(A); break;
-    case F_GRAD: k_fused<F_GRAD><<<grid, 256, 0, s>>>(A); break;
-    case F_GRAD | F_HUTCH: k_fused<F_GRAD | F_HUTCH><<<grid, 256, 0, s>>>(A); break;
-    case F_HUTCH: k_fused<F_HUTCH><<<grid, 256, 0, s>>>(A); break;
-    case F_HVP: k_fused<F_HVP><<<grid, 256, 0, s>>>(A); break;
-    case F_CURV: k_fused<F_CURV><<<grid, 256, 0, s>>>(A); break;
+    case F_ADJ: k_fused<F_ADJ><<<grid, block, 0, s>>>(A); break;
+    case F_GRAD: k_fused<F_GRAD><<<grid, block, 0, s>>>(A); break;
+    case F_GRAD | F_HUTCH: k_fused<F_GRAD | F_HUTCH><<<grid, block, 0, s>>>(A); break;
+    case F_HUTCH: k_fused<F_HUTCH><<<grid, block, 0, s>>>(A); break;
+    case F_HVP: k_fused<F_HVP><<<grid, block, 0, s>>>(A); break;
+    case F_CURV: k_fused<F_CURV><<<grid, block, 0, s>>>(A); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_multi(int flags, const MultiFusedArgs& MA, int grid, int block,
+                               cudaStream_t s) {
+  if (block != 128 && block != 256) return cudaErrorInvalidValue;
+  switch (flags) {
+    case F_GRAD: k_fused_multi<F_GRAD><<<grid, block, 0, s>>>(MA); break;
+    case F_GRAD | F_HUTCH: k_fused_multi<F_GRAD | F_HUTCH><<<grid, block, 0, s>>>(MA); break;
+    case F_CURV: k_fused_multi<F_CURV><<<grid, block, 0, s>>>(MA); break;
     default: return cudaErrorInvalidValue;
   }
   count_launches(1);

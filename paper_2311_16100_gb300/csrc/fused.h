@@ -7,7 +7,43 @@ namespace cs {
 
 enum FusedFlags { F_ADJ = 1, F_GRAD = 2, F_HUTCH = 4, F_HVP = 8, F_CURV = 16 };
 
+constexpr int kMaxProblems = 8;   // volumes per multi-volume launch
 
+
+
+struct FusedArgs {
+  Geo G;
+  const int* table;
+  const int* n_px_dev;
+  const float* rot;
+  const float* df;
+  int B;
+  float scale;
+  const float2* vol;    // F_GRAD: volume; F_CURV: direction d
+  const float* zr;      // F_HVP: real vector z
+  const float2* img;    // F_ADJ, F_GRAD
+  float2* E;
+  float2* O;
+  double* part;         // F_GRAD: data-term partials; F_CURV: curvature partials
+  const uint32_t* bits; // unused (probe words are generated in place)
+  float* P;             // F_HUTCH, F_HVP
+  int K;
+  const float4* vp;     // pair layout of vol (F_GRAD, F_CURV)
+  uint64_t seed;        // F_HUTCH: probe stream
+  uint64_t block_host;  // F_HUTCH: probe block, or
+  const double* k_dev;  //   (iterations done + 1) read from the SGD state
+  // batch selection on the device (multi-volume step): when cursor is set,
+  // img and df point at all n_batches batches and batch (k mod n_batches)
+  // is used, k = iterations done (*cursor)
+  const double* cursor;
+  int n_batches;
+};
+
+struct MultiFusedArgs {
+  int n;                              // problems
+  int start[kMaxProblems + 1];        // first block of each problem
+  FusedArgs a[kMaxProblems];
+};
 
 size_t fused_ws_bytes(int M);
 FusedWs fused_carve(void* base, int M);
@@ -16,11 +52,15 @@ cudaError_t launch_disc_table(int M, int r, const FusedWs& w, cudaStream_t s);
 // One trilinear traversal with the given flags (partials: one per block).
 // vol: natural layout, vp: its pair layout (F_GRAD, F_CURV); probe words
 // (F_HUTCH) come from (seed, block), block = *k_dev + 1 when k_dev != NULL.
+// block = threads per block (128 or 256).
 cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float* rot,
                          const float* df, int B, float scale, const float2* vol,
                          const float4* vp, const float* zr, const float2* img, double* part,
                          uint64_t seed, uint64_t block_host, const double* k_dev, int K,
-                         int grid, cudaStream_t s);
+                         int grid, cudaStream_t s, int block = 256);
+// One launch over several problems (flags F_GRAD, F_GRAD|F_HUTCH or F_CURV).
+cudaError_t launch_fused_multi(int flags, const MultiFusedArgs& MA, int grid, int block,
+                               cudaStream_t s);
 
 // Element-wise work of one step between the fused traversal and the
 // curvature pass (see fused.cu); partG holds the |g|^2/D-hat partials then

@@ -23,6 +23,14 @@ struct cs_handle {
   size_t ws_bytes = 0;
   int algo = 0;            // CS_ALGO_*
   int table_key = -1;      // (M, r_max) of the cached disc pixel table
+  // launch shape of the trilinear traversals (cs_set_launch_shape / cs_autotune)
+  int block = 256;
+  int blocks_per_sm = 8;
+  // multi-volume workspace
+  void* mws = nullptr;
+  size_t mws_bytes = 0;
+  int mws_generation = 0;
+  int mtable_key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
   // profiler: CS_NPHASES + 1 boundary events per timed step
   bool prof = false;
   int prof_max_steps = 0;
@@ -70,6 +78,9 @@ int pixel_grid(int num_sms, int B, int M);
 
 // ---- launchers (return the cudaError_t of the launch) ----
 cudaError_t launch_quat_to_rot(const float* quat, int B, float* rot, cudaStream_t s);
+// rotations of batch (*cursor mod n_batches) of a dataset's quaternions
+cudaError_t launch_quat_to_rot_cursor(const float* quat, int B, int n_batches,
+                                      const double* cursor, float* rot, cudaStream_t s);
 cudaError_t launch_slice_project(const Geo& G, const float2* vol, const float* rot,
                                  const float* df, int B, float2* out, int grid,
                                  cudaStream_t s);

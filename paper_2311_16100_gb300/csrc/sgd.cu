@@ -32,6 +32,29 @@ __global__ void k_quat_to_rot(const float* __restrict__ q, int B, float* __restr
   r[8] = 1.f - 2.f * (x * x + y * y);
 }
 
+// Rotations of batch (k mod n_batches) of a dataset's quaternions, k read
+// from the SGD state (iterations done).
+__global__ void k_quat_to_rot_cursor(const float* __restrict__ q, int B, int n_batches,
+                                     const double* __restrict__ cursor, float* __restrict__ R) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const long long bsel = (long long)(*cursor) % (long long)n_batches;
+  const float* qq = q + 4 * ((size_t)bsel * B + b);
+  float w = qq[0], x = qq[1], y = qq[2], z = qq[3];
+  float inv = rsqrtf(w * w + x * x + y * y + z * z);
+  w *= inv; x *= inv; y *= inv; z *= inv;
+  float* r = R + 9 * b;
+  r[0] = 1.f - 2.f * (y * y + z * z);
+  r[1] = 2.f * (x * y - w * z);
+  r[2] = 2.f * (x * z + w * y);
+  r[3] = 2.f * (x * y + w * z);
+  r[4] = 1.f - 2.f * (x * x + z * z);
+  r[5] = 2.f * (y * z - w * x);
+  r[6] = 2.f * (x * z - w * y);
+  r[7] = 2.f * (y * z + w * x);
+  r[8] = 1.f - 2.f * (x * x + y * y);
+}
+
 // Running mean of the Hutchinson estimates, EMA and threshold, for step
 // k = (iterations done) + 1.
 __global__ void __launch_bounds__(kBlock)
@@ -183,6 +206,13 @@ k_rel_err_final(const double* part, int nb, double* out) {
 
 cudaError_t launch_quat_to_rot(const float* quat, int B, float* rot, cudaStream_t s) {
   k_quat_to_rot<<<(B + 127) / 128, 128, 0, s>>>(quat, B, rot);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quat_to_rot_cursor(const float* quat, int B, int n_batches,
+                                      const double* cursor, float* rot, cudaStream_t s) {
+  k_quat_to_rot_cursor<<<(B + 127) / 128, 128, 0, s>>>(quat, B, n_batches, cursor, rot);
   count_launches(1);
   return cudaGetLastError();
 }

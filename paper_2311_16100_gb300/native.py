@@ -40,6 +40,14 @@ class CsSgdState(ctypes.Structure):
                 ("max_halvings", c_int)]
 
 
+class CsProblem(ctypes.Structure):
+    _fields_ = [("geom", CsGeom), ("state", CsSgdState), ("images", c_void_p),
+                ("quat", c_void_p), ("defocus", c_void_p), ("B", c_int), ("n_batches", c_int),
+                ("lam", c_float), ("scale", c_float)]
+
+
+CS_MAX_PROBLEMS = 8
+
 P = c_void_p
 G = POINTER(CsGeom)
 
@@ -70,6 +78,12 @@ SIGNATURES = {
     "cs_profile_read": (c_int, [P, POINTER(c_double), POINTER(c_int)]),
     "cs_kernel_launches": (c_uint64, []),
     "cs_measure_reduction_rate": (c_int, [P, POINTER(c_double)]),
+    "cs_multi_step": (c_int, [P, POINTER(CsProblem), c_int, P]),
+    "cs_multi_step_graph": (c_int, [P, POINTER(CsProblem), c_int, POINTER(c_void_p)]),
+    "cs_graph_launch": (c_int, [P, P]),
+    "cs_graph_destroy": (c_int, [P]),
+    "cs_set_launch_shape": (c_int, [P, c_int, c_int]),
+    "cs_autotune": (c_int, [P, POINTER(CsProblem), c_int, POINTER(c_int), POINTER(c_int)]),
 }
 
 _lib = None

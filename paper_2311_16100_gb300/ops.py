@@ -248,6 +248,39 @@ class Handle:
                     self.lib.cs_measure_reduction_rate(self.h, ctypes.byref(g)))
         return g.value
 
+    # ------------------------------------------------ several volumes
+    def _problems(self, problems):
+        arr = (N.CsProblem * len(problems))()
+        for i, p in enumerate(problems):
+            arr[i] = p.cstruct()
+        return arr
+
+    def multi_step(self, problems, stream=None):
+        """One Algorithm 1 iteration for each Problem; one traversal launch
+        for all of them (cs_multi_step)."""
+        arr = self._problems(problems)
+        self._check("cs_multi_step", self.lib.cs_multi_step(self.h, arr, len(problems),
+                                                            _stream(stream)))
+
+    def multi_step_graph(self, problems) -> "Graph":
+        arr = self._problems(problems)
+        g = ctypes.c_void_p()
+        self._check("cs_multi_step_graph",
+                    self.lib.cs_multi_step_graph(self.h, arr, len(problems), ctypes.byref(g)))
+        return Graph(self, g, problems)
+
+    def set_launch_shape(self, block_threads: int, blocks_per_sm: int):
+        self._check("cs_set_launch_shape",
+                    self.lib.cs_set_launch_shape(self.h, block_threads, blocks_per_sm))
+
+    def autotune(self, problems):
+        """(threads per block, blocks per SM) picked for these problems."""
+        arr = self._problems(problems)
+        bt, bps = ctypes.c_int(), ctypes.c_int()
+        self._check("cs_autotune", self.lib.cs_autotune(self.h, arr, len(problems),
+                                                        ctypes.byref(bt), ctypes.byref(bps)))
+        return bt.value, bps.value
+
     def rel_err(self, geom: Geometry, v, v_ref, out=None, stream=None):
         if out is None:
             out = torch.empty((), dtype=torch.float64, device=v.device)
@@ -298,3 +331,52 @@ class SGDState:
         s.max_halvings = self.max_halvings
         self._cs = s
         return s
+
+
+class Problem:
+    """One refinement problem of a multi-volume step: geometry, SGD state and
+    all of its images (n_batches batches of B) in device memory."""
+
+    def __init__(self, geom: Geometry, state: SGDState, images, quat, defocus, B: int,
+                 lam: float, scale: float):
+        n_img = images.shape[0]
+        if n_img % B:
+            raise ValueError("the image count must be a multiple of B")
+        for t, name in ((images, "images"), (quat, "quat")):
+            _ptr(t, None, name)
+        self.geom, self.state = geom, state
+        self.images, self.quat, self.defocus = images, quat, defocus
+        self.B, self.n_batches, self.lam, self.scale = B, n_img // B, lam, scale
+
+    def cstruct(self) -> N.CsProblem:
+        c = N.CsProblem()
+        c.geom = self.geom._c
+        c.state = self.state.cstruct()
+        c.images = self.images.data_ptr()
+        c.quat = self.quat.data_ptr()
+        c.defocus = self.defocus.data_ptr() if self.defocus is not None else None
+        c.B, c.n_batches = self.B, self.n_batches
+        c.lam, c.scale = self.lam, self.scale
+        return c
+
+
+class Graph:
+    """A captured multi-volume step; launch() replays one step."""
+
+    def __init__(self, handle: Handle, g, problems):
+        self.handle, self.g, self.problems = handle, g, problems
+
+    def launch(self, stream=None):
+        self.handle._check("cs_graph_launch",
+                           self.handle.lib.cs_graph_launch(self.g, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "g", None):
+            self.handle.lib.cs_graph_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

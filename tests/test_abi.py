@@ -66,6 +66,8 @@ int main(void) {
          offsetof(cs_sgd_state, seed), offsetof(cs_sgd_state, beta),
          offsetof(cs_sgd_state, c), offsetof(cs_sgd_state, max_halvings));
   printf("%d %d %d\n", CS_NSCALARS, CS_S_HALVINGS, CS_MAX_M);
+  printf("%zu %zu %zu %zu %zu\n", sizeof(cs_problem), offsetof(cs_problem, state),
+         offsetof(cs_problem, images), offsetof(cs_problem, B), offsetof(cs_problem, scale));
   return 0;
 }
 ''')
@@ -78,7 +80,9 @@ int main(void) {
             N.CsCtf.enabled.offset,
             ctypes.sizeof(N.CsSgdState), N.CsSgdState.scalars.offset, N.CsSgdState.seed.offset,
             N.CsSgdState.beta.offset, N.CsSgdState.c.offset, N.CsSgdState.max_halvings.offset,
-            N.CS_NSCALARS, N.CS_S_HALVINGS, N.CS_MAX_M]
+            N.CS_NSCALARS, N.CS_S_HALVINGS, N.CS_MAX_M,
+            ctypes.sizeof(N.CsProblem), N.CsProblem.state.offset, N.CsProblem.images.offset,
+            N.CsProblem.B.offset, N.CsProblem.scale.offset]
     assert got == want
 
 
