@@ -340,7 +340,8 @@ typedef struct cs_graph cs_graph;
  * graph keeps the problems' device pointers and the handle's workspace; it
  * is invalid once the handle is destroyed, and cs_graph_launch returns
  * CS_ERR_ARG if the handle's multi-volume workspace was reallocated since
- * the capture. */
+ * the capture.  A replay uses that workspace: do not run other calls of the
+ * same handle concurrently with it (other streams), use another handle. */
 int cs_multi_step_graph(cs_handle* h, const cs_problem* probs, int n, cs_graph** graph);
 int cs_graph_launch(cs_graph* graph, void* stream);
 int cs_graph_destroy(cs_graph* graph);

@@ -112,7 +112,8 @@ def test_graph_replay_matches_eager_steps(env):
     ops, h, sets = env
     eager = [ds.problem(ops) for ds in sets]
     graphed = [ds.problem(ops) for ds in sets]
-    g = h.multi_step_graph(graphed)
+    h2 = ops.Handle(0)             # a graph replays on its handle's workspace
+    g = h2.multi_step_graph(graphed)
     s = torch.cuda.Stream()
     for _ in range(3):
         h.multi_step(eager)
@@ -122,6 +123,7 @@ def test_graph_replay_matches_eager_steps(env):
         assert rel_l2(b.state.v.cpu().numpy(), a.state.v.cpu().numpy()) <= 1e-5
         assert float(a.state.scalars[1]) == float(b.state.scalars[1]) == 3.0
     g.close()
+    h2.close()
 
 
 def test_autotune_keeps_results(env):
