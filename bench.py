@@ -53,6 +53,10 @@ def parse():
     p.add_argument("--config", choices=sorted(CONFIGS), default="m128")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-metric2", action="store_true",
+                   help="skip the time-to-relative-error runs (plain vs preconditioned)")
+    p.add_argument("--no-multi", action="store_true",
+                   help="skip the multi-volume graph-replay throughput")
     p.add_argument("--cpu-sample", type=int, default=128,
                    help="images in the oracle's timed sample")
     p.add_argument("--algo", choices=["auto", "vector", "tiled", "pixel"], default="auto",
@@ -350,6 +354,135 @@ def run_gpu(args, cfg, rank, world):
                 roofline=roof, red_roofline=red_roof, e2e=e2e, clocks=clk, scalars=sc, n_img=W["n_img"])
 
 
+# ------------------------------------------- time to relative error (metric 2)
+TTE_CONFIGS = {
+    # Fourier volume, images, batch, epochs as in the refinement workloads
+    "m32_nearest": dict(M=32, n_img=1000, B=100, epochs=5, interp="nearest", K=16, df=None,
+                        snr=0.1, blobs=20, seed=1000),
+    "m64_trilinear_ctf": dict(M=64, n_img=20480, B=256, epochs=10, interp="trilinear", K=32,
+                              df=(1.0, 3.0), snr=0.05, blobs=200, seed=2000),
+}
+THRESHOLDS = [0.5, 0.3, 0.2, 0.15, 0.1, 0.05, 0.02, 0.01]
+
+
+def time_to_error(cfg, torch, ops, synth, h):
+    """Wall (device) time of Algorithm 1 to reach relative volume errors,
+    plain SGD vs Hutchinson-preconditioned, both with the Armijo rule.  The
+    ground truth v* solves H v = b on the whole dataset (closed form under
+    nearest interpolation, conjugate gradients with the library's gradient
+    otherwise); the error is evaluated after every step outside the timing."""
+    M, B = cfg["M"], cfg["B"]
+    r = M // 2 - 1
+    W = build_workload(dict(cfg, n_img=cfg["n_img"]), 0, h, torch, ops, synth)
+    geom, images, quat, df, n_img = W["geom"], W["images"], W["quat"], W["df"], W["n_img"]
+    dfa = df if W["ctf"] else None
+    lam = W["sigma2"]
+    rot_all = h.quat_to_rot(quat)
+    b = h.backproject_adjoint(geom, images, rot_all, dfa, 1.0)
+    ball = torch.from_numpy(synth.ball_mask(M, r)).cuda()
+    if cfg["interp"] == "nearest":
+        d, _, _ = h.exact_diag(geom, rot_all, dfa, lam, 1.0)
+        vstar = torch.where(ball, b / d, torch.zeros_like(b))
+    else:   # CG on H v = b, H x = loss_grad(x) with zero images
+        zeros = torch.zeros_like(images)
+        x = torch.zeros_like(b)
+        rr = b.clone()
+        pp = rr.clone()
+        rs = float(torch.sum(torch.abs(rr) ** 2))
+        bn = rs ** 0.5
+        for _ in range(500):
+            _, Hp = h.loss_grad(geom, pp, zeros, rot_all, dfa, lam, 1.0)
+            a = rs / float(torch.sum((torch.conj(pp) * Hp).real))
+            x += a * pp
+            rr -= a * Hp
+            rs_new = float(torch.sum(torch.abs(rr) ** 2))
+            if rs_new ** 0.5 <= 1e-6 * bn:
+                break
+            pp = rr + (rs_new / rs) * pp
+            rs = rs_new
+        del zeros
+        vstar = torch.where(ball, x, torch.zeros_like(x))
+    alpha = h.threshold_alpha(geom, dfa, n_img, lam)
+    v0 = torch.from_numpy(synth.initial_volume(M, r, 1.0, cfg["seed"] + 7)).cuda()
+    scale = n_img / B
+    out = {"workload": f"{M}^3, {n_img} images, batch {B}, {cfg['epochs']} epochs, "
+                       f"{cfg['interp']}, {'CTF' if cfg['df'] else 'no CTF'}, {cfg['K']} probes",
+           "lambda": lam}
+    for mode in ("plain", "hutchinson"):
+        st = ops.SGDState(v0, mode=mode, alpha=alpha, eta0=1.0, beta=0.9, armijo_c=0.5,
+                          n_probes=cfg["K"], seed=cfg["seed"] + 11)
+        err = h.rel_err(geom, st.v, vstar)
+        first = {t: None for t in THRESHOLDS}
+        t_ms = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        rot = torch.empty((B, 3, 3), dtype=torch.float32, device="cuda")
+        for ep in range(cfg["epochs"]):
+            perm = torch.from_numpy(synth.permutation(n_img, cfg["seed"] + 31 + ep)).cuda()
+            im_p, q_p = images[perm].contiguous(), quat[perm].contiguous()
+            df_p = df[perm].contiguous() if W["ctf"] else None
+            torch.cuda.synchronize()
+            for bi in range(n_img // B):
+                sl = slice(bi * B, (bi + 1) * B)
+                e0.record()
+                h.quat_to_rot(q_p[sl], rot)
+                h.precond_sgd_step(geom, st, im_p[sl], rot, df_p[sl] if df_p is not None else None,
+                                   lam, scale)
+                e1.record()
+                h.rel_err(geom, st.v, vstar, out=err)
+                torch.cuda.synchronize()
+                t_ms += e0.elapsed_time(e1)
+                e = float(err)
+                for t in THRESHOLDS:
+                    if first[t] is None and e <= t:
+                        first[t] = round(t_ms, 3)
+        out[mode] = {"ms_to_rel_err": {str(t): first[t] for t in THRESHOLDS},
+                     "reached_1e-2": first[0.01] is not None,
+                     "final_rel_err": round(float(err), 5), "total_ms": round(t_ms, 3),
+                     "final_eta": float(st.scalars[0])}
+    return out
+
+
+def multi_volume(args, torch, ops, synth):
+    """Throughput of the multi-volume step (grids 64/96/128/160, 10k-40k
+    images each, batch 1024 per volume), autotuned, replayed as a CUDA graph."""
+    h = ops.Handle(torch.cuda.current_device())
+    specs = [(64, 10240, 200), (96, 20480, 600), (128, 30720, 1000), (160, 40960, 1500)]
+    probs, keep = [], []
+    for i, (M, n_img, blobs) in enumerate(specs):
+        cfg = dict(M=M, n_img=n_img, B=1024, interp="trilinear", K=32, df=(1.0, 3.0),
+                   snr=0.05, blobs=blobs, seed=7000 + 10 * i)
+        W = build_workload(cfg, 0, h, torch, ops, synth)
+        lam = W["sigma2"]
+        alpha = h.threshold_alpha(W["geom"], W["df"], W["n_img"], lam)
+        v0 = torch.from_numpy(synth.initial_volume(M, M // 2 - 1, 1.0, 7)).cuda()
+        st = ops.SGDState(v0, mode="hutchinson", alpha=alpha, n_probes=32, seed=5)
+        probs.append(ops.Problem(W["geom"], st, W["images"], W["quat"], W["df"], 1024, lam,
+                                 W["n_img"] / 1024))
+        keep.append(W)
+    bt, bps = h.autotune(probs)
+    g = h.multi_step_graph(probs)
+    s = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        g.launch(s)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    steps = max(args.steps, 10)
+    for _ in range(steps):
+        g.launch(s)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    imgs = 1024 * len(specs) * steps
+    out = {"volumes": [f"{M}^3 x {n} images" for M, n, _ in specs], "batch_per_volume": 1024,
+           "launch_shape": {"block_threads": bt, "blocks_per_sm": bps},
+           "ms_per_step": round(ms / steps, 4), "images_per_s": round(imgs / (ms / 1e3), 1),
+           "cuda_graph": True}
+    g.close()
+    h.close()
+    return out
+
+
 # ---------------------------------------------------------- oracle (CPU) arm
 def oracle_sample(cfg, n, seed):
     """A bounded sample of the workload for the FP64 oracle (inputs from the
@@ -474,6 +607,15 @@ def main():
                 "gpu_launches": r["launches"], "phases_ms_per_step": r["phases"],
                 "final_scalars": {"eta": r["scalars"][0], "k": r["scalars"][1],
                                   "loss": r["scalars"][3]}}
+        if world == 1 and not args.no_metric2:
+            from paper_2311_16100_gb300 import ops, synth
+            h2 = ops.Handle(torch.cuda.current_device())
+            line["time_to_rel_err"] = {k: time_to_error(c, torch, ops, synth, h2)
+                                       for k, c in TTE_CONFIGS.items()}
+            h2.close()
+        if world == 1 and not args.no_multi:
+            from paper_2311_16100_gb300 import ops, synth
+            line["multi_volume"] = multi_volume(args, torch, ops, synth)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_sample)
         print(json.dumps(line), flush=True)

@@ -27,6 +27,10 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   alg1_step            pinned: EM M-step equivalence (nearest, exact D, eta=1),
                        monotone decrease under the Armijo rule
   cg_solve             pinned: closed form under nearest interpolation
+  mlp (learned preconditioner network; not in the paper)
+                       pinned: BF16 rounding and GELU against torch's
+                       library routines, backpropagation against central
+                       finite differences of the FP64 network
 """
 from .geometry import (ball_mask, ctf_of_s2, ctf_pixels, default_r_max, disc_mask,
                        electron_wavelength_A, freq_axis, nearest_coords_fp32,
@@ -36,5 +40,6 @@ from .operators import (backproject_adjoint, coverage_features, dense_hessian,
 from .hutchinson import hutchinson_diag, probe_words, rademacher_probes, splitmix64
 from .sgd import (alg1_step, alpha_threshold, cg_solve, full_rhs, rel_err,
                   shell_counts)
+from . import mlp
 
 __all__ = [n for n in dir() if not n.startswith("_")]
