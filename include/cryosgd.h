@@ -356,6 +356,41 @@ int cs_set_launch_shape(cs_handle* h, int block_threads, int blocks_per_sm);
 int cs_autotune(cs_handle* h, const cs_problem* probs, int n, int* block_threads,
                 int* blocks_per_sm);
 
+/* ------------------------------------------------------------------------
+ * Learned diagonal preconditioner (not in the paper): a 3 -> 64 -> 64 -> 1
+ * network with GELU (tanh form) activations predicts log D per voxel from
+ * the features (|k| / (M/2), log1p(coverage_j), log1p(ctf2w_j)) where
+ * coverage and ctf2w are the outputs of cs_exact_diag; it is trained by mean
+ * squared error against log of Hutchinson estimates (Eq. hutch).  The
+ * 64 x 64 layer runs on BF16 tensor cores (tcgen05) with FP32 accumulation:
+ * its operands (first hidden activations, weights, and in the backward pass
+ * the second hidden layer's gradient) are rounded to BF16.
+ * Parameters: float[CS_MLP_NPARAMS], FP32 master copy, layout
+ *   W1[64][3] | b1[64] | W2[64][64] (out, in) | b2[64] | w3[64] | b3.
+ * ------------------------------------------------------------------------ */
+#define CS_MLP_NPARAMS 4481
+
+/* out_j = network(features_j) for all M^3 voxels (exp_out: exp of it, the
+ * preconditioner D itself).  use_tensor_cores = 0 runs the FP32 reference
+ * kernel (same rounding points). */
+int cs_mlp_forward(cs_handle* h, int M, const float* params, const float* coverage,
+                   const float* ctf2w, float* out, int exp_out, int use_tensor_cores,
+                   void* stream);
+/* grad += gradient of L = mean over voxels with |k| <= r_ball of
+ * (network_j - target_j)^2; *sse += sum of squared residuals (device
+ * double).  The caller zeroes grad and sse. */
+int cs_mlp_grad(cs_handle* h, int M, int r_ball, const float* params, const float* coverage,
+                const float* ctf2w, const float* target, float* grad, double* sse,
+                int use_tensor_cores, void* stream);
+/* One Adam step (Kingma & Ba 2015) on params with moments m, v (caller
+ * zeroes them before step 1); grad is read and zeroed.  step >= 1. */
+int cs_mlp_adam_step(cs_handle* h, float* params, float* m, float* v, float* grad, int step,
+                     float lr, float beta1, float beta2, float eps, void* stream);
+/* Synchronises the handle's device and reports whether a bounded
+ * device-side wait ran out since the last check (CS_ERR_TIMEOUT, and the
+ * word is cleared) or not (CS_OK). */
+int cs_check_device_status(cs_handle* h);
+
 /* Relative error over the ball |k| <= r_max:
  *   |v - v_ref| / |v_ref| -> *out (device double). */
 int cs_rel_err(cs_handle* h, const cs_geom* g, const float* v, const float* v_ref,

@@ -286,6 +286,8 @@ int cs_destroy(cs_handle* h) {
       cudaFree(h->ws);
     }
     prof_free(h);
+    if (h->mws) cudaFree(h->mws);
+    if (h->status) cudaFree(h->status);
   }
   delete h;
   return CS_OK;
@@ -1203,6 +1205,102 @@ int cs_rel_err(cs_handle* h, const cs_geom* g, const float* v, const float* v_re
                          reinterpret_cast<const float2*>(v_ref), w.part, out, h->num_sms,
                          S(stream)),
           "rel_err launch");
+  return CS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------ learned preconditioner
+
+namespace {
+
+int ensure_status(cs_handle* h) {
+  if (h->status) return CS_OK;
+  int* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, CS_ERR_ALLOC, "status word: %s", cudaGetErrorString(e));
+  }
+  e = cudaMemset(p, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    return cuda_fail(h, e, "status word");
+  }
+  h->status = p;
+  return CS_OK;
+}
+
+long ball_count(int M, int r) {
+  const int half = M / 2;
+  long n = 0;
+  for (int z = -half; z < half; ++z)
+    for (int y = -half; y < half; ++y) {
+      const long q = (long)z * z + (long)y * y;
+      if (q > (long)r * r) continue;
+      const int xr = (int)std::floor(std::sqrt((double)((long)r * r - q)));
+      const int lo = -xr < -half ? -half : -xr, hi = xr > half - 1 ? half - 1 : xr;
+      n += hi - lo + 1;
+    }
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cs_mlp_forward(cs_handle* h, int M, const float* params, const float* cov, const float* c2w,
+                   float* out, int exp_out, int tc, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  if (M < 4 || M > CS_MAX_M || (M & 1)) return fail(h, CS_ERR_SHAPE, "M=%d invalid", M);
+  if (!params || !cov || !c2w || !out) return fail(h, CS_ERR_ARG, "NULL pointer argument");
+  CS_SCOPE(h);
+  CS_TRY(ensure_status(h));
+  CS_CUDA(launch_mlp_forward(M, params, cov, c2w, out, exp_out, tc != 0, h->status, h->num_sms,
+                             S(stream)),
+          "mlp_forward launch");
+  return CS_OK;
+}
+
+int cs_mlp_grad(cs_handle* h, int M, int r_ball, const float* params, const float* cov,
+                const float* c2w, const float* target, float* grad, double* sse, int tc,
+                void* stream) {
+  if (!h) return CS_ERR_ARG;
+  if (M < 4 || M > CS_MAX_M || (M & 1)) return fail(h, CS_ERR_SHAPE, "M=%d invalid", M);
+  if (r_ball < 1 || r_ball > M / 2) return fail(h, CS_ERR_SHAPE, "r_ball=%d invalid", r_ball);
+  if (!params || !cov || !c2w || !target || !grad || !sse)
+    return fail(h, CS_ERR_ARG, "NULL pointer argument");
+  CS_SCOPE(h);
+  CS_TRY(ensure_status(h));
+  const long nb = ball_count(M, r_ball);
+  CS_CUDA(launch_mlp_grad(M, r_ball * r_ball, 1.0f / (float)nb, params, cov, c2w, target, grad,
+                          sse, tc != 0, h->status, h->num_sms, S(stream)),
+          "mlp_grad launch");
+  return CS_OK;
+}
+
+int cs_mlp_adam_step(cs_handle* h, float* params, float* m, float* v, float* grad, int step,
+                     float lr, float b1, float b2, float eps, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  if (!params || !m || !v || !grad) return fail(h, CS_ERR_ARG, "NULL pointer argument");
+  if (step < 1 || !(lr > 0) || !(b1 >= 0 && b1 < 1) || !(b2 >= 0 && b2 < 1) || !(eps > 0))
+    return fail(h, CS_ERR_ARG, "Adam hyper-parameters out of range");
+  CS_SCOPE(h);
+  CS_CUDA(launch_adam(params, m, v, grad, step, lr, b1, b2, eps, S(stream)), "adam launch");
+  return CS_OK;
+}
+
+int cs_check_device_status(cs_handle* h) {
+  if (!h) return CS_ERR_ARG;
+  if (!h->status) return CS_OK;
+  CS_SCOPE(h);
+  CS_CUDA(cudaDeviceSynchronize(), "synchronise");
+  int flag = 0;
+  CS_CUDA(cudaMemcpy(&flag, h->status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+  if (flag) {
+    CS_CUDA(cudaMemset(h->status, 0, sizeof(int)), "status reset");
+    return fail(h, CS_ERR_TIMEOUT, "a bounded device-side wait ran out (tensor-core kernel)");
+  }
   return CS_OK;
 }
 

@@ -31,6 +31,8 @@ struct cs_handle {
   size_t mws_bytes = 0;
   int mws_generation = 0;
   int mtable_key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  // device status word: set by kernels whose bounded waits ran out
+  int* status = nullptr;
   // profiler: CS_NPHASES + 1 boundary events per timed step
   bool prof = false;
   int prof_max_steps = 0;
@@ -143,6 +145,17 @@ cudaError_t launch_eta(double* scalars, const double* part_loss, int n_loss,
                        int max_halvings, cudaStream_t s);
 cudaError_t launch_update(int n, float2* v, const float2* d, const double* scalars,
                           int num_sms, cudaStream_t s);
+// learned preconditioner network (mlp.cu)
+constexpr int kMlpParams = 4481;
+cudaError_t launch_mlp_forward(int M, const float* params, const float* cov, const float* c2w,
+                               float* out, int exp_out, bool tc, int* err, int num_sms,
+                               cudaStream_t s);
+cudaError_t launch_mlp_grad(int M, int r2, float inv_n, const float* params, const float* cov,
+                            const float* c2w, const float* target, float* grad, double* sse,
+                            bool tc, int* err, int num_sms, cudaStream_t s);
+cudaError_t launch_adam(float* p, float* m, float* v, float* g, int step, float lr, float b1,
+                        float b2, float eps, cudaStream_t s);
+
 // Rate of 16-byte global reductions (G ops/s) measured on a scratch buffer.
 cudaError_t measure_red_rate(void* scratch, size_t bytes, int num_sms, cudaStream_t s,
                              double* gops);

@@ -1,0 +1,668 @@
+// Learned diagonal preconditioner: a 3 -> 64 -> 64 -> 1 GELU network that
+// maps per-voxel features (|k| / (M/2), log1p(pose coverage),
+// log1p(sum C^2 w)) to log D, trained by mean squared error against
+// Hutchinson estimates of the diagonal (Eq. hutch).  Not in the paper.
+//
+// Two implementations of forward and gradient:
+//  * tensor cores (sm_103a): one CTA of 128 threads per tile of 128 voxels
+//    (thread t owns voxel row t = TMEM lane t).  The 64 x 64 layer
+//    H1 W2^T and the input gradient dA2 W2 are tcgen05.mma kind::f16
+//    (BF16 operands in shared memory, FP32 accumulators in tensor memory,
+//    M = 128, N = 64, K = 64); the weight gradient dA2^T H1 is read from the
+//    Gram matrix X X^T of X = [dA2 | H1]^T (M = N = 128, K = 128 voxels),
+//    accumulated in tensor memory over all tiles of the CTA.  The 3 -> 64
+//    and 64 -> 1 layers and the bias / small-layer gradients run on the FP32
+//    pipes.  Operands use the K-major, no-swizzle canonical layout: 8-row x
+//    16-byte core matrices, LBO = next core matrix along K, SBO = next
+//    8-row group.
+//  * FP32 reference (any GPU): the same arithmetic (same BF16 rounding
+//    points) with plain FMAs, used to cross-check the tensor-core kernels.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace cs {
+
+namespace {
+
+constexpr int kHid = 64;
+constexpr int kRows = 128;                      // voxels per tile
+constexpr int oW1 = 0, ob1 = 192, oW2 = 256, ob2 = 4352, ow3 = 4416, ob3 = 4480;
+constexpr int kNP = 4481;                        // parameters
+constexpr int kSmall = 192 + 64 + 64 + 64 + 1;  // dW1, db1, db2, dw3, db3
+constexpr long long kWaitLimit = 1ll << 26;     // bounded mbarrier waits
+
+__device__ __forceinline__ float gelu_f(float x) {
+  const float c = 0.7978845608028654f;           // sqrt(2/pi)
+  const float u = c * fmaf(0.044715f * x * x, x, x);
+  return 0.5f * x * (1.f + tanhf(u));
+}
+__device__ __forceinline__ float gelu_grad_f(float x) {
+  const float c = 0.7978845608028654f;
+  const float u = c * fmaf(0.044715f * x * x, x, x);
+  const float t = tanhf(u);
+  return 0.5f * (1.f + t) + 0.5f * x * (1.f - t * t) * c * fmaf(3.f * 0.044715f, x * x, 1.f);
+}
+__device__ __forceinline__ float bf16r(float x) {
+  return __bfloat162float(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ unsigned short bf16bits(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// features of voxel j; in_ball: |k|^2 <= r2
+__device__ __forceinline__ void features(int j, int M, const float* __restrict__ cov,
+                                         const float* __restrict__ c2w, float x[3], int r2,
+                                         bool& in_ball) {
+  const int half = M / 2;
+  const int ix = j % M, iy = (j / M) % M, iz = j / (M * M);
+  const int kx = ix - half, ky = iy - half, kz = iz - half;
+  const int q = kx * kx + ky * ky + kz * kz;
+  x[0] = sqrtf((float)q) / (float)half;
+  x[1] = log1pf(fmaxf(__ldg(cov + j), 0.f));
+  x[2] = log1pf(fmaxf(__ldg(c2w + j), 0.f));
+  in_ball = q <= r2;
+}
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// K-major, no-swizzle descriptor: start, LBO (K step), SBO (8-row step)
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;                       // descriptor version of sm_100 family
+  return d;                                     // base offset 0, no swizzle
+}
+
+// kind::f16 instruction descriptor: BF16 A and B, FP32 D, K-major A and B
+__host__ __device__ constexpr uint32_t umma_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+}
+
+// waits for phase `parity` of the barrier; false if the wait ran out
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (row, k) in a K-major canonical tile with K extent
+// kext (LBO = 128 bytes, SBO = kext/8 * 128 bytes)
+__device__ __forceinline__ uint32_t core_off(int row, int k, int kext) {
+  return (uint32_t)((row >> 3) * (kext / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 +
+                    (k & 7) * 2);
+}
+
+// ------------------------------------------------------ shared layouts
+struct FwdSmem {
+  unsigned short W2[kHid * kHid];       // B operand: rows o (N), K = i
+  unsigned short H1[kRows * kHid];      // A operand: rows = voxels, K = i
+  float W1[192], b1[64], b2[64], w3[64], b3;
+  unsigned long long bar;
+  uint32_t tmem;
+};
+
+struct GradSmem {
+  unsigned short W2[kHid * kHid];       // forward B: rows o, K = i
+  unsigned short W2T[kHid * kHid];      // backward B: rows i, K = o
+  unsigned short H1[kRows * kHid];      // forward A: rows = voxels, K = i
+  unsigned short DA[kRows * kHid];      // backward A: rows = voxels, K = o
+  unsigned short XT[128 * kRows];       // Gram operand: rows = features (dA2 | H1), K = voxels
+  float W1[192], b1[64], b2[64], w3[64], b3;
+  float small[kSmall];                  // dW1, db1, db2, dw3, db3 of this CTA
+  unsigned long long bar;
+  uint32_t tmem;
+};
+
+__device__ __forceinline__ void load_params(const float* __restrict__ p, float* W1, float* b1,
+                                            float* b2, float* w3, float* b3) {
+  for (int i = threadIdx.x; i < 192; i += blockDim.x) W1[i] = p[oW1 + i];
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+    b1[i] = p[ob1 + i];
+    b2[i] = p[ob2 + i];
+    w3[i] = p[ow3 + i];
+  }
+  if (threadIdx.x == 0) *b3 = p[ob3];
+}
+
+// ------------------------------------------------------ tensor-core kernels
+// logd[j] = MLP(features(j)) (exp_out: D = exp(logd) instead)
+__global__ void __launch_bounds__(kRows)
+k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restrict__ cov,
+                 const float* __restrict__ c2w, float* __restrict__ out, int exp_out,
+                 int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  FwdSmem& S = *reinterpret_cast<FwdSmem*>(smem_raw);
+  const int t = threadIdx.x, warp = t >> 5;
+  const int n = M * M * M;
+  const int n_tiles = (n + kRows - 1) / kRows;
+  load_params(params, S.W1, S.b1, S.b2, S.w3, &S.b3);
+  for (int e = t; e < kHid * kHid; e += kRows) {
+    const int o = e / kHid, i = e % kHid;
+    *reinterpret_cast<unsigned short*>(reinterpret_cast<unsigned char*>(S.W2) +
+                                       core_off(o, i, kHid)) = bf16bits(params[oW2 + e]);
+  }
+  if (t == 0) bar_init(smem_u32(&S.bar));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;"
+                 :: "r"(smem_u32(&S.tmem)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = S.tmem;
+  const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t bar = smem_u32(&S.bar);
+  const uint32_t idesc = umma_idesc(128, 64);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    const int j = tile * kRows + t;
+    float x[3] = {0.f, 0.f, 0.f};
+    bool inb = false;
+    if (j < n) features(j, M, cov, c2w, x, 0x7fffffff, inb);
+    unsigned char* H1b = reinterpret_cast<unsigned char*>(S.H1);
+#pragma unroll 8
+    for (int i = 0; i < kHid; ++i) {
+      const float a = fmaf(S.W1[3 * i + 2], x[2], fmaf(S.W1[3 * i + 1], x[1],
+                                                       fmaf(S.W1[3 * i], x[0], S.b1[i])));
+      *reinterpret_cast<unsigned short*>(H1b + core_off(t, i, kHid)) = bf16bits(gelu_f(a));
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (t == 0) {
+      fence_after();
+      const uint32_t aB = smem_u32(S.H1), bB = smem_u32(S.W2);
+#pragma unroll
+      for (int kc = 0; kc < kHid / 16; ++kc)
+        mma_bf16(tmem, umma_desc(aB + 256 * kc, 128, 1024), umma_desc(bB + 256 * kc, 128, 1024),
+                 idesc, kc > 0);
+      mma_commit(bar);
+    }
+    ok = __syncthreads_and(bar_wait(bar, phase)) != 0;
+    phase ^= 1u;
+    fence_after();
+    if (!ok) break;
+    float y = S.b3;
+#pragma unroll
+    for (int c = 0; c < kHid; c += 16) {
+      float a2[16];
+      tmem_ld16(lane_addr + c, a2);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) y = fmaf(S.w3[c + u], gelu_f(a2[u] + S.b2[c + u]), y);
+    }
+    if (j < n) out[j] = exp_out ? expf(y) : y;
+    fence_before();
+    __syncthreads();
+  }
+  if (!ok && t == 0) atomicExch(err, 1);
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" :: "r"(tmem));
+  }
+}
+
+// Gradient of L = (1/n_ball) sum_{|k| <= r} (y_j - target_j)^2 (accumulated
+// into grad with atomics), and the sum of squared residuals into *sse.
+__global__ void __launch_bounds__(kRows)
+k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
+              const float* __restrict__ cov, const float* __restrict__ c2w,
+              const float* __restrict__ target, float* __restrict__ grad, double* __restrict__ sse,
+              int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  GradSmem& S = *reinterpret_cast<GradSmem*>(smem_raw);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int n = M * M * M;
+  const int n_tiles = (n + kRows - 1) / kRows;
+  load_params(params, S.W1, S.b1, S.b2, S.w3, &S.b3);
+  for (int e = t; e < kHid * kHid; e += kRows) {
+    const int o = e / kHid, i = e % kHid;
+    const unsigned short w = bf16bits(params[oW2 + e]);
+    *reinterpret_cast<unsigned short*>(reinterpret_cast<unsigned char*>(S.W2) +
+                                       core_off(o, i, kHid)) = w;
+    *reinterpret_cast<unsigned short*>(reinterpret_cast<unsigned char*>(S.W2T) +
+                                       core_off(i, o, kHid)) = w;
+  }
+  for (int i = t; i < kSmall; i += kRows) S.small[i] = 0.f;
+  if (t == 0) bar_init(smem_u32(&S.bar));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
+                 :: "r"(smem_u32(&S.tmem)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = S.tmem;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t d1 = tmem, d2 = tmem + 64, d3 = tmem + 128;   // TMEM columns
+  const uint32_t bar = smem_u32(&S.bar);
+  const uint32_t idesc64 = umma_idesc(128, 64), idesc128 = umma_idesc(128, 128);
+  uint32_t phase = 0;
+  bool ok = true;
+  int tiles_done = 0;
+  double my_sse = 0.0;
+  unsigned char* H1b = reinterpret_cast<unsigned char*>(S.H1);
+  unsigned char* DAb = reinterpret_cast<unsigned char*>(S.DA);
+  unsigned char* XTb = reinterpret_cast<unsigned char*>(S.XT);
+  for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    const int j = tile * kRows + t;
+    float x[3] = {0.f, 0.f, 0.f};
+    bool inb = false;
+    if (j < n) features(j, M, cov, c2w, x, r2, inb);
+    // ---- forward, layer 1 -> smem (A of the forward MMA, rows 64.. of X^T)
+#pragma unroll 8
+    for (int i = 0; i < kHid; ++i) {
+      const float a = fmaf(S.W1[3 * i + 2], x[2], fmaf(S.W1[3 * i + 1], x[1],
+                                                       fmaf(S.W1[3 * i], x[0], S.b1[i])));
+      const unsigned short hb = bf16bits(gelu_f(a));
+      *reinterpret_cast<unsigned short*>(H1b + core_off(t, i, kHid)) = hb;
+      *reinterpret_cast<unsigned short*>(XTb + core_off(64 + i, t, kRows)) = hb;
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (t == 0) {
+      fence_after();
+      const uint32_t aB = smem_u32(S.H1), bB = smem_u32(S.W2);
+#pragma unroll
+      for (int kc = 0; kc < kHid / 16; ++kc)
+        mma_bf16(d1, umma_desc(aB + 256 * kc, 128, 1024), umma_desc(bB + 256 * kc, 128, 1024),
+                 idesc64, kc > 0);
+      mma_commit(bar);
+    }
+    ok = __syncthreads_and(bar_wait(bar, phase)) != 0;
+    phase ^= 1u;
+    fence_after();
+    if (!ok) break;
+    // ---- forward, layers 2-3, loss, backward through layer 3
+    float y = S.b3;
+    float a2[kHid];
+#pragma unroll
+    for (int c = 0; c < kHid; c += 16) tmem_ld16(d1 + lane_off + c, a2 + c);
+#pragma unroll
+    for (int o = 0; o < kHid; ++o) {
+      a2[o] += S.b2[o];
+      y = fmaf(S.w3[o], gelu_f(a2[o]), y);
+    }
+    const float r = inb ? y - __ldg(target + j) : 0.f;
+    my_sse += (double)r * r;
+    const float dy = 2.f * r * inv_n;
+    float acc_db3 = dy;
+    // dA2 -> smem (A of the backward MMA, rows 0..63 of X^T); dw3, db2
+#pragma unroll
+    for (int o = 0; o < kHid; ++o) {
+      const float h2 = gelu_f(a2[o]);
+      const float da = dy * S.w3[o] * gelu_grad_f(a2[o]);
+      const unsigned short db = bf16bits(da);
+      *reinterpret_cast<unsigned short*>(DAb + core_off(t, o, kHid)) = db;
+      *reinterpret_cast<unsigned short*>(XTb + core_off(o, t, kRows)) = db;
+      float v1 = dy * h2, v2 = da;
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) {
+        v1 += __shfl_xor_sync(0xffffffffu, v1, s);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, s);
+      }
+      if (lane == 0) {
+        atomicAdd(&S.small[192 + 64 + 64 + o], v1);   // dw3
+        atomicAdd(&S.small[192 + 64 + o], v2);        // db2
+      }
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) acc_db3 += __shfl_xor_sync(0xffffffffu, acc_db3, s);
+    if (lane == 0) atomicAdd(&S.small[kSmall - 1], acc_db3);
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (t == 0) {
+      fence_after();
+      const uint32_t aB = smem_u32(S.DA), bB = smem_u32(S.W2T), xB = smem_u32(S.XT);
+#pragma unroll
+      for (int kc = 0; kc < kHid / 16; ++kc)
+        mma_bf16(d2, umma_desc(aB + 256 * kc, 128, 1024), umma_desc(bB + 256 * kc, 128, 1024),
+                 idesc64, kc > 0);
+#pragma unroll
+      for (int kc = 0; kc < kRows / 16; ++kc)
+        mma_bf16(d3, umma_desc(xB + 256 * kc, 128, 2048), umma_desc(xB + 256 * kc, 128, 2048),
+                 idesc128, (tiles_done > 0 || kc > 0) ? 1u : 0u);
+      mma_commit(bar);
+    }
+    ok = __syncthreads_and(bar_wait(bar, phase)) != 0;
+    phase ^= 1u;
+    fence_after();
+    if (!ok) break;
+    ++tiles_done;
+    // ---- backward through layer 1: dA1 = dH1 * gelu'(A1); dW1, db1
+#pragma unroll
+    for (int c = 0; c < kHid; c += 16) {
+      float dh[16];
+      tmem_ld16(d2 + lane_off + c, dh);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int i = c + u;
+        const float a = fmaf(S.W1[3 * i + 2], x[2], fmaf(S.W1[3 * i + 1], x[1],
+                                                         fmaf(S.W1[3 * i], x[0], S.b1[i])));
+        const float da1 = dh[u] * gelu_grad_f(a);
+        float g0 = da1 * x[0], g1 = da1 * x[1], g2 = da1 * x[2], gb = da1;
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+          g0 += __shfl_xor_sync(0xffffffffu, g0, s);
+          g1 += __shfl_xor_sync(0xffffffffu, g1, s);
+          g2 += __shfl_xor_sync(0xffffffffu, g2, s);
+          gb += __shfl_xor_sync(0xffffffffu, gb, s);
+        }
+        if (lane == 0) {
+          atomicAdd(&S.small[3 * i], g0);
+          atomicAdd(&S.small[3 * i + 1], g1);
+          atomicAdd(&S.small[3 * i + 2], g2);
+          atomicAdd(&S.small[192 + i], gb);
+        }
+      }
+    }
+    fence_before();
+    __syncthreads();
+  }
+  if (!ok && t == 0) atomicExch(err, 1);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  // dW2 = rows 0..63 (dA2 features), columns 64..127 (H1 features) of the Gram
+  if (ok && tiles_done > 0 && t < 64) {
+#pragma unroll
+    for (int c = 0; c < kHid; c += 16) {
+      float gv[16];
+      tmem_ld16(d3 + lane_off + 64 + c, gv);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) atomicAdd(grad + oW2 + t * kHid + c + u, gv[u]);
+    }
+  }
+  __syncthreads();
+  for (int i = t; i < kSmall; i += kRows) {
+    const float v = S.small[i];
+    int dst;
+    if (i < 192) dst = oW1 + i;
+    else if (i < 256) dst = ob1 + (i - 192);
+    else if (i < 320) dst = ob2 + (i - 256);
+    else if (i < 384) dst = ow3 + (i - 320);
+    else dst = ob3;
+    atomicAdd(grad + dst, v);
+  }
+  double s = block_sum(my_sse);
+  if (t == 0) atomicAdd(sse, s);
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem));
+  }
+}
+
+// ------------------------------------------------------ FP32 reference kernels
+__global__ void __launch_bounds__(128)
+k_mlp_forward_ref(int M, const float* __restrict__ params, const float* __restrict__ cov,
+                  const float* __restrict__ c2w, float* __restrict__ out, int exp_out) {
+  __shared__ float W1[192], b1[64], W2[kHid * kHid], b2[64], w3[64], b3;
+  load_params(params, W1, b1, b2, w3, &b3);
+  for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) W2[e] = bf16r(params[oW2 + e]);
+  __syncthreads();
+  const int n = M * M * M;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    float x[3];
+    bool inb;
+    features(j, M, cov, c2w, x, 0x7fffffff, inb);
+    float h1[kHid];
+#pragma unroll
+    for (int i = 0; i < kHid; ++i)
+      h1[i] = bf16r(gelu_f(fmaf(W1[3 * i + 2], x[2], fmaf(W1[3 * i + 1], x[1],
+                                                          fmaf(W1[3 * i], x[0], b1[i])))));
+    float y = b3;
+    for (int o = 0; o < kHid; ++o) {
+      float a = 0.f;
+#pragma unroll
+      for (int i = 0; i < kHid; ++i) a = fmaf(W2[o * kHid + i], h1[i], a);
+      y = fmaf(w3[o], gelu_f(a + b2[o]), y);
+    }
+    out[j] = exp_out ? expf(y) : y;
+  }
+}
+
+__global__ void __launch_bounds__(128)
+k_mlp_grad_ref(int M, int r2, float inv_n, const float* __restrict__ params,
+               const float* __restrict__ cov, const float* __restrict__ c2w,
+               const float* __restrict__ target, float* __restrict__ grad,
+               double* __restrict__ sse) {
+  __shared__ float W1[192], b1[64], b2[64], w3[64], b3;
+  __shared__ float small[kSmall];
+  extern __shared__ float dyn[];
+  float* W2 = dyn;                                            // [64][64]
+  float (*H1s)[kHid + 1] = reinterpret_cast<float (*)[kHid + 1]>(dyn + kHid * kHid);
+  float (*DAs)[kHid + 1] = reinterpret_cast<float (*)[kHid + 1]>(dyn + kHid * kHid +
+                                                                 kRows * (kHid + 1));
+  load_params(params, W1, b1, b2, w3, &b3);
+  for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) W2[e] = bf16r(params[oW2 + e]);
+  for (int i = threadIdx.x; i < kSmall; i += blockDim.x) small[i] = 0.f;
+  const int t = threadIdx.x;
+  // this thread's 32 outputs of dW2: entries t*32 .. t*32+31
+  float gW2[32];
+#pragma unroll
+  for (int u = 0; u < 32; ++u) gW2[u] = 0.f;
+  double my_sse = 0.0;
+  __syncthreads();
+  const int n = M * M * M;
+  const int n_tiles = (n + kRows - 1) / kRows;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int j = tile * kRows + t;
+    float x[3] = {0.f, 0.f, 0.f};
+    bool inb = false;
+    if (j < n) features(j, M, cov, c2w, x, r2, inb);
+    float h1[kHid];
+#pragma unroll
+    for (int i = 0; i < kHid; ++i) {
+      h1[i] = bf16r(gelu_f(fmaf(W1[3 * i + 2], x[2], fmaf(W1[3 * i + 1], x[1],
+                                                          fmaf(W1[3 * i], x[0], b1[i])))));
+      H1s[t][i] = h1[i];
+    }
+    float a2[kHid];
+    float y = b3;
+    for (int o = 0; o < kHid; ++o) {
+      float a = 0.f;
+#pragma unroll
+      for (int i = 0; i < kHid; ++i) a = fmaf(W2[o * kHid + i], h1[i], a);
+      a2[o] = a + b2[o];
+      y = fmaf(w3[o], gelu_f(a2[o]), y);
+    }
+    const float r = inb ? y - target[j] : 0.f;
+    my_sse += (double)r * r;
+    const float dy = 2.f * r * inv_n;
+    atomicAdd(&small[kSmall - 1], dy);
+    for (int o = 0; o < kHid; ++o) {
+      const float da = dy * w3[o] * gelu_grad_f(a2[o]);
+      DAs[t][o] = bf16r(da);
+      atomicAdd(&small[320 + o], dy * gelu_f(a2[o]));
+      atomicAdd(&small[256 + o], da);
+    }
+    // dH1 = bf(dA2) W2, then dA1
+    for (int i = 0; i < kHid; ++i) {
+      float dh = 0.f;
+      for (int o = 0; o < kHid; ++o) dh = fmaf(DAs[t][o], W2[o * kHid + i], dh);
+      const float a = fmaf(W1[3 * i + 2], x[2], fmaf(W1[3 * i + 1], x[1],
+                                                     fmaf(W1[3 * i], x[0], b1[i])));
+      const float da1 = dh * gelu_grad_f(a);
+      atomicAdd(&small[3 * i], da1 * x[0]);
+      atomicAdd(&small[3 * i + 1], da1 * x[1]);
+      atomicAdd(&small[3 * i + 2], da1 * x[2]);
+      atomicAdd(&small[192 + i], da1);
+    }
+    __syncthreads();
+    // dW2[o][i] += sum_v bf(dA2)[v][o] bf(H1)[v][i], outputs t*32..t*32+31
+#pragma unroll 4
+    for (int u = 0; u < 32; ++u) {
+      const int e = t * 32 + u, o = e / kHid, i = e % kHid;
+      float s = 0.f;
+      for (int v = 0; v < kRows; ++v) s = fmaf(DAs[v][o], H1s[v][i], s);
+      gW2[u] += s;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 32; ++u) atomicAdd(grad + oW2 + t * 32 + u, gW2[u]);
+  __syncthreads();
+  for (int i = t; i < kSmall; i += blockDim.x) {
+    int dst;
+    if (i < 192) dst = oW1 + i;
+    else if (i < 256) dst = ob1 + (i - 192);
+    else if (i < 320) dst = ob2 + (i - 256);
+    else if (i < 384) dst = ow3 + (i - 320);
+    else dst = ob3;
+    atomicAdd(grad + dst, small[i]);
+  }
+  double s = block_sum(my_sse);
+  if (t == 0) atomicAdd(sse, s);
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 master parameters; grad is zeroed.
+__global__ void k_adam(int np, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                       float* __restrict__ g, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
+    const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    g[i] = 0.f;
+  }
+}
+
+}  // namespace
+
+size_t mlp_fwd_smem() { return sizeof(FwdSmem); }
+size_t mlp_grad_smem() { return sizeof(GradSmem); }
+
+cudaError_t launch_mlp_forward(int M, const float* params, const float* cov, const float* c2w,
+                               float* out, int exp_out, bool tc, int* err, int num_sms,
+                               cudaStream_t s) {
+  const int n = M * M * M;
+  if (!tc) {
+    const int g = (n + 127) / 128;
+    k_mlp_forward_ref<<<g < num_sms * 16 ? g : num_sms * 16, 128, 0, s>>>(M, params, cov, c2w,
+                                                                         out, exp_out);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_tc,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(FwdSmem));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int tiles = (n + kRows - 1) / kRows;
+  const int g = tiles < num_sms * 4 ? tiles : num_sms * 4;
+  k_mlp_forward_tc<<<g, kRows, sizeof(FwdSmem), s>>>(M, params, cov, c2w, out, exp_out, err);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_grad(int M, int r2, float inv_n, const float* params, const float* cov,
+                            const float* c2w, const float* target, float* grad, double* sse,
+                            bool tc, int* err, int num_sms, cudaStream_t s) {
+  const int n = M * M * M;
+  const int tiles = (n + kRows - 1) / kRows;
+  if (!tc) {
+    const size_t dyn = sizeof(float) * (kHid * kHid + 2 * kRows * (kHid + 1));
+    static bool configured_ref = false;
+    if (!configured_ref) {
+      cudaError_t e = cudaFuncSetAttribute(k_mlp_grad_ref,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      if (e != cudaSuccess) return e;
+      configured_ref = true;
+    }
+    const int g = tiles < num_sms * 2 ? tiles : num_sms * 2;
+    k_mlp_grad_ref<<<g, kRows, dyn, s>>>(M, r2, inv_n, params, cov, c2w, target, grad, sse);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(GradSmem));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  // two CTAs per SM: 2 x 256 TMEM columns, the whole tensor memory
+  const int g = tiles < num_sms * 2 ? tiles : num_sms * 2;
+  k_mlp_grad_tc<<<g, kRows, sizeof(GradSmem), s>>>(M, r2, inv_n, params, cov, c2w, target, grad,
+                                                   sse, err);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, float* m, float* v, float* g, int step, float lr, float b1,
+                        float b2, float eps, cudaStream_t s) {
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  k_adam<<<(kNP + 255) / 256, 256, 0, s>>>(kNP, p, m, v, g, lr, b1, b2, eps, c1, c2);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace cs

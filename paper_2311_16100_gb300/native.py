@@ -47,6 +47,7 @@ class CsProblem(ctypes.Structure):
 
 
 CS_MAX_PROBLEMS = 8
+CS_MLP_NPARAMS = 4481
 
 P = c_void_p
 G = POINTER(CsGeom)
@@ -84,6 +85,10 @@ SIGNATURES = {
     "cs_graph_destroy": (c_int, [P]),
     "cs_set_launch_shape": (c_int, [P, c_int, c_int]),
     "cs_autotune": (c_int, [P, POINTER(CsProblem), c_int, POINTER(c_int), POINTER(c_int)]),
+    "cs_mlp_forward": (c_int, [P, c_int, P, P, P, P, c_int, c_int, P]),
+    "cs_mlp_grad": (c_int, [P, c_int, c_int, P, P, P, P, P, P, c_int, P]),
+    "cs_mlp_adam_step": (c_int, [P, P, P, P, P, c_int, c_float, c_float, c_float, c_float, P]),
+    "cs_check_device_status": (c_int, [P]),
 }
 
 _lib = None

@@ -281,6 +281,35 @@ class Handle:
                                                         ctypes.byref(bt), ctypes.byref(bps)))
         return bt.value, bps.value
 
+    # ------------------------------------------- learned preconditioner
+    def mlp_forward(self, M, params, coverage, ctf2w, out=None, exp=False, tensor_cores=True,
+                    stream=None):
+        if out is None:
+            out = torch.empty((M, M, M), dtype=torch.float32, device=params.device)
+        self._check("cs_mlp_forward", self.lib.cs_mlp_forward(
+            self.h, M, _ptr(params, torch.float32, "params"),
+            _ptr(coverage, torch.float32, "coverage"), _ptr(ctf2w, torch.float32, "ctf2w"),
+            _ptr(out, torch.float32, "out"), int(exp), int(tensor_cores), _stream(stream)))
+        return out
+
+    def mlp_grad(self, M, r_ball, params, coverage, ctf2w, target, grad, sse,
+                 tensor_cores=True, stream=None):
+        self._check("cs_mlp_grad", self.lib.cs_mlp_grad(
+            self.h, M, int(r_ball), _ptr(params, torch.float32, "params"),
+            _ptr(coverage, torch.float32, "coverage"), _ptr(ctf2w, torch.float32, "ctf2w"),
+            _ptr(target, torch.float32, "target"), _ptr(grad, torch.float32, "grad"),
+            _ptr(sse, torch.float64, "sse"), int(tensor_cores), _stream(stream)))
+
+    def mlp_adam_step(self, params, m, v, grad, step, lr=1e-2, beta1=0.9, beta2=0.999,
+                      eps=1e-8, stream=None):
+        self._check("cs_mlp_adam_step", self.lib.cs_mlp_adam_step(
+            self.h, _ptr(params, torch.float32, "params"), _ptr(m, torch.float32, "m"),
+            _ptr(v, torch.float32, "v"), _ptr(grad, torch.float32, "grad"), int(step),
+            float(lr), float(beta1), float(beta2), float(eps), _stream(stream)))
+
+    def check_device_status(self):
+        self._check("cs_check_device_status", self.lib.cs_check_device_status(self.h))
+
     def rel_err(self, geom: Geometry, v, v_ref, out=None, stream=None):
         if out is None:
             out = torch.empty((), dtype=torch.float64, device=v.device)
