@@ -55,6 +55,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-metric2", action="store_true",
                    help="skip the time-to-relative-error runs (plain vs preconditioned)")
+    p.add_argument("--mlp-only", action="store_true",
+                   help="only time the learned-preconditioner network kernels at 128^3")
+    p.add_argument("--no-learned", action="store_true",
+                   help="skip the learned-preconditioner leg")
     p.add_argument("--no-multi", action="store_true",
                    help="skip the multi-volume graph-replay throughput")
     p.add_argument("--cpu-sample", type=int, default=128,
@@ -365,58 +369,62 @@ TTE_CONFIGS = {
 THRESHOLDS = [0.5, 0.3, 0.2, 0.15, 0.1, 0.05, 0.02, 0.01]
 
 
-def time_to_error(cfg, torch, ops, synth, h):
-    """Wall (device) time of Algorithm 1 to reach relative volume errors,
-    plain SGD vs Hutchinson-preconditioned, both with the Armijo rule.  The
-    ground truth v* solves H v = b on the whole dataset (closed form under
-    nearest interpolation, conjugate gradients with the library's gradient
-    otherwise); the error is evaluated after every step outside the timing."""
-    M, B = cfg["M"], cfg["B"]
+def ground_truth(h, torch, synth, W, cfg, lam):
+    """v* solving H v = b over the whole dataset: closed form under nearest
+    interpolation, conjugate gradients with the library's gradient otherwise."""
+    M = cfg["M"]
     r = M // 2 - 1
-    W = build_workload(dict(cfg, n_img=cfg["n_img"]), 0, h, torch, ops, synth)
-    geom, images, quat, df, n_img = W["geom"], W["images"], W["quat"], W["df"], W["n_img"]
+    geom, images, quat, df = W["geom"], W["images"], W["quat"], W["df"]
     dfa = df if W["ctf"] else None
-    lam = W["sigma2"]
     rot_all = h.quat_to_rot(quat)
     b = h.backproject_adjoint(geom, images, rot_all, dfa, 1.0)
     ball = torch.from_numpy(synth.ball_mask(M, r)).cuda()
     if cfg["interp"] == "nearest":
         d, _, _ = h.exact_diag(geom, rot_all, dfa, lam, 1.0)
-        vstar = torch.where(ball, b / d, torch.zeros_like(b))
-    else:   # CG on H v = b, H x = loss_grad(x) with zero images
-        zeros = torch.zeros_like(images)
-        x = torch.zeros_like(b)
-        rr = b.clone()
-        pp = rr.clone()
-        rs = float(torch.sum(torch.abs(rr) ** 2))
-        bn = rs ** 0.5
-        for _ in range(500):
-            _, Hp = h.loss_grad(geom, pp, zeros, rot_all, dfa, lam, 1.0)
-            a = rs / float(torch.sum((torch.conj(pp) * Hp).real))
-            x += a * pp
-            rr -= a * Hp
-            rs_new = float(torch.sum(torch.abs(rr) ** 2))
-            if rs_new ** 0.5 <= 1e-6 * bn:
-                break
-            pp = rr + (rs_new / rs) * pp
-            rs = rs_new
-        del zeros
-        vstar = torch.where(ball, x, torch.zeros_like(x))
-    alpha = h.threshold_alpha(geom, dfa, n_img, lam)
+        return torch.where(ball, b / d, torch.zeros_like(b)), rot_all
+    zeros = torch.zeros_like(images)
+    x = torch.zeros_like(b)
+    rr = b.clone()
+    pp = rr.clone()
+    rs = float(torch.sum(torch.abs(rr) ** 2))
+    bn = rs ** 0.5
+    for _ in range(500):
+        _, Hp = h.loss_grad(geom, pp, zeros, rot_all, dfa, lam, 1.0)
+        a = rs / float(torch.sum((torch.conj(pp) * Hp).real))
+        x += a * pp
+        rr -= a * Hp
+        rs_new = float(torch.sum(torch.abs(rr) ** 2))
+        if rs_new ** 0.5 <= 1e-6 * bn:
+            break
+        pp = rr + (rs_new / rs) * pp
+        rs = rs_new
+    del zeros
+    return torch.where(ball, x, torch.zeros_like(x)), rot_all
+
+
+def sgd_arms(h, torch, ops, synth, W, cfg, vstar, lam, arms, epochs):
+    """Algorithm 1 from the same start for each arm ({name: (mode, D)}):
+    device time of the steps to reach each relative error (evaluated after
+    every step outside the timing), and the Fourier shell correlation with
+    v* after every epoch at a low, a middle and a high shell."""
+    M, B = cfg["M"], cfg["B"]
+    r = M // 2 - 1
+    geom, images, quat, df, n_img = W["geom"], W["images"], W["quat"], W["df"], W["n_img"]
+    alpha = h.threshold_alpha(geom, df if W["ctf"] else None, n_img, lam)
     v0 = torch.from_numpy(synth.initial_volume(M, r, 1.0, cfg["seed"] + 7)).cuda()
     scale = n_img / B
-    out = {"workload": f"{M}^3, {n_img} images, batch {B}, {cfg['epochs']} epochs, "
-                       f"{cfg['interp']}, {'CTF' if cfg['df'] else 'no CTF'}, {cfg['K']} probes",
-           "lambda": lam}
-    for mode in ("plain", "hutchinson"):
+    out = {}
+    for name, (mode, D) in arms.items():
         st = ops.SGDState(v0, mode=mode, alpha=alpha, eta0=1.0, beta=0.9, armijo_c=0.5,
-                          n_probes=cfg["K"], seed=cfg["seed"] + 11)
+                          n_probes=cfg["K"], seed=cfg["seed"] + 11, D=D)
         err = h.rel_err(geom, st.v, vstar)
         first = {t: None for t in THRESHOLDS}
         t_ms = 0.0
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         rot = torch.empty((B, 3, 3), dtype=torch.float32, device="cuda")
-        for ep in range(cfg["epochs"]):
+        shells = (M // 16, M // 4, M // 2 - 2)
+        fsc_ep = {str(r_): [] for r_ in shells}
+        for ep in range(epochs):
             perm = torch.from_numpy(synth.permutation(n_img, cfg["seed"] + 31 + ep)).cuda()
             im_p, q_p = images[perm].contiguous(), quat[perm].contiguous()
             df_p = df[perm].contiguous() if W["ctf"] else None
@@ -435,11 +443,238 @@ def time_to_error(cfg, torch, ops, synth, h):
                 for t in THRESHOLDS:
                     if first[t] is None and e <= t:
                         first[t] = round(t_ms, 3)
-        out[mode] = {"ms_to_rel_err": {str(t): first[t] for t in THRESHOLDS},
+            del im_p, q_p, df_p
+            f, _ = h.fsc(st.v, vstar, M // 2)          # Eq. fsc against v*, per epoch
+            f = f.cpu().numpy()
+            for r_ in shells:
+                fsc_ep[str(r_)].append(round(float(f[r_]), 4))
+        below = [r_ for r_ in range(1, M // 2) if f[r_] < 0.5]
+        out[name] = {"ms_to_rel_err": {str(t): first[t] for t in THRESHOLDS},
                      "reached_1e-2": first[0.01] is not None,
                      "final_rel_err": round(float(err), 5), "total_ms": round(t_ms, 3),
-                     "final_eta": float(st.scalars[0])}
+                     "final_eta": float(st.scalars[0]),
+                     "fsc_by_epoch_at_shell": fsc_ep,
+                     "first_shell_fsc_below_0.5": below[0] if below else None}
     return out
+
+
+def time_to_error(cfg, torch, ops, synth, h):
+    """Wall (device) time of Algorithm 1 to reach relative volume errors,
+    plain SGD vs Hutchinson-preconditioned, both with the Armijo rule."""
+    W = build_workload(dict(cfg, n_img=cfg["n_img"]), 0, h, torch, ops, synth)
+    lam = W["sigma2"]
+    vstar, rot_all = ground_truth(h, torch, synth, W, cfg, lam)
+    D_pre, pre = precomputed(h, torch, W, rot_all, cfg, lam)
+    out = {"workload": f"{cfg['M']}^3, {W['n_img']} images, batch {cfg['B']}, "
+                       f"{cfg['epochs']} epochs, {cfg['interp']}, "
+                       f"{'CTF' if cfg['df'] else 'no CTF'}, {cfg['K']} probes", "lambda": lam,
+           "precomputed_setup": pre}
+    out.update(sgd_arms(h, torch, ops, synth, W, cfg, vstar, lam,
+                        {"plain": ("plain", None), "precomputed": ("fixed", D_pre),
+                         "hutchinson": ("hutchinson", None)},
+                        cfg["epochs"]))
+    return out
+
+
+def precomputed(h, torch, W, rot_all, cfg, lam):
+    """Section 4's precomputed preconditioner: Eq. diag est rule over
+    ceil(1000/K) epochs of K-probe batch estimates (as many probe draws per
+    image as the paper's 1000 single-probe epochs)."""
+    epochs = -(-1000 // cfg["K"])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    D = h.precompute_preconditioner(W["geom"], rot_all, W["df"] if W["ctf"] else None,
+                                    B=cfg["B"], n_epochs=epochs, lam=lam, n_probes=cfg["K"],
+                                    seed=cfg["seed"] + 13)
+    e1.record()
+    torch.cuda.synchronize()
+    return D, {"epochs": epochs, "probes_per_batch": cfg["K"], "ms": round(e0.elapsed_time(e1), 3)}
+
+
+def mlp_kernels(h, torch, M, r, params, cov, c2w, target):
+    """Device time of the network's forward (inference over the M^3 grid) and
+    gradient kernels, tensor-core and FP32 reference, and the forward's
+    tensor roofline.  Algorithmic FLOPs per voxel: forward 2 (3*64 + 64*64 +
+    64) = 8704; gradient adds the 64 x 64 backward product and the weight
+    Gram product (2 * 2 * 64*64) and the small layers (2 * (3*64 + 64*3)),
+    25,472 in all; both kernels process every voxel of the grid."""
+    dev = params.device
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out_buf = torch.empty((M, M, M), device=dev)
+    res = {}
+    for tc in (True, False):
+        for _ in range(3):
+            h.mlp_forward(M, params, cov, c2w, out=out_buf, tensor_cores=tc)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(10):
+            h.mlp_forward(M, params, cov, c2w, out=out_buf, tensor_cores=tc)
+        e1.record()
+        torch.cuda.synchronize()
+        fwd = e0.elapsed_time(e1) / 10
+        g = torch.zeros_like(params)
+        sse = torch.zeros((), dtype=torch.float64, device=dev)
+        for _ in range(3):
+            h.mlp_grad(M, r, params, cov, c2w, target, g, sse, tc)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(10):
+            h.mlp_grad(M, r, params, cov, c2w, target, g, sse, tc)
+        e1.record()
+        torch.cuda.synchronize()
+        grd = e0.elapsed_time(e1) / 10
+        res["tensor_cores" if tc else "fp32_reference"] = {"forward_ms": round(fwd, 4),
+                                                           "gradient_ms": round(grd, 4)}
+    h.check_device_status()
+    nvox = M ** 3
+    peaks, src = measured_peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    fwd_flops = nvox * 2 * (3 * 64 + 64 * 64 + 64)
+    grad_flops = nvox * 2 * (3 * 64 + 3 * 64 * 64 + 64 + 64 * 3)
+    tcf = res["tensor_cores"]
+    ach = fwd_flops / (tcf["forward_ms"] / 1e3) / 1e12
+    ach_g = grad_flops / (tcf["gradient_ms"] / 1e3) / 1e12
+    roof = {"bound": "tensor", "kernel": "k_mlp_forward_tc", "achieved": round(ach, 2),
+            "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 5),
+            "peak_source": src, "flops_per_launch": fwd_flops,
+            "gradient": {"kernel": "k_mlp_grad_tc", "achieved": round(ach_g, 2),
+                         "frac": round(ach_g / peak, 5), "flops_per_launch": grad_flops}}
+    return res, roof
+
+
+def mlp_only(args):
+    """Only the network kernels at 128^3 on seeded features (random weights)."""
+    import torch
+    from paper_2311_16100_gb300 import ops
+    from paper_2311_16100_gb300.learned import init_params
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    h = ops.Handle(0)
+    M, r = 128, 63
+    g = torch.Generator(device="cpu")
+    g.manual_seed(4242)
+    cov = (torch.rand((M, M, M), generator=g) * 400).to(dev)
+    c2w = (torch.rand((M, M, M), generator=g) * 200).to(dev)
+    target = torch.randn((M, M, M), generator=g).to(dev)
+    params = torch.from_numpy(init_params(7)).to(dev)
+    res, roof = mlp_kernels(h, torch, M, r, params, cov, c2w, target)
+    print(json.dumps({"workload": "learned-preconditioner network, 128^3 voxels",
+                      "kernels": res, "roofline": roof}), flush=True)
+    h.close()
+
+
+def learned_leg(args, torch, ops, synth):
+    """The learned preconditioner: trained on Hutchinson estimates from 8
+    seeded 128^3 pose sets (50k poses each, defocus U[0.5, 3.5] um), its
+    kernels timed against the tensor roofline, its D compared with the exact
+    diagonal, and SGD preconditioned by it raced against Algorithm 1 and
+    plain SGD on the benchmark's dataset."""
+    from paper_2311_16100_gb300.learned import (LearnedPreconditioner, Sample, dataset_features,
+                                                hutchinson_target)
+    h = ops.Handle(torch.cuda.current_device())
+    M, r = 128, 63
+    geom = ops.Geometry(M, r, "trilinear", ops.CTF())
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.perf_counter()
+    samples = []
+    for s_ in range(8):
+        q = torch.from_numpy(synth.shoemake_quaternions(50000, 8000 + 10 * s_)
+                             .astype("float32")).to(dev)
+        rot = h.quat_to_rot(q)
+        df = torch.from_numpy(synth.defocus_angstrom(50000, 8001 + 10 * s_, 0.5, 3.5)
+                              .astype("float32")).to(dev)
+        cov, c2w = dataset_features(h, geom, rot, df)
+        samples.append(Sample(M, r, cov, c2w, hutchinson_target(h, geom, rot, df)))
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = LearnedPreconditioner(h, seed=1)
+    t0 = time.perf_counter()
+    hist = net.fit(samples, steps=300, lr=1e-2)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    s0 = samples[0]
+    res, mlp_roof = mlp_kernels(h, torch, M, r, net.params, s0.coverage, s0.ctf2w, s0.target)
+    # the benchmark's dataset: D from the network (one pose-only feature pass
+    # and one inference) vs the exact diagonal, then the SGD race
+    cfg = dict(CONFIGS["m128"], epochs=10)
+    W = build_workload(cfg, 0, h, torch, ops, synth)
+    lam = W["sigma2"]
+    vstar, rot_all = ground_truth(h, torch, synth, W, cfg, lam)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    cov, c2w = dataset_features(h, geom, rot_all, W["df"])
+    D_learned = net.predict(M, cov, c2w, lam)
+    e1.record()
+    torch.cuda.synchronize()
+    setup_learned = e0.elapsed_time(e1)
+    e0.record()
+    exact, _, _ = h.exact_diag(geom, rot_all, W["df"], lam, 1.0)
+    e1.record()
+    torch.cuda.synchronize()
+    setup_exact = e0.elapsed_time(e1)
+    ball = torch.from_numpy(synth.ball_mask(M, r)).to(dev)
+    rel = lambda a, b: float(torch.linalg.vector_norm((a - b)[ball]) /
+                             torch.linalg.vector_norm(b[ball]))
+    per = len(samples) * samples[0].n_ball
+    out = {"training": {"datasets": "8 x 50000 poses, 128^3, defocus U[0.5,3.5] um",
+                        "targets": "log of Hutchinson estimates, 4 x 32 probes",
+                        "adam_steps": len(hist), "mse_first": hist[0] / per,
+                        "mse_last": hist[-1] / per,
+                        "data_s": round(t_data, 3), "train_s": round(t_train, 3)},
+           "kernels_128cubed": res, "roofline": mlp_roof,
+           "D_rel_err_vs_exact": round(rel(D_learned, exact), 4),
+           "setup_ms": {"learned": round(setup_learned, 3),
+                        "exact_diagonal_control": round(setup_exact, 3)}}
+    D_pre, pre = precomputed(h, torch, W, rot_all, cfg, lam)
+    out["setup_ms"]["precomputed"] = pre["ms"]
+    out["D_rel_err_vs_exact_precomputed"] = round(rel(D_pre, exact), 4)
+    arms = {"plain": ("plain", None), "precomputed": ("fixed", D_pre),
+            "hutchinson": ("hutchinson", None), "learned": ("fixed", D_learned),
+            "exact_diagonal_control": ("fixed", exact)}
+    out["time_to_rel_err"] = sgd_arms(h, torch, ops, synth, W, cfg, vstar, lam, arms,
+                                      cfg["epochs"])
+    out["time_to_rel_err"]["workload"] = (f"128^3, {W['n_img']} images, batch 1024, 10 epochs, "
+                                          "trilinear, CTF, 32 probes")
+    del W
+    h.close()
+    return out
+
+
+def conditioning(args, torch, ops, synth):
+    """Section 3.1's conditioning analysis: kappa of diag(H) over the ball of
+    radius R (nearest interpolation, no CTF, so H is diagonal) for N = 10000
+    uniform poses and lam = 1e-8, against the lower bound of Eq. cond number
+    p, R = 1, 17, 33, ... on a 512^3 grid."""
+    import numpy as np
+    h = ops.Handle(torch.cuda.current_device())
+    M, N, lam = 512, 10000, 1e-8
+    geom = ops.Geometry(M, M // 2 - 1, "nearest", None)
+    q = torch.from_numpy(synth.shoemake_quaternions(N, 9100).astype("float32")).cuda()
+    rot = h.quat_to_rot(q)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    d, _, _ = h.exact_diag(geom, rot, None, lam, 1.0)
+    lo, hi, cnt = h.shell_minmax(d, M // 2)
+    e1.record()
+    torch.cuda.synchronize()
+    lo, hi, cnt = lo.cpu().numpy(), hi.cpu().numpy(), cnt.cpu().numpy()
+    k = np.arange(M) - M // 2
+    q2 = k[:, None] ** 2 + k[None, :] ** 2
+    n2 = np.bincount(np.rint(np.sqrt(q2)).astype(int).ravel(), minlength=M)[: M // 2]
+    radii = list(range(1, M // 2 - 1, 16))
+    rows = []
+    for R in radii:
+        kap = float(np.max(hi[: R + 1]) / np.min(lo[: R + 1]))
+        p = float(np.sum(n2[: R + 1]) / np.sum(cnt[: R + 1]))
+        bound = (N + lam) / (p * N + lam) if 1 / p <= N else None
+        rows.append({"R": R, "kappa": kap, "lower_bound": bound})
+    del d
+    h.close()
+    return {"workload": f"{M}^3 grid, {N} uniform poses, nearest, no CTF, lambda {lam}",
+            "ms": round(e0.elapsed_time(e1), 3), "by_radius": rows}
 
 
 def multi_volume(args, torch, ops, synth):
@@ -587,6 +822,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, cfg, rank, world)
         return
+    if args.mlp_only:
+        mlp_only(args)
+        return
     import torch
     import torch.distributed as dist
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -613,6 +851,12 @@ def main():
             line["time_to_rel_err"] = {k: time_to_error(c, torch, ops, synth, h2)
                                        for k, c in TTE_CONFIGS.items()}
             h2.close()
+        if world == 1 and not args.no_learned:
+            from paper_2311_16100_gb300 import ops, synth
+            line["learned_preconditioner"] = learned_leg(args, torch, ops, synth)
+        if world == 1 and not args.no_metric2:
+            from paper_2311_16100_gb300 import ops, synth
+            line["conditioning"] = conditioning(args, torch, ops, synth)
         if world == 1 and not args.no_multi:
             from paper_2311_16100_gb300 import ops, synth
             line["multi_volume"] = multi_volume(args, torch, ops, synth)

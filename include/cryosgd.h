@@ -178,6 +178,26 @@ int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
                        int n_probes, uint64_t seed, uint64_t probe_block,
                        float* diag_out, void* stream);
 
+/* Precomputed preconditioner (Section 4, the comparison arm that estimates
+ * the diagonal in advance with Eq. diag est rule before SGD starts):
+ *   for epoch e = 1..n_epochs, for batch b = 1..ceil(N/B) (images b*B ..
+ *   b*B + |I_b| - 1 in the given order, the last batch possibly short):
+ *     k = k + 1,  est = cs_hutchinson_diag(batch, lambda, scale = N/|I_b|,
+ *                                          n_probes, seed, probe_block = k),
+ *     D_out = ((k-1)/k) D_out + (1/k) est.
+ * rot_all float[N][9] and defocus_all float[N] (NULL without CTF) cover the
+ * whole dataset; D_out float[M^3] is overwritten (its previous contents are
+ * never read).  Probe blocks 1..n_epochs*ceil(N/B) are used, so the result
+ * averages n_epochs * ceil(N/B) * n_probes probes; its expectation is the
+ * diagonal of the full-data Hessian (plus lambda) when B divides N.  Errors:
+ * CS_ERR_SHAPE for N, B or n_epochs < 1, n_probes outside [1, 32], or more
+ * than 2^31 - 1 iterations; CS_ERR_ARG for NULL pointers or non-finite
+ * lambda. */
+int cs_precompute_preconditioner(cs_handle* h, const cs_geom* g, const float* rot_all,
+                                 const float* defocus_all, int N, int B, int n_epochs,
+                                 float lambda, int n_probes, uint64_t seed, float* D_out,
+                                 void* stream);
+
 /* Hutchinson's diagonal estimate without device allocation.  The paper has
  * no counterpart: this is a deployment variant of cs_hutchinson_diag for
  * callers that cannot allocate device memory when they need the estimate
@@ -390,6 +410,44 @@ int cs_mlp_adam_step(cs_handle* h, float* params, float* m, float* v, float* gra
  * device-side wait ran out since the last check (CS_ERR_TIMEOUT, and the
  * word is cleared) or not (CS_OK). */
 int cs_check_device_status(cs_handle* h);
+
+/* In-plane shift operator T_i of Definition 2.1 (a diagonal phase):
+ *   images[i][y][x] *= T_i(k)      (sign = +1)
+ *   images[i][y][x] *= conj T_i(k) (sign = -1),
+ *   T_i(k) = exp(-2 pi i (kx tx_i + ky ty_i) / M),  k = (x, y) - M/2,
+ * i.e. a real-space shift of image i by +(tx_i, ty_i) pixels.  images
+ * complex64[B][M][M] in place (all pixels); shifts float[B][2] (tx, ty),
+ * finite, |t| < 8192.  T_i is unitary and commutes with the CTF, so
+ * |x_i - C_i T_i S_i v| = |T_i^* x_i - C_i S_i v|: every operator of this
+ * library works with the unshifted slice S_i, a dataset with known shifts is
+ * corrected once with sign -1, and the shifted forward model is
+ * cs_slice_project followed by sign +1.  Errors: CS_ERR_SHAPE (M, B),
+ * CS_ERR_ARG (NULL pointers, sign not +-1). */
+int cs_phase_shift(cs_handle* h, int M, float* images, const float* shifts, int B, int sign,
+                   void* stream);
+
+/* Fourier shell correlation (Eq. fsc, Section 4) of complex volumes u, v
+ * (complex64[M][M][M], grid as above) over the shells
+ *   S_r = { k : round(|k|) = r },  r = 0 .. n_shells-1  (1 <= n_shells <= 1024;
+ * voxels beyond the last shell are ignored):
+ *   sums[r] = (Re sum_{S_r} u conj(v), sum_{S_r} |u|^2, sum_{S_r} |v|^2)
+ * (device double[n_shells][3], overwritten) and, if fsc is not NULL,
+ *   fsc[r] = sums[r][0] / sqrt(sums[r][1] sums[r][2])  (0 for an empty or
+ * all-zero shell; device double[n_shells]).  The real part is reported: it
+ * is the whole value for Hermitian-symmetric volumes.  Sums are FP64 with
+ * atomics, so the last bits may vary between runs. */
+int cs_fsc(cs_handle* h, int M, const float* u, const float* v, int n_shells, double* sums,
+           double* fsc, void* stream);
+
+/* Per-shell statistics of a real field x (float[M][M][M], finite values),
+ * shells as in cs_fsc: count_out[r] = |S_r| (int), min_out[r] / max_out[r] =
+ * min / max of x over S_r (float; +inf / -inf for an empty shell).  With x
+ * = diag(H) (cs_exact_diag) this gives the condition number of the
+ * diagonal restricted to the ball of radius R, max_{r <= R} max_out[r] /
+ * min_{r <= R} min_out[r] (Section 3.1, Proposition 3.1).  Exact (no
+ * rounding). */
+int cs_shell_minmax(cs_handle* h, int M, const float* x, int n_shells, float* min_out,
+                    float* max_out, int* count_out, void* stream);
 
 /* Relative error over the ball |k| <= r_max:
  *   |v - v_ref| / |v_ref| -> *out (device double). */

@@ -15,6 +15,9 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
                        exactly), identity/90-degree rotations, brute-force
                        argmin over all grid points
   ctf                  pinned: textbook electron wavelengths, CTF zeros
+  shift_phase          pinned: Fourier shift theorem (integer shifts = circular
+                       roll of the real-space image), unitarity, and the
+                       loss identity |x - C T S v| = |T* x - C S v|
   slice/adjoint        pinned: adjoint identity <Px, y> = <x, P*y>
   loss_grad            pinned: central finite differences (exact for a quadratic)
   hvp / dense H        pinned: linearity of the gradient, symmetry
@@ -23,10 +26,23 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   splitmix64           pinned: published test vector
   hutchinson_diag      pinned: exact under nearest (Remark 3.3), unbiased
                        under trilinear (z-score against the dense Hessian)
+  precomputed_preconditioner
+                       pinned: brute-force pixel counts under nearest
+                       (every probe exact, equal batches average to the
+                       full diagonal), dense-Hessian z-scores under trilinear
   alpha_threshold      pinned: shell-ratio asymptotics, shell mean of diag(H)
   alg1_step            pinned: EM M-step equivalence (nearest, exact D, eta=1),
                        monotone decrease under the Armijo rule
   cg_solve             pinned: closed form under nearest interpolation
+  diagnostics.fsc      pinned: Eq. fsc identities (1, -1, cos theta, shell
+                       locality, energy partition), independent noise ~ 0
+  diagnostics.shell_minmax / shell_index
+                       pinned: integer shell rule, Legendre's three-square
+                       theorem for the extremes of |k|^2 per shell
+  diagnostics.condition_by_radius / p_ratio / kappa_lower_bound
+                       pinned: brute-force max/min over the ball,
+                       monotonicity, Eq. cond number p, Proposition 3.1
+                       (unhit voxel => min = lam), p(R) ~ 3/(4R)
   mlp (learned preconditioner network; not in the paper)
                        pinned: BF16 rounding and GELU against torch's
                        library routines, backpropagation against central
@@ -34,12 +50,13 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
 """
 from .geometry import (ball_mask, ctf_of_s2, ctf_pixels, default_r_max, disc_mask,
                        electron_wavelength_A, freq_axis, nearest_coords_fp32,
-                       pixel_coords, quat_to_rot, sample_points, stencil)
+                       phase_shift, pixel_coords, quat_to_rot, sample_points, shift_phase,
+                       stencil)
 from .operators import (backproject_adjoint, coverage_features, dense_hessian,
                         exact_diag, hvp, loss, loss_grad, slice_project)
 from .hutchinson import hutchinson_diag, probe_words, rademacher_probes, splitmix64
-from .sgd import (alg1_step, alpha_threshold, cg_solve, full_rhs, rel_err,
-                  shell_counts)
-from . import mlp
+from .sgd import (alg1_step, alpha_threshold, cg_solve, full_rhs, precomputed_preconditioner,
+                  rel_err, shell_counts)
+from . import diagnostics, mlp
 
 __all__ = [n for n in dir() if not n.startswith("_")]

@@ -29,6 +29,24 @@ def pixel_coords(M: int):
     return kx.ravel(), ky.ravel()
 
 
+def shift_phase(M: int, shifts) -> np.ndarray:
+    """In-plane shift operators of Definition 2.1 as phases [B][M][M]:
+    T_i(k) = exp(-2 pi i (kx tx_i + ky ty_i) / M) for shifts (tx, ty) in
+    pixels (the paper gives no formula; this is the Fourier shift theorem for
+    a real-space shift by +t)."""
+    kx, ky = pixel_coords(M)
+    t = np.asarray(shifts, np.float64).reshape(-1, 2)
+    a = (kx[None, :] * t[:, :1] + ky[None, :] * t[:, 1:]) / M
+    return np.exp(-2j * np.pi * a).reshape(-1, M, M)
+
+
+def phase_shift(images, shifts, sign=-1):
+    """images * T (sign +1) or images * conj(T) (sign -1)."""
+    M = images.shape[-1]
+    T = shift_phase(M, shifts)
+    return np.asarray(images, np.complex128) * (T if sign > 0 else np.conj(T))
+
+
 def disc_mask(M: int, r_max: int) -> np.ndarray:
     """Pixels used by the model: kx^2 + ky^2 <= r_max^2 (flattened)."""
     kx, ky = pixel_coords(M)

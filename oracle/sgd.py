@@ -87,6 +87,29 @@ def alg1_step(v, D, D_avg, eta_prev, k, images, R, defocus, M, r_max, interp,
     return dict(v=v_new, D=D, D_avg=D_avg, eta=eta, halvings=h, loss=f0, G=G)
 
 
+def precomputed_preconditioner(R_all, defocus_all, M, r_max, interp, ctf, lam, B, n_epochs,
+                               n_probes, seed):
+    """The preconditioner estimated in advance (Section 4's precomputed arm):
+    Eq. diag est rule run over n_epochs passes of the dataset in batches of B
+    (the last batch may be short), each batch's Hutchinson estimate taken with
+    its own scale N/|I| (Eq. optim cp's batch reading) and probe block k = the
+    running iteration count, and averaged with the running mean
+    D = ((k-1)/k) D + (1/k) est.  Images are taken in the given order."""
+    N = R_all.shape[0]
+    D = np.zeros((M, M, M))
+    k = 0
+    for _ in range(n_epochs):
+        for start in range(0, N, B):
+            sl = slice(start, min(start + B, N))
+            nb = sl.stop - sl.start
+            k += 1
+            df = np.zeros(nb) if defocus_all is None else defocus_all[sl]
+            est = hutchinson_diag(R_all[sl], df, M, r_max, interp, ctf, lam, N / nb,
+                                  n_probes, seed, k)
+            D = ((k - 1) / k) * D + (1.0 / k) * est
+    return D
+
+
 def full_rhs(images, R, defocus, M, r_max, interp, ctf):
     """b = sum_i P_i^* C_i x_i over the whole dataset (Eq. lin sys)."""
     return backproject_adjoint(images, R, defocus, M, r_max, interp, ctf)

@@ -1,6 +1,7 @@
 // C ABI of libcryosgd (declared in include/cryosgd.h): handle, workspace,
 // host-side argument validation and the stream-ordered composition of the
 // kernels into the calls of the paper's problem statement.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdlib>
@@ -508,6 +509,50 @@ int cs_hvp(cs_handle* h, const cs_geom* g, const float* z, const float* rot,
   return CS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Enqueues one Hutchinson estimate of a validated batch into `out`
+// (workspace already sized for M and B).
+int hutch_enqueue(cs_handle* h, const cs_geom* g, const Workspace& w, const float* rot,
+                  const float* defocus, int B, float lambda, float scale, int n_probes,
+                  uint64_t seed, uint64_t probe_block, float* out, cudaStream_t s) {
+  Geo G = make_geo(*g);
+  if (use_vector(h, g) && B > 0) {
+    const int grid = vec_grid(h, B, g->M);
+    CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
+    CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
+    CS_CUDA(launch_fused(F_HUTCH, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
+                         nullptr, nullptr, seed, probe_block, nullptr, n_probes, grid, s, h->block),
+            "hutchinson launch");
+    CS_CUDA(launch_combine_r4(g->M, w.fw, lambda, 0.0f, nullptr, out, h->num_sms, s),
+            "combine launch");
+    return CS_OK;
+  }
+  if (g->interp == CS_TRILINEAR)
+    CS_CUDA(launch_probe_bits(g->M, seed, probe_block, nullptr, w.bits, h->num_sms, s),
+            "probe_bits launch");
+  if (!use_tiles(h) || B == 0) {
+    CS_CUDA(launch_hutchinson(G, w.bits, rot, defocus, B, lambda, scale, n_probes, out,
+                              pixel_grid(h->num_sms, B, g->M), h->num_sms, s),
+            "hutchinson launch");
+    return CS_OK;
+  }
+  CS_CUDA(launch_fill(g->M * g->M * g->M, lambda, out, h->num_sms, s), "fill launch");
+  TileArgs A;
+  CS_CUDA(bin_batch(h, G, w, rot, defocus, B, scale, A, s), "binning launch");
+  A.src = w.bits;
+  A.dst = out;
+  A.K = n_probes;
+  CS_CUDA(launch_tile_op(OP_HUTCH, A, h->num_sms, s), "hutchinson tile launch");
+  return CS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
                        const float* defocus, int B, float lambda, float scale,
                        int n_probes, uint64_t seed, uint64_t probe_block, float* diag_out,
@@ -522,35 +567,43 @@ int cs_hutchinson_diag(cs_handle* h, const cs_geom* g, const float* rot,
   CS_SCOPE(h);
   Workspace w;
   CS_TRY(ensure_ws(h, g->M, B, &w));
-  Geo G = make_geo(*g);
+  return hutch_enqueue(h, g, w, rot, defocus, B, lambda, scale, n_probes, seed, probe_block,
+                       diag_out, S(stream));
+}
+
+int cs_precompute_preconditioner(cs_handle* h, const cs_geom* g, const float* rot_all,
+                                 const float* defocus_all, int N, int B, int n_epochs,
+                                 float lambda, int n_probes, uint64_t seed, float* D_out,
+                                 void* stream) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_geom(h, g));
+  if (N < 1 || B < 1 || n_epochs < 1)
+    return fail(h, CS_ERR_SHAPE, "N=%d, B=%d and n_epochs=%d must be positive", N, B, n_epochs);
+  CS_TRY(check_batch(h, g, B, rot_all, defocus_all));
+  if (!is_finite(lambda)) return fail(h, CS_ERR_ARG, "lambda not finite");
+  if (n_probes < 1 || n_probes > 32)
+    return fail(h, CS_ERR_SHAPE, "n_probes=%d must be in [1, 32]", n_probes);
+  if (!D_out) return fail(h, CS_ERR_ARG, "D_out is NULL");
+  const long n_batches = ((long)N + B - 1) / B;
+  if (n_batches * n_epochs > 0x7fffffffL)
+    return fail(h, CS_ERR_SHAPE, "n_epochs=%d too large for %ld batches", n_epochs, n_batches);
+  CS_SCOPE(h);
+  Workspace w;
+  CS_TRY(ensure_ws(h, g->M, B, &w));
   cudaStream_t s = S(stream);
-  if (use_vector(h, g) && B > 0) {
-    const int grid = vec_grid(h, B, g->M);
-    CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
-    CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
-    CS_CUDA(launch_fused(F_HUTCH, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
-                         nullptr, nullptr, seed, probe_block, nullptr, n_probes, grid, s, h->block),
-            "hutchinson launch");
-    CS_CUDA(launch_combine_r4(g->M, w.fw, lambda, 0.0f, nullptr, diag_out, h->num_sms, s),
-            "combine launch");
-    return CS_OK;
-  }
-  if (g->interp == CS_TRILINEAR)
-    CS_CUDA(launch_probe_bits(g->M, seed, probe_block, nullptr, w.bits, h->num_sms, s),
-            "probe_bits launch");
-  if (!use_tiles(h) || B == 0) {
-    CS_CUDA(launch_hutchinson(G, w.bits, rot, defocus, B, lambda, scale, n_probes, diag_out,
-                              pixel_grid(h->num_sms, B, g->M), h->num_sms, s),
-            "hutchinson launch");
-    return CS_OK;
-  }
-  CS_CUDA(launch_fill(g->M * g->M * g->M, lambda, diag_out, h->num_sms, s), "fill launch");
-  TileArgs A;
-  CS_CUDA(bin_batch(h, G, w, rot, defocus, B, scale, A, s), "binning launch");
-  A.src = w.bits;
-  A.dst = diag_out;
-  A.K = n_probes;
-  CS_CUDA(launch_tile_op(OP_HUTCH, A, h->num_sms, s), "hutchinson tile launch");
+  const int n = g->M * g->M * g->M;
+  long k = 0;
+  for (int e = 0; e < n_epochs; ++e)
+    for (long b = 0; b < n_batches; ++b) {
+      ++k;
+      const int Bb = (int)std::min<long>(B, N - b * B);
+      const float scale = (float)((double)N / Bb);
+      CS_TRY(hutch_enqueue(h, g, w, rot_all + 9 * b * B,
+                           defocus_all ? defocus_all + b * B : nullptr, Bb, lambda, scale,
+                           n_probes, seed, (uint64_t)k, w.dest, s));
+      CS_CUDA(launch_running_mean(n, w.dest, D_out, k, h->num_sms, s),
+              "running-mean launch");
+    }
   return CS_OK;
 }
 
@@ -1189,6 +1242,53 @@ int cs_autotune(cs_handle* h, const cs_problem* probs, int n, int* block_out, in
   h->blocks_per_sm = pick.bps;
   if (block_out) *block_out = pick.block;
   if (bps_out) *bps_out = pick.bps;
+  return CS_OK;
+}
+
+int cs_phase_shift(cs_handle* h, int M, float* images, const float* shifts, int B, int sign,
+                   void* stream) {
+  if (!h) return CS_ERR_ARG;
+  if (M < 4 || M > CS_MAX_M || (M & 1))
+    return fail(h, CS_ERR_SHAPE, "M=%d must be even and in [4, %d]", M, CS_MAX_M);
+  if (B < 0) return fail(h, CS_ERR_SHAPE, "batch size B=%d is negative", B);
+  if (sign != 1 && sign != -1) return fail(h, CS_ERR_ARG, "sign=%d must be +1 or -1", sign);
+  if (B == 0) return CS_OK;
+  if (!images || !shifts) return fail(h, CS_ERR_ARG, "images or shifts is NULL");
+  CS_SCOPE(h);
+  CS_CUDA(launch_phase_shift(M, B, reinterpret_cast<float2*>(images), shifts, sign, h->num_sms,
+                             S(stream)),
+          "phase shift launch");
+  return CS_OK;
+}
+
+int cs_fsc(cs_handle* h, int M, const float* u, const float* v, int n_shells, double* sums,
+           double* fsc, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  if (M < 4 || M > CS_MAX_M || (M & 1))
+    return fail(h, CS_ERR_SHAPE, "M=%d must be even and in [4, %d]", M, CS_MAX_M);
+  if (n_shells < 1 || n_shells > kMaxShells)
+    return fail(h, CS_ERR_SHAPE, "n_shells=%d must be in [1, %d]", n_shells, kMaxShells);
+  if (!u || !v || !sums) return fail(h, CS_ERR_ARG, "u, v or sums is NULL");
+  CS_SCOPE(h);
+  CS_CUDA(launch_fsc(M, reinterpret_cast<const float2*>(u), reinterpret_cast<const float2*>(v),
+                     n_shells, sums, fsc, h->num_sms, S(stream)),
+          "fsc launch");
+  return CS_OK;
+}
+
+int cs_shell_minmax(cs_handle* h, int M, const float* x, int n_shells, float* min_out,
+                    float* max_out, int* count_out, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  if (M < 4 || M > CS_MAX_M || (M & 1))
+    return fail(h, CS_ERR_SHAPE, "M=%d must be even and in [4, %d]", M, CS_MAX_M);
+  if (n_shells < 1 || n_shells > kMaxShells)
+    return fail(h, CS_ERR_SHAPE, "n_shells=%d must be in [1, %d]", n_shells, kMaxShells);
+  if (!x || !min_out || !max_out || !count_out)
+    return fail(h, CS_ERR_ARG, "x, min_out, max_out or count_out is NULL");
+  CS_SCOPE(h);
+  CS_CUDA(launch_shell_minmax(M, x, n_shells, min_out, max_out, count_out, h->num_sms,
+                              S(stream)),
+          "shell min/max launch");
   return CS_OK;
 }
 

@@ -127,6 +127,9 @@ cudaError_t launch_alpha(const Geo& G, const float* df, int N, double px_over_pv
 cudaError_t launch_precond_update(int n, const float* dest, float* D, float* Davg,
                                   float* dhat, const double* scalars, float beta,
                                   int num_sms, cudaStream_t s);
+// D = ((k-1)/k) D + (1/k) est (D = est at k = 1, whatever D held).
+cudaError_t launch_running_mean(int n, const float* est, float* D, long k, int num_sms,
+                                cudaStream_t s);
 cudaError_t launch_fixed_dhat(int n, const float* D, float* dhat, const double* scalars,
                               int num_sms, cudaStream_t s);
 // d = g / dhat (dhat NULL: d = g); part[0..gb) <- sum |g|^2/dhat,
@@ -159,6 +162,15 @@ cudaError_t launch_adam(float* p, float* m, float* v, float* g, int step, float 
 // Rate of 16-byte global reductions (G ops/s) measured on a scratch buffer.
 cudaError_t measure_red_rate(void* scratch, size_t bytes, int num_sms, cudaStream_t s,
                              double* gops);
+// In-plane shift phase (shifts.cu): images[i] *= T_i (sign +1) or T_i^* (-1).
+cudaError_t launch_phase_shift(int M, int B, float2* images, const float* shifts, int sign,
+                               int num_sms, cudaStream_t s);
+// Per-shell reductions (shells.cu); n_sh <= kMaxShells.
+constexpr int kMaxShells = 1024;
+cudaError_t launch_fsc(int M, const float2* u, const float2* v, int n_sh, double* sums,
+                       double* fsc, int num_sms, cudaStream_t s);
+cudaError_t launch_shell_minmax(int M, const float* x, int n_sh, float* lo, float* hi, int* count,
+                                int num_sms, cudaStream_t s);
 cudaError_t launch_rel_err(const Geo& G, const float2* v, const float2* vref,
                            double* part, double* out, int num_sms, cudaStream_t s);
 

@@ -81,6 +81,15 @@ k_fixed_dhat(int n, const float* __restrict__ D, float* __restrict__ dhat,
     dhat[j] = fmaxf(fabsf(D[j]), alpha);
 }
 
+// Running mean of the k-th estimate (Eq. diag est rule); at k = 1 the
+// estimate is copied so that D's previous contents never leak in.
+__global__ void __launch_bounds__(kBlock)
+k_running_mean(int n, const float* __restrict__ est, float* __restrict__ D, float a, float b,
+               int first) {
+  for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock)
+    D[j] = first ? est[j] : a * D[j] + b * est[j];
+}
+
 __global__ void __launch_bounds__(kBlock)
 k_direction(int n, const float2* __restrict__ g, const float* __restrict__ dhat,
             float2* __restrict__ d, double* __restrict__ part) {
@@ -222,6 +231,15 @@ cudaError_t launch_precond_update(int n, const float* dest, float* D, float* Dav
                                   int num_sms, cudaStream_t s) {
   k_precond_update<<<elem_grid(n, num_sms), kBlock, 0, s>>>(n, dest, D, Davg, dhat,
                                                             scalars, beta);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_running_mean(int n, const float* est, float* D, long k, int num_sms,
+                                cudaStream_t s) {
+  const double kd = (double)k;
+  k_running_mean<<<elem_grid(n, num_sms), kBlock, 0, s>>>(n, est, D, (float)((kd - 1.0) / kd),
+                                                          (float)(1.0 / kd), k == 1);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -70,6 +70,11 @@ SIGNATURES = {
                                    c_uint64, P, P]),
     "cs_hutchinson_diag_noalloc": (c_int, [G, P, P, c_int, c_float, c_float, c_int, c_uint64,
                                            c_uint64, P, P]),
+    "cs_precompute_preconditioner": (c_int, [P, G, P, P, c_int, c_int, c_int, c_float, c_int,
+                                             c_uint64, P, P]),
+    "cs_phase_shift": (c_int, [P, c_int, P, P, c_int, c_int, P]),
+    "cs_fsc": (c_int, [P, c_int, P, P, c_int, P, P, P]),
+    "cs_shell_minmax": (c_int, [P, c_int, P, c_int, P, P, P, P]),
     "cs_exact_diag": (c_int, [P, G, P, P, c_int, c_float, c_float, P, P, P, P]),
     "cs_threshold_alpha": (c_int, [P, G, P, c_int, c_double, c_double, P, P]),
     "cs_precond_sgd_step": (c_int, [P, G, POINTER(CsSgdState), P, P, P, c_int, c_float,

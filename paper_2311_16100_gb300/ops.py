@@ -198,6 +198,20 @@ class Handle:
             _stream(stream)))
         return out
 
+    def precompute_preconditioner(self, geom: Geometry, rot_all, defocus_all=None, B=1024,
+                                  n_epochs=1, lam=0.0, n_probes=32, seed=0, out=None,
+                                  stream=None):
+        N = rot_all.shape[0]
+        M = geom.M
+        if out is None:
+            out = torch.empty((M, M, M), dtype=torch.float32, device=rot_all.device)
+        self._check("cs_precompute_preconditioner", self.lib.cs_precompute_preconditioner(
+            self.h, geom.c, _ptr(rot_all, torch.float32, "rot_all"),
+            _ptr(defocus_all, torch.float32, "defocus_all"), N, int(B), int(n_epochs),
+            float(lam), int(n_probes), int(seed), _ptr(out, torch.float32, "D_out"),
+            _stream(stream)))
+        return out
+
     def exact_diag(self, geom: Geometry, rot, defocus=None, lam=0.0, scale=1.0,
                    diag=True, coverage=False, ctf2w=False, stream=None):
         B = rot.shape[0]
@@ -309,6 +323,42 @@ class Handle:
 
     def check_device_status(self):
         self._check("cs_check_device_status", self.lib.cs_check_device_status(self.h))
+
+    def phase_shift(self, images, shifts, sign=-1, stream=None):
+        """In place: images[i] *= T_i (sign +1) or conj(T_i) (sign -1)."""
+        B, M = images.shape[0], images.shape[1]
+        self._check("cs_phase_shift", self.lib.cs_phase_shift(
+            self.h, M, _ptr(images, torch.complex64, "images"),
+            _ptr(shifts, torch.float32, "shifts"), B, int(sign), _stream(stream)))
+        return images
+
+    def fsc(self, u, v, n_shells=None, stream=None):
+        """Fourier shell correlation per shell; returns (fsc, sums) as device
+        double tensors [n_shells] and [n_shells][3]."""
+        M = u.shape[0]
+        if n_shells is None:
+            n_shells = M // 2
+        sums = torch.empty((n_shells, 3), dtype=torch.float64, device=u.device)
+        f = torch.empty(n_shells, dtype=torch.float64, device=u.device)
+        self._check("cs_fsc", self.lib.cs_fsc(
+            self.h, M, _ptr(u, torch.complex64, "u"), _ptr(v, torch.complex64, "v"),
+            int(n_shells), _ptr(sums, torch.float64, "sums"), _ptr(f, torch.float64, "fsc"),
+            _stream(stream)))
+        return f, sums
+
+    def shell_minmax(self, x, n_shells=None, stream=None):
+        """Per-shell (min, max, count) of a real field [M][M][M]."""
+        M = x.shape[0]
+        if n_shells is None:
+            n_shells = M // 2
+        lo = torch.empty(n_shells, dtype=torch.float32, device=x.device)
+        hi = torch.empty(n_shells, dtype=torch.float32, device=x.device)
+        cnt = torch.empty(n_shells, dtype=torch.int32, device=x.device)
+        self._check("cs_shell_minmax", self.lib.cs_shell_minmax(
+            self.h, M, _ptr(x, torch.float32, "x"), int(n_shells),
+            _ptr(lo, torch.float32, "min_out"), _ptr(hi, torch.float32, "max_out"),
+            _ptr(cnt, torch.int32, "count_out"), _stream(stream)))
+        return lo, hi, cnt
 
     def rel_err(self, geom: Geometry, v, v_ref, out=None, stream=None):
         if out is None:

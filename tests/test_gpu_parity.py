@@ -190,6 +190,32 @@ def test_hutchinson_equals_exact_diag_under_nearest(h):
     assert rel_l2(hd, ed) <= 1e-6
 
 
+@pytest.mark.parametrize("interp", ["nearest", "trilinear"])
+def test_precompute_preconditioner(h, interp):
+    """Section 4's precomputed arm: running mean of batch estimates over
+    epochs, a short last batch with its own scale, probe block = iteration."""
+    c = Case(24, 20, interp=interp, ctf=True, seed=29)
+    g = c.to_gpu()
+    lam = 0.05
+    D = torch.full((24, 24, 24), float("nan"), device="cuda")   # never read
+    h.precompute_preconditioner(c.gpu_geometry(), g["rot"], g["df"], B=8, n_epochs=2, lam=lam,
+                                n_probes=4, seed=77, out=D)
+    want = O.precomputed_preconditioner(c.R, c.df, c.M, c.r_max, c.interp, c.ctf, lam, 8, 2, 4,
+                                        seed=77)
+    assert rel_l2(cpu(D), want) <= TOL_GRAD
+
+
+def test_precompute_preconditioner_rejects_bad_arguments(h):
+    from paper_2311_16100_gb300.ops import CryoSGDError
+    c = Case(16, 4, seed=31)
+    g = c.to_gpu()
+    for kw in (dict(B=0), dict(n_epochs=0), dict(n_probes=33)):
+        args = dict(B=2, n_epochs=1, n_probes=4)
+        args.update(kw)
+        with pytest.raises(CryoSGDError):
+            h.precompute_preconditioner(c.gpu_geometry(), g["rot"], g["df"], **args)
+
+
 def test_threshold_alpha(h):
     for ctf in (False, True):
         c = Case(64, 300, ctf=ctf, seed=23)

@@ -345,6 +345,104 @@ def test_hutchinson_unbiased_under_trilinear():
     np.testing.assert_allclose(est[~used], np.diag(H)[~used], rtol=1e-12)
 
 
+def nearest_counts(R, M):
+    """(image, pixel) pairs per voxel whose nearest grid point it is, by
+    exhaustive argmin over the grid (Definition 2.1 literally)."""
+    h = M // 2
+    k = np.arange(M) - h
+    kz, ky3, kx3 = np.meshgrid(k, k, k, indexing="ij")
+    grid = np.stack([kx3.ravel(), ky3.ravel(), kz.ravel()], axis=1).astype(np.float64)
+    count = np.zeros(M ** 3)
+    kx, ky = O.pixel_coords(M)
+    m = O.disc_mask(M, h - 1)
+    for i in range(R.shape[0]):
+        pts = (R[i].astype(np.float64).T @ np.stack([kx[m], ky[m], 0 * kx[m]])).T
+        for t in pts:
+            count[np.argmin(np.sum((grid - t) ** 2, axis=1))] += 1
+    return count
+
+
+def test_precomputed_preconditioner_nearest_is_the_full_diagonal():
+    """Section 4's precomputed arm under nearest, no CTF: each probe gives a
+    batch's diagonal exactly (Remark 3.3) and equal batches scaled by N/B
+    average to the full-data diagonal |Omega_j| + lam, whatever the epochs."""
+    M, N, B = 8, 6, 2
+    R = rots(N, 40)
+    lam = 1e-3
+    want = nearest_counts(R, M) + lam
+    for epochs in (1, 3):
+        got = O.precomputed_preconditioner(R, None, M, M // 2 - 1, "nearest", None, lam, B,
+                                           epochs, 1, seed=3).ravel()
+        np.testing.assert_allclose(got, want, rtol=1e-12)
+    # a short last batch carries scale N/|I_last|: batches {0..3} and {4, 5}
+    c1, c2 = nearest_counts(R[:4], M), nearest_counts(R[4:], M)
+    got = O.precomputed_preconditioner(R, None, M, M // 2 - 1, "nearest", None, lam, 4, 2,
+                                       3, seed=3).ravel()
+    np.testing.assert_allclose(got, 0.5 * (lam + 1.5 * c1) + 0.5 * (lam + 3.0 * c2),
+                               rtol=1e-12)
+
+
+def test_precomputed_preconditioner_unbiased_under_trilinear():
+    """Trilinear: the average of many batch estimates is unbiased for the
+    full-data diagonal (z-scores against the dense Hessian, whose per-probe
+    variance is sum_{l != j} H_jl^2 within each batch)."""
+    M, N, B, E, K = 4, 6, 3, 16, 32
+    R = rots(N, 41)
+    df = synth.defocus_angstrom(N, 42)
+    lam = 0.1
+    H = O.dense_hessian(R, df, M, 1, "trilinear", CTF, lam, 1.0)
+    # per-batch Hessians at scale N/B, to get the estimator's variance
+    var = np.zeros(M ** 3)
+    for sl in (slice(0, 3), slice(3, 6)):
+        Hb = O.dense_hessian(R[sl], df[sl], M, 1, "trilinear", CTF, lam, N / B)
+        var += (np.sum(Hb ** 2, axis=1) - np.diag(Hb) ** 2) / K
+    n_it = E * (N // B)
+    var = var / (N // B) / n_it
+    est = O.precomputed_preconditioner(R, df, M, 1, "trilinear", CTF, lam, B, E, K,
+                                       seed=8).ravel()
+    sd = np.sqrt(var)
+    used = sd > 0
+    z = (est - np.diag(H))[used] / sd[used]
+    assert np.max(np.abs(z)) < 5.0
+    np.testing.assert_allclose(est[~used], np.diag(H)[~used], rtol=1e-12)
+
+
+# ------------------------------------------------------------- in-plane shifts
+def test_shift_phase_is_the_fourier_shift_theorem():
+    """Integer shifts: multiplying the centred spectrum by T and transforming
+    back rolls the real-space image by +t (numpy's FFT as the independent
+    reference); T is unitary, T(0) = 1 and T(a) T(b) = T(a + b)."""
+    M = 16
+    g = np.random.default_rng(5)
+    x = g.normal(size=(M, M))
+    X = np.fft.fftshift(np.fft.fft2(x))          # index M/2 holds frequency 0
+    for tx, ty in ((3, 0), (0, -5), (2, 7), (-8, 1)):
+        T = O.shift_phase(M, [(tx, ty)])[0]
+        y = np.fft.ifft2(np.fft.ifftshift(X * T)).real
+        np.testing.assert_allclose(y, np.roll(x, (ty, tx), axis=(0, 1)), atol=1e-12)
+    t1, t2 = (0.3, -1.7), (2.25, 0.5)
+    T1, T2 = O.shift_phase(M, [t1])[0], O.shift_phase(M, [t2])[0]
+    T12 = O.shift_phase(M, [(t1[0] + t2[0], t1[1] + t2[1])])[0]
+    np.testing.assert_allclose(T1 * T2, T12, atol=1e-12)
+    np.testing.assert_allclose(np.abs(T1), 1.0, rtol=1e-14)
+    assert O.shift_phase(M, [(1.3, 2.1)])[0][M // 2, M // 2] == 1.0
+
+
+def test_shifted_loss_equals_loss_on_corrected_images():
+    """|x - C T S v| = |T* x - C S v| (T unitary, diagonal, commuting with C):
+    the identity that lets the operators work with the unshifted slice."""
+    M, B = 12, 4
+    R = rots(B, 60)
+    df = synth.defocus_angstrom(B, 61)
+    v = cplx((M, M, M), 62)
+    t = np.random.default_rng(63).uniform(-4, 4, size=(B, 2))
+    x = cplx((B, M, M), 64)
+    model = O.slice_project(v, R, df, M, M // 2 - 1, "trilinear", CTF)
+    lhs = np.sum(np.abs(x - O.phase_shift(model, t, +1)) ** 2)
+    rhs = np.sum(np.abs(O.phase_shift(x, t, -1) - model) ** 2)
+    assert abs(lhs - rhs) <= 1e-12 * lhs
+
+
 # ------------------------------------------------------- threshold alpha
 def test_shell_ratio_asymptotics():
     """P_x(R)/P_v(R) ~ 2 pi R / (4 pi R^2) = 1/(2R) for 1-voxel shells (the
