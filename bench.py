@@ -59,6 +59,8 @@ def parse():
                    help="only time the learned-preconditioner network kernels at 128^3")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-preconditioner leg")
+    p.add_argument("--no-loss-grad", action="store_true",
+                   help="skip the cs_loss_grad-only throughput")
     p.add_argument("--no-multi", action="store_true",
                    help="skip the multi-volume graph-replay throughput")
     p.add_argument("--cpu-sample", type=int, default=128,
@@ -279,47 +281,48 @@ def run_gpu(args, cfg, rank, world):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t)
 
-    # --- end to end through the public API with host buffers
+    # --- end to end through the public API with host buffers: every step
+    # copies its batch from pinned host memory (cs_precond_sgd_step_host,
+    # double-buffered: the copy of batch n+1 overlaps step n) and reads the
+    # batch loss back into pinned host memory
     e2e = None
     if not args.no_e2e:
         nh = min(4, nb)
         pin_img = [images[i * B:(i + 1) * B].cpu().pin_memory() for i in range(nh)]
         pin_q = [quat[i * B:(i + 1) * B].cpu().pin_memory() for i in range(nh)]
         pin_df = [df[i * B:(i + 1) * B].cpu().pin_memory() for i in range(nh)]
-        d_img = torch.empty((B, M, M), dtype=torch.complex64, device="cuda")
-        d_q = torch.empty((B, 4), dtype=torch.float32, device="cuda")
-        d_df = torch.empty((B,), dtype=torch.float32, device="cuda")
-        out_loss = torch.empty(args.steps, dtype=torch.float64).pin_memory()
+        out_loss = torch.zeros(max(args.steps, args.warmup), dtype=torch.float64).pin_memory()
 
         def e2e_step(s, i):
             j = s % nh
-            d_img.copy_(pin_img[j], non_blocking=True)
-            d_q.copy_(pin_q[j], non_blocking=True)
-            d_df.copy_(pin_df[j], non_blocking=True)
-            h.quat_to_rot(d_q, rot)
-            h.precond_sgd_step(geom, st, d_img, rot, d_df if W["ctf"] else None, lam, scale)
-            if i >= 0:
-                out_loss[i].copy_(st.scalars[N.CS_S_LOSS], non_blocking=True)
+            h.precond_sgd_step_host(geom, st, pin_img[j], pin_q[j],
+                                    pin_df[j] if W["ctf"] else None, lam, scale,
+                                    loss_host=out_loss[i])
 
         for s in range(args.warmup):
-            e2e_step(s, -1)
+            e2e_step(s, s)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
         a0.record(stream)
         for i in range(args.steps):
             e2e_step(i, i)
         a1.record(stream)
         torch.cuda.synchronize()
+        wall = (time.perf_counter() - w0) * 1e3
         ems = a0.elapsed_time(a1)
         if world > 1:
-            t = torch.tensor([ems], dtype=torch.float64, device="cuda")
+            t = torch.tensor([ems, wall], dtype=torch.float64, device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t)
+            ems, wall = float(t[0]), float(t[1])
+        assert bool(torch.isfinite(out_loss[: args.steps]).all()) and float(out_loss[0]) != 0.0
         e2e = {"value": world * B * args.steps / (ems / 1e3), "unit": "images/s",
                "h2d_bytes_per_step": B * M * M * 8 + B * 16 + B * 4,
-               "d2h_bytes_per_step": 8}
+               "d2h_bytes_per_step": 8,
+               "host_wall_value": round(world * B * args.steps / (wall / 1e3), 1),
+               "api": "cs_precond_sgd_step_host (double-buffered staging, copy stream)"}
 
     # --- roofline of the dominant phase
     n_px = n_disc_pixels(M, M // 2 - 1)
@@ -354,8 +357,36 @@ def run_gpu(args, cfg, rank, world):
                     "frac": round(red_ach / red_peak, 4),
                     "peak_source": "measured live (cs_measure_reduction_rate)",
                     "reductions_per_launch": reds[dom]}
+    # cs_loss_grad alone (loss and gradient, no Hutchinson, no step): median
+    # over 20 passes of the per-batch time, every batch of the image set
+    lg = None
+    if not args.no_loss_grad:
+        g_buf = torch.empty_like(st.v)
+        l_buf = torch.empty((), dtype=torch.float64, device="cuda")
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(20)]
+        for _ in range(3):
+            h.loss_grad(geom, st.v, images[:B], rot, dfs(slice(0, B)), lam, scale, grad=g_buf,
+                        loss=l_buf)
+        per_pass = []
+        for i in range(20):
+            ev[i][0].record(stream)
+            for b in range(nb):
+                sl = slice(b * B, (b + 1) * B)
+                h.quat_to_rot(quat[sl], rot)
+                h.loss_grad(geom, st.v, images[sl], rot, dfs(sl), lam, scale, grad=g_buf,
+                            loss=l_buf)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        per_pass = sorted(a.elapsed_time(b_) for a, b_ in ev)
+        med = per_pass[len(per_pass) // 2]
+        lg = {"metric": "cs_loss_grad images/s (loss + gradient only)",
+              "value": round(nb * B / (med / 1e3), 1), "unit": "images/s",
+              "ms_per_pass_median": round(med, 4), "passes": 20,
+              "pass": f"{nb} batches of {B} (every image once), poses converted per batch"}
     return dict(ms=ms, launches=launches, phases={k: round(v, 4) for k, v in per.items()},
-                roofline=roof, red_roofline=red_roof, e2e=e2e, clocks=clk, scalars=sc, n_img=W["n_img"])
+                roofline=roof, red_roofline=red_roof, e2e=e2e, clocks=clk, scalars=sc, n_img=W["n_img"],
+                loss_grad_only=lg)
 
 
 # ------------------------------------------- time to relative error (metric 2)
@@ -843,6 +874,7 @@ def main():
                 "roofline": r["roofline"], "roofline_l2_reductions": r["red_roofline"],
                 "e2e": r["e2e"], "clocks": r["clocks"],
                 "gpu_launches": r["launches"], "phases_ms_per_step": r["phases"],
+                "loss_grad_only": r["loss_grad_only"],
                 "final_scalars": {"eta": r["scalars"][0], "k": r["scalars"][1],
                                   "loss": r["scalars"][3]}}
         if world == 1 and not args.no_metric2:

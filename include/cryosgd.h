@@ -286,6 +286,26 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
                         const float* defocus, int B, float lambda, float scale,
                         void* stream);
 
+/* cs_precond_sgd_step on a batch held in HOST memory: images_host
+ * complex64[B][M][M], quat_host float[B][4] (unit quaternions, w first),
+ * defocus_host float[B] (NULL without CTF).  The batch is copied into one
+ * of two device staging slots owned by the handle, on the handle's own copy
+ * stream, after the step that last used that slot has finished; the step
+ * (quaternions -> rotations, then Algorithm 1) runs on `stream` once its
+ * copy is done, and if loss_host is not NULL the batch loss is copied to
+ * *loss_host (a host double) after it.  Everything is asynchronous: the
+ * call returns at once, so issuing step n+1 while step n runs overlaps the
+ * copy of batch n+1 with the compute of step n.  Host buffers should be
+ * page-locked (pinned) for the copies to be asynchronous; they must stay
+ * valid and unmodified, and *loss_host unread, until `stream` has completed
+ * the step.  Issue all steps of one handle on one stream.  Staging grows on
+ * demand (device synchronisation, CS_ERR_ALLOC on failure).  Errors as
+ * cs_precond_sgd_step, plus CS_ERR_ARG for NULL host pointers. */
+int cs_precond_sgd_step_host(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
+                             const float* images_host, const float* quat_host,
+                             const float* defocus_host, int B, float lambda, float scale,
+                             double* loss_host, void* stream);
+
 /* Phases of cs_precond_sgd_step timed by the profiler. */
 enum {
   CS_PH_PRECOND = 0,   /* probe words, Hutchinson estimate, D update (vector

@@ -587,6 +587,61 @@ cudaError_t launch_disc_table(int M, int r, const FusedWs& w, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+namespace {
+
+template <typename K>
+int resident_of(K kernel, int block) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+int flag_slot(int flags) {
+  switch (flags) {
+    case F_ADJ: return 0;
+    case F_GRAD: return 1;
+    case F_GRAD | F_HUTCH: return 2;
+    case F_HUTCH: return 3;
+    case F_HVP: return 4;
+    case F_CURV: return 5;
+    default: return -1;
+  }
+}
+
+}  // namespace
+
+int fused_resident(int flags, int block, bool multi) {
+  // cached per (kernel, block size); every device of a process is a GB300
+  static int cache[2][6][2];
+  const int f = flag_slot(flags), b = block == 128 ? 0 : 1, m = multi ? 1 : 0;
+  if (f < 0 || (block != 128 && block != 256)) return 1;
+  int& c = cache[m][f][b];
+  if (c > 0) return c;
+  int n = 1;
+  if (!multi) {
+    switch (flags) {
+      case F_ADJ: n = resident_of(k_fused<F_ADJ>, block); break;
+      case F_GRAD: n = resident_of(k_fused<F_GRAD>, block); break;
+      case F_GRAD | F_HUTCH: n = resident_of(k_fused<F_GRAD | F_HUTCH>, block); break;
+      case F_HUTCH: n = resident_of(k_fused<F_HUTCH>, block); break;
+      case F_HVP: n = resident_of(k_fused<F_HVP>, block); break;
+      case F_CURV: n = resident_of(k_fused<F_CURV>, block); break;
+    }
+  } else {
+    switch (flags) {
+      case F_GRAD: n = resident_of(k_fused_multi<F_GRAD>, block); break;
+      case F_GRAD | F_HUTCH: n = resident_of(k_fused_multi<F_GRAD | F_HUTCH>, block); break;
+      case F_CURV: n = resident_of(k_fused_multi<F_CURV>, block); break;
+      default: n = 1;
+    }
+  }
+  c = n;
+  return n;
+}
+
 cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float* rot,
                          const float* df, int B, float scale, const float2* vol,
                          const float4* vp, const float* zr, const float2* img, double* part,

@@ -59,6 +59,10 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
                          uint64_t seed, uint64_t block_host, const double* k_dev, int K,
                          int grid, cudaStream_t s, int block = 256);
 // One launch over several problems (flags F_GRAD, F_GRAD|F_HUTCH or F_CURV).
+// Blocks of a traversal kernel (flags, block size; multi: the multi-volume
+// kernel) that fit on one SM at once.  A traversal grid larger than
+// num_sms x this would run in more than one wave, the last one part-empty.
+int fused_resident(int flags, int block, bool multi);
 cudaError_t launch_fused_multi(int flags, const MultiFusedArgs& MA, int grid, int block,
                                cudaStream_t s);
 

@@ -38,6 +38,13 @@ struct cs_handle {
   int prof_max_steps = 0;
   int prof_steps = 0;
   std::vector<cudaEvent_t> prof_events;
+  // double-buffered staging of host batches (cs_precond_sgd_step_host)
+  void* stage = nullptr;
+  int stage_M = 0, stage_B = 0;
+  unsigned long long stage_calls = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_done[2] = {nullptr, nullptr};
+  cudaEvent_t compute_done[2] = {nullptr, nullptr};
 };
 
 namespace cs {

@@ -152,6 +152,36 @@ __device__ __forceinline__ uint32_t core_off(int row, int k, int kext) {
                     (k & 7) * 2);
 }
 
+
+// eight consecutive K elements of one row of a K-major canonical tile are
+// 16 contiguous bytes: stored with one 128-bit shared-memory store
+__device__ __forceinline__ void st_bf16x8(unsigned char* base, uint32_t off, const float* v) {
+  uint4 q;
+  q.x = (uint32_t)bf16bits(v[0]) | ((uint32_t)bf16bits(v[1]) << 16);
+  q.y = (uint32_t)bf16bits(v[2]) | ((uint32_t)bf16bits(v[3]) << 16);
+  q.z = (uint32_t)bf16bits(v[4]) | ((uint32_t)bf16bits(v[5]) << 16);
+  q.w = (uint32_t)bf16bits(v[6]) | ((uint32_t)bf16bits(v[7]) << 16);
+  *reinterpret_cast<uint4*>(base + off) = q;
+}
+
+
+// Warp reduce-scatter: on return, lane l holds in v[0 .. N/32) the warp-wide
+// sums of elements l*N/32 .. (l+1)*N/32 - 1 (five butterfly rounds, each
+// lane sending the half it does not keep).  N is a multiple of 32.
+template <int N>
+__device__ __forceinline__ void warp_reduce_scatter(float (&v)[N], int lane) {
+#pragma unroll
+  for (int s = 16, L = N; s > 0; s >>= 1, L >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < L / 2; ++i) {
+      const float lo = v[i], hi = v[i + L / 2];
+      const float got = __shfl_xor_sync(0xffffffffu, up ? lo : hi, s);
+      v[i] = (up ? hi : lo) + got;
+    }
+  }
+}
+
 // ------------------------------------------------------ shared layouts
 struct FwdSmem {
   unsigned short W2[kHid * kHid];       // B operand: rows o (N), K = i
@@ -222,11 +252,16 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
     bool inb = false;
     if (j < n) features(j, M, cov, c2w, x, 0x7fffffff, inb);
     unsigned char* H1b = reinterpret_cast<unsigned char*>(S.H1);
-#pragma unroll 8
-    for (int i = 0; i < kHid; ++i) {
-      const float a = fmaf(S.W1[3 * i + 2], x[2], fmaf(S.W1[3 * i + 1], x[1],
-                                                       fmaf(S.W1[3 * i], x[0], S.b1[i])));
-      *reinterpret_cast<unsigned short*>(H1b + core_off(t, i, kHid)) = bf16bits(gelu_f(a));
+#pragma unroll 2
+    for (int i0 = 0; i0 < kHid; i0 += 8) {
+      float h[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u;
+        h[u] = gelu_f(fmaf(S.W1[3 * i + 2], x[2], fmaf(S.W1[3 * i + 1], x[1],
+                                                         fmaf(S.W1[3 * i], x[0], S.b1[i]))));
+      }
+      st_bf16x8(H1b, core_off(t, i0, kHid), h);
     }
     fence_async_smem();
     fence_before();
@@ -314,13 +349,17 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
     bool inb = false;
     if (j < n) features(j, M, cov, c2w, x, r2, inb);
     // ---- forward, layer 1 -> smem (A of the forward MMA, rows 64.. of X^T)
-#pragma unroll 8
-    for (int i = 0; i < kHid; ++i) {
-      const float a = fmaf(S.W1[3 * i + 2], x[2], fmaf(S.W1[3 * i + 1], x[1],
-                                                       fmaf(S.W1[3 * i], x[0], S.b1[i])));
-      const unsigned short hb = bf16bits(gelu_f(a));
-      *reinterpret_cast<unsigned short*>(H1b + core_off(t, i, kHid)) = hb;
-      *reinterpret_cast<unsigned short*>(XTb + core_off(64 + i, t, kRows)) = hb;
+#pragma unroll 2
+    for (int i0 = 0; i0 < kHid; i0 += 8) {
+      float h[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u;
+        h[u] = gelu_f(fmaf(S.W1[3 * i + 2], x[2], fmaf(S.W1[3 * i + 1], x[1],
+                                                         fmaf(S.W1[3 * i], x[0], S.b1[i]))));
+        *reinterpret_cast<unsigned short*>(XTb + core_off(64 + i, t, kRows)) = bf16bits(h[u]);
+      }
+      st_bf16x8(H1b, core_off(t, i0, kHid), h);
     }
     fence_async_smem();
     fence_before();
@@ -354,22 +393,22 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
     float acc_db3 = dy;
     // dA2 -> smem (A of the backward MMA, rows 0..63 of X^T); dw3, db2
 #pragma unroll
-    for (int o = 0; o < kHid; ++o) {
-      const float h2 = gelu_f(a2[o]);
-      const float da = dy * S.w3[o] * gelu_grad_f(a2[o]);
-      const unsigned short db = bf16bits(da);
-      *reinterpret_cast<unsigned short*>(DAb + core_off(t, o, kHid)) = db;
-      *reinterpret_cast<unsigned short*>(XTb + core_off(o, t, kRows)) = db;
-      float v1 = dy * h2, v2 = da;
+    for (int c = 0; c < kHid; c += 16) {
+      float v[32], dab[8];
 #pragma unroll
-      for (int s = 16; s > 0; s >>= 1) {
-        v1 += __shfl_xor_sync(0xffffffffu, v1, s);
-        v2 += __shfl_xor_sync(0xffffffffu, v2, s);
+      for (int u = 0; u < 16; ++u) {
+        const int o = c + u;
+        const float h2 = gelu_f(a2[o]);
+        const float da = dy * S.w3[o] * gelu_grad_f(a2[o]);
+        dab[u & 7] = da;
+        *reinterpret_cast<unsigned short*>(XTb + core_off(o, t, kRows)) = bf16bits(da);
+        if ((u & 7) == 7) st_bf16x8(DAb, core_off(t, o - 7, kHid), dab);
+        v[u] = dy * h2;          // dw3[o]
+        v[16 + u] = da;          // db2[o]
       }
-      if (lane == 0) {
-        atomicAdd(&S.small[192 + 64 + 64 + o], v1);   // dw3
-        atomicAdd(&S.small[192 + 64 + o], v2);        // db2
-      }
+      warp_reduce_scatter(v, lane);
+      // lane l holds element l: dw3[c + l] (l < 16) or db2[c + l - 16]
+      atomicAdd(&S.small[lane < 16 ? 192 + 64 + 64 + c + lane : 192 + 64 + c + lane - 16], v[0]);
     }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) acc_db3 += __shfl_xor_sync(0xffffffffu, acc_db3, s);
@@ -400,26 +439,25 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
     for (int c = 0; c < kHid; c += 16) {
       float dh[16];
       tmem_ld16(d2 + lane_off + c, dh);
+      // v[4u + f] = dA1 x_f (f < 3) and dA1 (f = 3) of unit c + u
+      float v[64];
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const int i = c + u;
         const float a = fmaf(S.W1[3 * i + 2], x[2], fmaf(S.W1[3 * i + 1], x[1],
                                                          fmaf(S.W1[3 * i], x[0], S.b1[i])));
         const float da1 = dh[u] * gelu_grad_f(a);
-        float g0 = da1 * x[0], g1 = da1 * x[1], g2 = da1 * x[2], gb = da1;
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) {
-          g0 += __shfl_xor_sync(0xffffffffu, g0, s);
-          g1 += __shfl_xor_sync(0xffffffffu, g1, s);
-          g2 += __shfl_xor_sync(0xffffffffu, g2, s);
-          gb += __shfl_xor_sync(0xffffffffu, gb, s);
-        }
-        if (lane == 0) {
-          atomicAdd(&S.small[3 * i], g0);
-          atomicAdd(&S.small[3 * i + 1], g1);
-          atomicAdd(&S.small[3 * i + 2], g2);
-          atomicAdd(&S.small[192 + i], gb);
-        }
+        v[4 * u] = da1 * x[0];
+        v[4 * u + 1] = da1 * x[1];
+        v[4 * u + 2] = da1 * x[2];
+        v[4 * u + 3] = da1;
+      }
+      warp_reduce_scatter(v, lane);
+      // lane l holds elements 2l and 2l+1: unit c + l/2, quantities f = 2(l%2), 2(l%2)+1
+      {
+        const int i = c + (lane >> 1), f = 2 * (lane & 1);
+        atomicAdd(&S.small[3 * i + f], v[0]);
+        atomicAdd(f == 0 ? &S.small[3 * i + 1] : &S.small[192 + i], v[1]);
       }
     }
     fence_before();

@@ -79,6 +79,8 @@ SIGNATURES = {
     "cs_threshold_alpha": (c_int, [P, G, P, c_int, c_double, c_double, P, P]),
     "cs_precond_sgd_step": (c_int, [P, G, POINTER(CsSgdState), P, P, P, c_int, c_float,
                                     c_float, P]),
+    "cs_precond_sgd_step_host": (c_int, [P, G, POINTER(CsSgdState), P, P, P, c_int, c_float,
+                                         c_float, P, P]),
     "cs_rel_err": (c_int, [P, G, P, P, P, P]),
     "cs_profile_enable": (c_int, [P, c_int, c_int]),
     "cs_profile_read": (c_int, [P, POINTER(c_double), POINTER(c_int)]),

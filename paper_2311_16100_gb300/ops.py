@@ -79,6 +79,19 @@ def _ptr(t: torch.Tensor | None, dtype=None, name="tensor"):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _hptr(t: torch.Tensor | None, dtype=None, name="tensor"):
+    """Pointer of a host tensor (page-locked for asynchronous copies)."""
+    if t is None:
+        return None
+    if t.is_cuda:
+        raise ValueError(f"{name} must be a host (CPU) tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -243,6 +256,20 @@ class Handle:
             self.h, geom.c, ctypes.byref(state.cstruct()), _ptr(images, torch.complex64, "images"),
             _ptr(rot, torch.float32, "rot"), _ptr(defocus, torch.float32, "defocus"), B,
             float(lam), float(scale), _stream(stream)))
+
+    def precond_sgd_step_host(self, geom: Geometry, state: "SGDState", images_host, quat_host,
+                              defocus_host=None, lam=0.0, scale=1.0, loss_host=None,
+                              stream=None):
+        """One step on a batch in (pinned) host memory; asynchronous: the
+        host tensors and loss_host (a host float64 element) must not be
+        touched until the stream has completed the step."""
+        B = quat_host.shape[0]
+        self._check("cs_precond_sgd_step_host", self.lib.cs_precond_sgd_step_host(
+            self.h, geom.c, ctypes.byref(state.cstruct()),
+            _hptr(images_host, torch.complex64, "images_host"),
+            _hptr(quat_host, torch.float32, "quat_host"),
+            _hptr(defocus_host, torch.float32, "defocus_host"), B, float(lam), float(scale),
+            _hptr(loss_host, torch.float64, "loss_host"), _stream(stream)))
 
     def profile_enable(self, enable=True, max_steps=4096):
         self._check("cs_profile_enable", self.lib.cs_profile_enable(self.h, int(enable),

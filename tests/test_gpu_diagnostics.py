@@ -41,10 +41,11 @@ def test_fsc_matches_oracle(h, M, n):
 def test_fsc_of_a_volume_with_itself_and_empty_shells(h):
     M = 16
     u = torch.from_numpy(cplx(M, 9)).cuda()
-    f, sums = h.fsc(u, u, 30)                     # shells 14.. are empty at M = 16
+    f, sums = h.fsc(u, u, 30)
     f = f.cpu().numpy()
-    np.testing.assert_allclose(f[:14], 1.0, rtol=1e-12)
-    assert np.all(f[14:] == 0) and np.all(sums.cpu().numpy()[14:] == 0)
+    last = int(np.rint(np.sqrt(3 * (M // 2) ** 2)))   # corner (-M/2, -M/2, -M/2): shell 14
+    np.testing.assert_allclose(f[: last + 1], 1.0, rtol=1e-12)
+    assert np.all(f[last + 1:] == 0) and np.all(sums.cpu().numpy()[last + 1:] == 0)
 
 
 @pytest.mark.parametrize("M,n", [(8, 20), (32, 16), (96, 84)])

@@ -1,0 +1,72 @@
+"""Steps fed from host memory (cs_precond_sgd_step_host): double-buffered
+staging on the handle's copy stream must give the same iterates as steps on
+device-resident batches, and the loss read back into host memory."""
+import numpy as np
+import pytest
+
+from cryo_cases import Case, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def make_state(ops, c, alpha):
+    v0 = torch.from_numpy((0.3 * c.vol).astype(np.complex64)).cuda()
+    return ops.SGDState(v0, mode="hutchinson", alpha=alpha, eta0=1.0, beta=0.9, armijo_c=0.5,
+                        n_probes=8, seed=5)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_steps_match_device_steps(pinned):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_16100_gb300 import ops
+    B, nb = 16, 3
+    c = Case(32, B * nb, interp="trilinear", ctf=True, seed=81)
+    geom = c.gpu_geometry()
+    h_dev, h_host = ops.Handle(0), ops.Handle(0)
+    g = c.to_gpu()
+    alpha = float(h_dev.threshold_alpha(geom, g["df"], B * nb, 0.01))
+    st_dev, st_host = make_state(ops, c, alpha), make_state(ops, c, alpha)
+    img = torch.from_numpy(c.images)
+    q = torch.from_numpy(c.quat.astype(np.float32))
+    df = torch.from_numpy(c.df)
+    if pinned:
+        img, q, df = img.pin_memory(), q.pin_memory(), df.pin_memory()
+    losses = torch.zeros(6, dtype=torch.float64)
+    if pinned:
+        losses = losses.pin_memory()
+    rot = torch.empty((B, 3, 3), device="cuda")
+    dev_losses = []
+    for k in range(6):
+        sl = slice((k % nb) * B, (k % nb + 1) * B)
+        h_host.precond_sgd_step_host(geom, st_host, img[sl], q[sl], df[sl], 0.01, float(nb),
+                                     loss_host=losses[k])
+        h_dev.quat_to_rot(g["quat"][sl].contiguous(), rot)
+        h_dev.precond_sgd_step(geom, st_dev, g["images"][sl].contiguous(), rot,
+                               g["df"][sl].contiguous(), 0.01, float(nb))
+        dev_losses.append(st_dev.scalars[3].clone())
+    torch.cuda.synchronize()
+    assert rel_l2(st_host.v.cpu().numpy(), st_dev.v.cpu().numpy()) <= 1e-6
+    assert float(st_host.scalars[0]) == float(st_dev.scalars[0])
+    for k in range(6):
+        assert abs(float(losses[k]) - float(dev_losses[k])) <= 1e-6 * abs(float(dev_losses[k]))
+    h_dev.close()
+    h_host.close()
+
+
+def test_host_step_rejects_bad_arguments():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_16100_gb300 import ops
+    from paper_2311_16100_gb300.ops import CryoSGDError
+    c = Case(16, 4, seed=83)
+    h = ops.Handle(0)
+    st = make_state(ops, c, 1.0)
+    img = torch.from_numpy(c.images)
+    q = torch.from_numpy(c.quat.astype(np.float32))
+    with pytest.raises(CryoSGDError):          # CTF enabled, defocus missing
+        h.precond_sgd_step_host(c.gpu_geometry(), st, img, q, None, 0.01, 1.0)
+    with pytest.raises(ValueError):            # device tensor where host memory is required
+        h.precond_sgd_step_host(c.gpu_geometry(), st, img.cuda(), q, None, 0.01, 1.0)
+    h.close()
