@@ -188,6 +188,28 @@ class ClockSampler:
                 "samples": len(self.samples), "source": "nvml"}
 
 
+# ------------------------------------------------------- replicas (N > 1)
+def replica_seed(cfg, rank):
+    """Each rank runs an independent replica on its own seeded dataset."""
+    return cfg["seed"] + 100 * rank
+
+
+def max_over_ranks(values, world, device="cuda"):
+    """Element-wise maximum over ranks (the slowest replica sets the time)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_value(world, batch, steps, ms):
+    """Whole-job throughput: images processed by all ranks / the max time."""
+    return world * batch * steps / (ms / 1e3)
+
+
 # ------------------------------------------------------------------ GPU arm
 def build_workload(cfg, rank, h, torch, ops, synth):
     M, B = cfg["M"], cfg["B"]
@@ -196,7 +218,7 @@ def build_workload(cfg, rank, h, torch, ops, synth):
     dev = torch.device("cuda", torch.cuda.current_device())
     ctf = ops.CTF() if cfg["df"] else None
     geom = ops.Geometry(M, M // 2 - 1, cfg["interp"], ctf)
-    seed = cfg["seed"] + 100 * rank
+    seed = replica_seed(cfg, rank)
     v_true = torch.from_numpy(synth.blob_volume(M, cfg["blobs"], seed=seed)).to(dev)
     quat = torch.from_numpy(synth.shoemake_quaternions(n_img, seed + 1).astype("float32")).to(dev)
     if cfg["df"]:
@@ -276,10 +298,7 @@ def run_gpu(args, cfg, rank, world):
     h.profile_enable(False)
     clk = clocks.stop() if clocks else None
     sc = st.scalars.cpu().tolist()
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t)
+    ms = max_over_ranks([ms], world)[0]
 
     # --- end to end through the public API with host buffers: every step
     # copies its batch from pinned host memory (cs_precond_sgd_step_host,
@@ -313,15 +332,12 @@ def run_gpu(args, cfg, rank, world):
         torch.cuda.synchronize()
         wall = (time.perf_counter() - w0) * 1e3
         ems = a0.elapsed_time(a1)
-        if world > 1:
-            t = torch.tensor([ems, wall], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems, wall = float(t[0]), float(t[1])
+        ems, wall = max_over_ranks([ems, wall], world)
         assert bool(torch.isfinite(out_loss[: args.steps]).all()) and float(out_loss[0]) != 0.0
-        e2e = {"value": world * B * args.steps / (ems / 1e3), "unit": "images/s",
+        e2e = {"value": job_value(world, B, args.steps, ems), "unit": "images/s",
                "h2d_bytes_per_step": B * M * M * 8 + B * 16 + B * 4,
                "d2h_bytes_per_step": 8,
-               "host_wall_value": round(world * B * args.steps / (wall / 1e3), 1),
+               "host_wall_value": round(job_value(world, B, args.steps, wall), 1),
                "api": "cs_precond_sgd_step_host (double-buffered staging, copy stream)"}
 
     # --- roofline of the dominant phase
@@ -865,7 +881,7 @@ def main():
     r = run_gpu(args, cfg, rank, world)
     if rank == 0:
         ms_step = r["ms"] / args.steps
-        value = world * cfg["B"] * args.steps / (r["ms"] / 1e3)
+        value = job_value(world, cfg["B"], args.steps, r["ms"])
         line = {"metric": METRIC, "value": round(value, 1), "unit": "images/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms_step, 4), "higher_is_better": True,
