@@ -164,6 +164,55 @@ __device__ __forceinline__ bool base_in(const Geo& G, const Cell& c) {
          (unsigned)c.z0 < (unsigned)G.M;
 }
 
+// Corner weights of a cell whose base corner is inside the grid, k = dx +
+// 2 dy + 4 dz; corners past the grid's upper edge get weight 0.
+__device__ __forceinline__ void cell_weights(const Geo& G, const Cell& c, float w8[8]) {
+  const float wx1 = c.x0 + 1 < G.M ? c.tx : 0.f, wy1 = c.y0 + 1 < G.M ? c.ty : 0.f;
+  const float wz1 = c.z0 + 1 < G.M ? c.tz : 0.f;
+  const float wx0 = 1.f - c.tx, wy0 = 1.f - c.ty, wz0 = 1.f - c.tz;
+  const float wzy[4] = {wz0 * wy0, wz0 * wy1, wz1 * wy0, wz1 * wy1};
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    w8[2 * r] = wzy[r] * wx0;
+    w8[2 * r + 1] = wzy[r] * wx1;
+  }
+}
+
+// gather from the pair layout with precomputed corner weights (base_in cells)
+__device__ __forceinline__ float2 gather_pairs_w(const Geo& G, const Cell& c,
+                                                 const float4* __restrict__ vp,
+                                                 const float w8[8]) {
+  const int M = G.M;
+  float re = 0.f, im = 0.f;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int y = c.y0 + (r & 1), z = c.z0 + (r >> 1);
+    if (z >= M || y >= M) continue;
+    const float4 a = __ldg(vp + ((size_t)z * M + y) * M + c.x0);
+    re = fmaf(w8[2 * r], a.x, fmaf(w8[2 * r + 1], a.z, re));
+    im = fmaf(w8[2 * r], a.y, fmaf(w8[2 * r + 1], a.w, im));
+  }
+  return make_float2(re, im);
+}
+
+// scatter of val * w8 into E / O (base_in cells), one v4 reduction per row
+__device__ __forceinline__ void scatter_c2_w(const Geo& G, const Cell& c, float2 val,
+                                             float2* __restrict__ E, float2* __restrict__ O,
+                                             const float w8[8]) {
+  const int M = G.M;
+  const bool odd = c.x0 & 1;
+  float2* base = odd ? O : E;
+  const int xb = odd ? c.x0 - 1 : c.x0;      // even slot of the pair
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int y = c.y0 + (r & 1), z = c.z0 + (r >> 1);
+    if (z >= M || y >= M) continue;
+    const float a0 = w8[2 * r], a1 = w8[2 * r + 1];
+    float4* p = reinterpret_cast<float4*>(base + ((size_t)z * M + y) * M + xb);
+    atomicAdd(p, make_float4(a0 * val.x, a0 * val.y, a1 * val.x, a1 * val.y));
+  }
+}
+
 // adds val * w(corner) to the 8 corners of a cell: one v4 reduction per
 // (y, z) corner row, into E (x0 even) or O (x0 odd, shifted by one voxel)
 __device__ __forceinline__ void scatter_cell_c2(const Geo& G, const Cell& c, float2 val,
@@ -247,17 +296,17 @@ __device__ __forceinline__ float gather_cell_r(const Geo& G, const Cell& c,
 
 
 // Probe words of the corners (x0, x0+1) of one cell row starting at linear
-// index j = row + x0: voxels (2i, 2i+1) share SplitMix64 output i.
+// index j = row + x0: voxels (2i, 2i+1) share SplitMix64 output i.  Both
+// outputs j/2 and (j+1)/2 are evaluated (the same one when j is even) so
+// that lanes of either parity run the same instructions: a branch on the
+// parity diverges within a warp and costs three evaluations instead of two.
 __device__ __forceinline__ void row_words(uint64_t seed, uint64_t base, size_t j, uint32_t& b0,
                                           uint32_t& b1) {
-  if ((j & 1) == 0) {
-    const uint64_t w = probe_pair(seed, base, (uint64_t)(j >> 1));
-    b0 = (uint32_t)w;
-    b1 = (uint32_t)(w >> 32);
-  } else {
-    b0 = (uint32_t)(probe_pair(seed, base, (uint64_t)(j >> 1)) >> 32);
-    b1 = (uint32_t)probe_pair(seed, base, (uint64_t)((j + 1) >> 1));
-  }
+  const uint64_t w0 = probe_pair(seed, base, (uint64_t)(j >> 1));
+  const uint64_t w1 = probe_pair(seed, base, (uint64_t)((j + 1) >> 1));
+  const bool odd = (j & 1) != 0;
+  b0 = odd ? (uint32_t)(w0 >> 32) : (uint32_t)w0;
+  b1 = odd ? (uint32_t)w1 : (uint32_t)(w1 >> 32);
 }
 
 // One traversal of the batch's disc pixels (trilinear).  Work item =
@@ -291,9 +340,19 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
     pbase = blk * (((uint64_t)G.M * G.M * G.M) >> 1);
   }
   float acc = 0.f;
+  // item w = (image b, chunk ch) = (w / nch, w % nch), advanced by nblk
+  // items per iteration without a division
+  int b_next = blk / nch, ch = blk - b_next * nch;
+  const int db = nblk / nch, dch = nblk - db * nch;
   for (int w = blk; w < total; w += nblk) {
-    const int b = w / nch;
-    const int p = (w - b * nch) * bd + threadIdx.x;
+    const int b = b_next;
+    const int p = ch * bd + threadIdx.x;
+    ch += dch;
+    b_next += db;
+    if (ch >= nch) {
+      ch -= nch;
+      ++b_next;
+    }
     if (p >= n_px) continue;
     const int e = __ldg(A.table + p);
     const int ix = e & 0xffff, iy = e >> 16;
@@ -307,18 +366,23 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
       C = ctf_value(G, a_hi, a_lo, kx * kx + ky * ky);
     }
     const bool inb = base_in(G, c);
+    float w8[8];
+    if (inb) cell_weights(G, c, w8);
     if (FL & (F_ADJ | F_GRAD)) {
       float2 r = __ldcs(img + (size_t)b * MM + (size_t)iy * G.M + ix);
       if (FL & F_GRAD) {
-        const float2 a = inb ? gather_cell_pairs(G, c, A.vp) : gather_cell_pairs_slow(G, c, A.vp);
+        const float2 a = inb ? gather_pairs_w(G, c, A.vp, w8) : gather_cell_pairs_slow(G, c, A.vp);
         r = make_float2(fmaf(C, a.x, -r.x), fmaf(C, a.y, -r.y));
         acc = fmaf(r.x, r.x, fmaf(r.y, r.y, acc));
       }
       const float sc = A.scale * C;
-      scatter_cell_c2(G, c, make_float2(sc * r.x, sc * r.y), A.E, A.O);
+      if (inb)
+        scatter_c2_w(G, c, make_float2(sc * r.x, sc * r.y), A.E, A.O, w8);
+      else
+        scatter_cell_c2(G, c, make_float2(sc * r.x, sc * r.y), A.E, A.O);
     }
     if (FL & F_CURV) {
-      const float2 a = inb ? gather_cell_pairs(G, c, A.vp) : gather_cell_pairs_slow(G, c, A.vp);
+      const float2 a = inb ? gather_pairs_w(G, c, A.vp, w8) : gather_cell_pairs_slow(G, c, A.vp);
       acc = fmaf(C * C, fmaf(a.x, a.x, a.y * a.y), acc);
     }
     if (FL & F_HVP) {
@@ -330,12 +394,13 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
     }
     if (FL & F_HUTCH) {
       uint32_t bw[8];
-      float w8[8], wsum = 0.f;
+      float wsum = 0.f;
+      if (!inb) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        w8[k] = corner_in(G, c, k) ? corner_w(c, k) : 0.f;
-        wsum += w8[k];
+        for (int k = 0; k < 8; ++k) w8[k] = corner_in(G, c, k) ? corner_w(c, k) : 0.f;
       }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) wsum += w8[k];
       if (inb) {
 #pragma unroll
         for (int r2 = 0; r2 < 4; ++r2) {
@@ -357,6 +422,8 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
           bw[k] = (uint32_t)(probe_pair(A.seed, pbase, (uint64_t)(j >> 1)) >> (32 * (j & 1)));
         }
       }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) bw[k] &= pmask;
       // S_j = sum_l w_l popc(b_j ^ b_l): each of the 28 unordered pairs is
       // counted once and feeds both of its corners
       const float sc = A.scale * C * C;
@@ -367,7 +434,7 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
       for (int j = 0; j < 8; ++j) {
 #pragma unroll
         for (int l = j + 1; l < 8; ++l) {
-          const float pc = (float)__popc((bw[j] ^ bw[l]) & pmask);
+          const float pc = (float)__popc(bw[j] ^ bw[l]);
           S[j] = fmaf(w8[l], pc, S[j]);
           S[l] = fmaf(w8[j], pc, S[l]);
         }
