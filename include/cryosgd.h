@@ -390,6 +390,14 @@ int cs_graph_destroy(cs_graph* graph);
  * (128 or 256) and blocks per SM (1..32 for 256 threads, 1..64 for 128).
  * Default 256 x 8. */
 int cs_set_launch_shape(cs_handle* h, int block_threads, int blocks_per_sm);
+/* z-slabs of the trilinear vector traversals: each pass is split into
+ * `slabs` launches, launch s processing the pixels whose cell lies in the
+ * s-th slab of the grid along z, so that the accumulators and the gathered
+ * volume a launch touches stay in L2 on large grids.  0 (default): chosen
+ * from the grid's footprint (1 slab up to 160^3, 2 at 192^3, 4 for the
+ * loss-gradient and Hutchinson passes and 2 for the curvature at 256^3).
+ * Results are the same sums in another order.  0 <= slabs <= 16. */
+int cs_set_slabs(cs_handle* h, int slabs);
 /* Autotuner: times the fused traversal of these problems (without changing
  * their state) for a set of launch shapes, keeps the fastest on the handle
  * and returns it.  Synchronous. */

@@ -2,6 +2,7 @@
 // host-side argument validation and the stream-ordered composition of the
 // kernels into the calls of the paper's problem statement.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdlib>
@@ -397,7 +398,7 @@ int cs_backproject_adjoint(cs_handle* h, const cs_geom* g, const float* images,
     CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_ADJ, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
                          reinterpret_cast<const float2*>(images), nullptr, 0, 0, nullptr, 1,
-                         grid, s, h->block),
+                         grid, s, h->block, h->slabs),
             "adjoint launch");
     CS_CUDA(launch_combine_c2(g->M, reinterpret_cast<const float2*>(vol_accum), 1.0f, w.fw,
                               reinterpret_cast<float2*>(vol_accum), nullptr, nullptr,
@@ -446,7 +447,7 @@ int cs_loss_grad(cs_handle* h, const cs_geom* g, const float* vol, const float* 
     CS_CUDA(launch_fused(F_GRAD, G, w.fw, rot, defocus, B, scale,
                          reinterpret_cast<const float2*>(vol), w.fw.pairs, nullptr,
                          reinterpret_cast<const float2*>(images), w.part, 0, 0, nullptr, 1,
-                         grid, s, h->block),
+                         grid, s, h->block, h->slabs),
             "loss_grad launch");
     CS_CUDA(launch_combine_c2(g->M, reinterpret_cast<const float2*>(vol), lambda, w.fw,
                               reinterpret_cast<float2*>(grad), w.part + kPartRegion, &nvv,
@@ -505,7 +506,7 @@ int cs_hvp(cs_handle* h, const cs_geom* g, const float* z, const float* rot,
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
     CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_HVP, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, z, nullptr,
-                         nullptr, 0, 0, nullptr, 1, grid, s, h->block),
+                         nullptr, 0, 0, nullptr, 1, grid, s, h->block, h->slabs),
             "hvp launch");
     CS_CUDA(launch_combine_r4(g->M, w.fw, 0.0f, lambda, z, Hz, h->num_sms, s), "combine launch");
     return CS_OK;
@@ -543,7 +544,8 @@ int hutch_enqueue(cs_handle* h, const cs_geom* g, const Workspace& w, const floa
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
     CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_HUTCH, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
-                         nullptr, nullptr, seed, probe_block, nullptr, n_probes, grid, s, h->block),
+                         nullptr, nullptr, seed, probe_block, nullptr, n_probes, grid, s, h->block,
+                         h->slabs),
             "hutchinson launch");
     CS_CUDA(launch_combine_r4(g->M, w.fw, lambda, 0.0f, nullptr, out, h->num_sms, s),
             "combine launch");
@@ -727,7 +729,7 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
     CS_CUDA(launch_fused(hutch ? (F_GRAD | F_HUTCH) : F_GRAD, G, w.fw, rot, defocus, B, scale,
                          reinterpret_cast<const float2*>(st->v), w.fw.pairs, nullptr,
                          reinterpret_cast<const float2*>(images), pL, st->seed, 0,
-                         st->scalars + CS_S_K, st->n_probes, vgrid, s, h->block),
+                         st->scalars + CS_S_K, st->n_probes, vgrid, s, h->block, h->slabs),
             "fused loss_grad launch");
     prof_mark(h, CS_PH_DIRECTION, s);
     CS_CUDA(launch_step_post(g->M, st->mode, reinterpret_cast<const float2*>(st->v), lambda,
@@ -737,7 +739,7 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
     nvv = nd;
     prof_mark(h, CS_PH_CURVATURE, s);
     CS_CUDA(launch_fused(F_CURV, G, w.fw, rot, defocus, B, scale, w.d, w.fw.pairs, nullptr,
-                         nullptr, pQ, 0, 0, nullptr, 1, cgrid, s, h->block),
+                         nullptr, pQ, 0, 0, nullptr, 1, cgrid, s, h->block, h->slabs),
             "curvature launch");
     prof_mark(h, CS_PH_UPDATE, s);
     CS_CUDA(launch_eta(st->scalars, pL, vgrid, pV, nvv, pD, pD + nd, nd, pQ, cgrid, nullptr,
@@ -1040,6 +1042,9 @@ FusedArgs problem_args(const cs_problem& q, const ProblemWs& w, const Geo& G) {
   A.k_dev = q.state.scalars + CS_S_K;
   A.cursor = q.state.scalars + CS_S_K;
   A.n_batches = q.n_batches;
+  A.z_lo = INT_MIN;
+  A.z_hi = INT_MAX;
+  A.part_add = 0;
   return A;
 }
 
@@ -1191,6 +1196,13 @@ int cs_graph_destroy(cs_graph* g) {
   return CS_OK;
 }
 
+int cs_set_slabs(cs_handle* h, int slabs) {
+  if (!h) return CS_ERR_ARG;
+  if (slabs < 0 || slabs > 16) return fail(h, CS_ERR_ARG, "slabs=%d must be in [0, 16]", slabs);
+  h->slabs = slabs;
+  return CS_OK;
+}
+
 int cs_set_launch_shape(cs_handle* h, int block, int bps) {
   if (!h) return CS_ERR_ARG;
   if (block != 128 && block != 256)
@@ -1227,7 +1239,8 @@ int cs_autotune(cs_handle* h, const cs_problem* probs, int n, int* block_out, in
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   const int old_block = h->block, old_bps = h->blocks_per_sm;
   struct Shape { int block, bps; };
-  const Shape cands[] = {{256, 4}, {256, 6}, {256, 8}, {128, 8}, {128, 12}, {128, 16}};
+  const Shape cands[] = {{256, 4},  {256, 6},  {256, 8},  {256, 12}, {256, 16},
+                         {128, 8},  {128, 12}, {128, 16}, {128, 24}, {128, 32}};
   float best = 1e30f;
   Shape pick = {old_block, old_bps};
   for (const Shape& c : cands) {

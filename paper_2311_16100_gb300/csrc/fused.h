@@ -37,6 +37,10 @@ struct FusedArgs {
   // is used, k = iterations done (*cursor)
   const double* cursor;
   int n_batches;
+  // z-slab of this launch: only cells with z0 in [z_lo, z_hi) are processed;
+  // part_add: add the block partial to part[] instead of storing it
+  int z_lo, z_hi;
+  int part_add;
 };
 
 struct MultiFusedArgs {
@@ -52,13 +56,18 @@ cudaError_t launch_disc_table(int M, int r, const FusedWs& w, cudaStream_t s);
 // One trilinear traversal with the given flags (partials: one per block).
 // vol: natural layout, vp: its pair layout (F_GRAD, F_CURV); probe words
 // (F_HUTCH) come from (seed, block), block = *k_dev + 1 when k_dev != NULL.
-// block = threads per block (128 or 256).
+// block = threads per block (128 or 256); slabs = z-slabs (one launch each;
+// 0: slab_count).
 cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float* rot,
                          const float* df, int B, float scale, const float2* vol,
                          const float4* vp, const float* zr, const float2* img, double* part,
                          uint64_t seed, uint64_t block_host, const double* k_dev, int K,
-                         int grid, cudaStream_t s, int block = 256);
+                         int grid, cudaStream_t s, int block = 256,
+                         int slabs = 0);
 // One launch over several problems (flags F_GRAD, F_GRAD|F_HUTCH or F_CURV).
+// Number of z-slabs a traversal of an M^3 grid is split into: one launch
+// per slab keeps the slab's accumulators and gathered volume in L2.
+int slab_count(int M, int flags);
 // Blocks of a traversal kernel (flags, block size; multi: the multi-volume
 // kernel) that fit on one SM at once.  A traversal grid larger than
 // num_sms x this would run in more than one wave, the last one part-empty.

@@ -26,6 +26,7 @@ struct cs_handle {
   // launch shape of the trilinear traversals (cs_set_launch_shape / cs_autotune)
   int block = 256;
   int blocks_per_sm = 8;
+  int slabs = 0;           // z-slabs per traversal (0: by footprint, cs_set_slabs)
   // multi-volume workspace
   void* mws = nullptr;
   size_t mws_bytes = 0;

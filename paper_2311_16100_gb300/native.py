@@ -73,6 +73,7 @@ SIGNATURES = {
     "cs_precompute_preconditioner": (c_int, [P, G, P, P, c_int, c_int, c_int, c_float, c_int,
                                              c_uint64, P, P]),
     "cs_phase_shift": (c_int, [P, c_int, P, P, c_int, c_int, P]),
+    "cs_set_slabs": (c_int, [P, c_int]),
     "cs_fsc": (c_int, [P, c_int, P, P, c_int, P, P, P]),
     "cs_shell_minmax": (c_int, [P, c_int, P, c_int, P, P, P, P]),
     "cs_exact_diag": (c_int, [P, G, P, P, c_int, c_float, c_float, P, P, P, P]),

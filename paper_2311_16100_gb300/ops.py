@@ -310,6 +310,10 @@ class Handle:
                     self.lib.cs_multi_step_graph(self.h, arr, len(problems), ctypes.byref(g)))
         return Graph(self, g, problems)
 
+    def set_slabs(self, slabs: int):
+        """z-slabs per vector traversal (0: chosen from the grid's footprint)."""
+        self._check("cs_set_slabs", self.lib.cs_set_slabs(self.h, int(slabs)))
+
     def set_launch_shape(self, block_threads: int, blocks_per_sm: int):
         self._check("cs_set_launch_shape",
                     self.lib.cs_set_launch_shape(self.h, block_threads, blocks_per_sm))

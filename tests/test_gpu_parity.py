@@ -17,14 +17,19 @@ TOL_SLICE = 1e-5
 TOL_GRAD = 1e-4
 
 
-@pytest.fixture(scope="module", params=["vector", "tiled", "pixel"])
+@pytest.fixture(scope="module", params=["vector", "vector_slabs3", "tiled", "pixel"])
 def h(request):
-    """A handle per scatter algorithm: every parity test runs on both."""
+    """A handle per scatter algorithm (and the vector traversal split into
+    three z-slabs, as large grids run it): every parity test runs on each."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2311_16100_gb300.ops import Handle
     hd = Handle(0)
-    hd.set_algo(request.param)
+    if request.param == "vector_slabs3":
+        hd.set_algo("vector")
+        hd.set_slabs(3)
+    else:
+        hd.set_algo(request.param)
     hd.algo_name = request.param
     yield hd
     hd.close()
