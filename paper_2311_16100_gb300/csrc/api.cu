@@ -183,10 +183,21 @@ int ensure_ws(cs_handle* h, int M, int B, Workspace* w) {
 
 // Disc pixel table of the vector passes for grid M, disc r (rebuilt on the
 // stream when the grid, the disc or the workspace changed).
+// The traversals of grids split into z-slabs use the tile-ordered disc
+// table (whole items outside a slab are skipped); one slab keeps the
+// row-ordered table (no idle lanes on the disc's edge tiles).
+bool tiled_table(const cs_handle* h, int M) {
+  const int S = h->slabs > 0 ? h->slabs : slab_count(M, F_GRAD | F_HUTCH);
+  return S > 1;
+}
+
+// Builds the disc table the handle's traversals of (M, r) need, once.
 cudaError_t prepare_vector(cs_handle* h, const Workspace& w, int M, int r, cudaStream_t s) {
-  const int key = M * 1024 + r;
+  const bool tiled = tiled_table(h, M);
+  const int key = ((tiled ? 1 + (h->block == 128) : 0) << 28) | (M << 12) | r;
   if (h->table_key != key) {
-    cudaError_t e = launch_disc_table(M, r, w.fw, s);
+    cudaError_t e = tiled ? launch_disc_table_tiled(M, r, h->block, w.fw, s)
+                          : launch_disc_table(M, r, w.fw, s);
     if (e != cudaSuccess) return e;
     h->table_key = key;
   }
@@ -398,7 +409,8 @@ int cs_backproject_adjoint(cs_handle* h, const cs_geom* g, const float* images,
     CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_ADJ, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
                          reinterpret_cast<const float2*>(images), nullptr, 0, 0, nullptr, 1,
-                         grid, s, h->block, h->slabs),
+                         grid, s, h->block, h->slabs,
+                         tiled_table(h, g->M)),
             "adjoint launch");
     CS_CUDA(launch_combine_c2(g->M, reinterpret_cast<const float2*>(vol_accum), 1.0f, w.fw,
                               reinterpret_cast<float2*>(vol_accum), nullptr, nullptr,
@@ -447,7 +459,8 @@ int cs_loss_grad(cs_handle* h, const cs_geom* g, const float* vol, const float* 
     CS_CUDA(launch_fused(F_GRAD, G, w.fw, rot, defocus, B, scale,
                          reinterpret_cast<const float2*>(vol), w.fw.pairs, nullptr,
                          reinterpret_cast<const float2*>(images), w.part, 0, 0, nullptr, 1,
-                         grid, s, h->block, h->slabs),
+                         grid, s, h->block, h->slabs,
+                         tiled_table(h, g->M)),
             "loss_grad launch");
     CS_CUDA(launch_combine_c2(g->M, reinterpret_cast<const float2*>(vol), lambda, w.fw,
                               reinterpret_cast<float2*>(grad), w.part + kPartRegion, &nvv,
@@ -506,7 +519,8 @@ int cs_hvp(cs_handle* h, const cs_geom* g, const float* z, const float* rot,
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
     CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_HVP, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, z, nullptr,
-                         nullptr, 0, 0, nullptr, 1, grid, s, h->block, h->slabs),
+                         nullptr, 0, 0, nullptr, 1, grid, s, h->block, h->slabs,
+                         tiled_table(h, g->M)),
             "hvp launch");
     CS_CUDA(launch_combine_r4(g->M, w.fw, 0.0f, lambda, z, Hz, h->num_sms, s), "combine launch");
     return CS_OK;
@@ -545,7 +559,7 @@ int hutch_enqueue(cs_handle* h, const cs_geom* g, const Workspace& w, const floa
     CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
     CS_CUDA(launch_fused(F_HUTCH, G, w.fw, rot, defocus, B, scale, nullptr, nullptr, nullptr,
                          nullptr, nullptr, seed, probe_block, nullptr, n_probes, grid, s, h->block,
-                         h->slabs),
+                         h->slabs, tiled_table(h, g->M)),
             "hutchinson launch");
     CS_CUDA(launch_combine_r4(g->M, w.fw, lambda, 0.0f, nullptr, out, h->num_sms, s),
             "combine launch");
@@ -729,7 +743,8 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
     CS_CUDA(launch_fused(hutch ? (F_GRAD | F_HUTCH) : F_GRAD, G, w.fw, rot, defocus, B, scale,
                          reinterpret_cast<const float2*>(st->v), w.fw.pairs, nullptr,
                          reinterpret_cast<const float2*>(images), pL, st->seed, 0,
-                         st->scalars + CS_S_K, st->n_probes, vgrid, s, h->block, h->slabs),
+                         st->scalars + CS_S_K, st->n_probes, vgrid, s, h->block, h->slabs,
+                         tiled_table(h, g->M)),
             "fused loss_grad launch");
     prof_mark(h, CS_PH_DIRECTION, s);
     CS_CUDA(launch_step_post(g->M, st->mode, reinterpret_cast<const float2*>(st->v), lambda,
@@ -739,7 +754,8 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
     nvv = nd;
     prof_mark(h, CS_PH_CURVATURE, s);
     CS_CUDA(launch_fused(F_CURV, G, w.fw, rot, defocus, B, scale, w.d, w.fw.pairs, nullptr,
-                         nullptr, pQ, 0, 0, nullptr, 1, cgrid, s, h->block, h->slabs),
+                         nullptr, pQ, 0, 0, nullptr, 1, cgrid, s, h->block, h->slabs,
+                         tiled_table(h, g->M)),
             "curvature launch");
     prof_mark(h, CS_PH_UPDATE, s);
     CS_CUDA(launch_eta(st->scalars, pL, vgrid, pV, nvv, pD, pD + nd, nd, pQ, cgrid, nullptr,

@@ -58,6 +58,42 @@ __global__ void k_disc_table(int M, int r, int* __restrict__ table, int* __restr
   if (threadIdx.x == 0) *n_out = row_off[2 * r + 1];
 }
 
+// Tile-ordered table: tiles of 16 x th pixels (th = block / 16) in row-major
+// tile order over [-half, half)^2; each tile meeting the disc gets one chunk
+// of `block` entries, slot i = pixel (x0 + i % 16, y0 + i / 16), -1 outside
+// the disc.  One block; the tile count is at most (512/16) x (512/8).
+__global__ void k_disc_table_tiled(int M, int r, int block, int* __restrict__ table,
+                                   int* __restrict__ org, int* __restrict__ n_out) {
+  __shared__ int off[2049];
+  const int half = M / 2, th = block / 16;
+  const int ntx = (M + 15) / 16, nty = (M + th - 1) / th, nt = ntx * nty;
+  const int r2 = r * r;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    const int x0 = (t % ntx) * 16 - half, y0 = (t / ntx) * th - half;
+    // nearest point of the tile to the origin decides whether it meets the disc
+    const int nx = x0 > 0 ? x0 : (x0 + 15 < 0 ? x0 + 15 : 0);
+    const int ny = y0 > 0 ? y0 : (y0 + th - 1 < 0 ? y0 + th - 1 : 0);
+    off[t + 1] = nx * nx + ny * ny <= r2 ? 1 : 0;
+  }
+  if (threadIdx.x == 0) off[0] = 0;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int t = 1; t <= nt; ++t) off[t] += off[t - 1];
+  __syncthreads();
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    if (off[t + 1] == off[t]) continue;
+    const int c = off[t];
+    const int x0 = (t % ntx) * 16 - half, y0 = (t / ntx) * th - half;
+    org[c] = (x0 + half) | ((y0 + half) << 16);
+    for (int i = 0; i < block; ++i) {
+      const int kx = x0 + i % 16, ky = y0 + i / 16;
+      table[(size_t)c * block + i] =
+          kx * kx + ky * ky <= r2 ? (kx + half) | ((ky + half) << 16) : -1;
+    }
+  }
+  if (threadIdx.x == 0) *n_out = off[nt] * block;
+}
+
 struct Cell {
   int x0, y0, z0;
   float tx, ty, tz;
@@ -349,20 +385,34 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
   const int db = nblk / nch, dch = nblk - db * nch;
   for (int w = blk; w < total; w += nblk) {
     const int b = b_next;
-    const int p = ch * bd + threadIdx.x;
+    const int chc = ch;
+    const int p = chc * bd + threadIdx.x;
     ch += dch;
     b_next += db;
     if (ch >= nch) {
       ch -= nch;
       ++b_next;
     }
+    if ((FL & F_SLAB) && A.tile_org) {
+      // tile-ordered table: skip (block-uniformly) items whose tile cannot
+      // reach this launch's slab, and the slots outside the disc
+      const int o = __ldg(A.tile_org + chc);
+      const float x0 = (float)((o & 0xffff) - G.half), y0 = (float)((o >> 16) - G.half);
+      const float* rp = A.rot + 9 * (size_t)b;
+      const float a = __ldg(rp + 2), c2 = __ldg(rp + 5);
+      const float za = a * x0, zb = a * (x0 + 15.f), zc = c2 * y0, zd = c2 * (y0 + A.tile_h - 1);
+      const float zlo = fminf(za, zb) + fminf(zc, zd) + (float)G.half - 0.01f;
+      const float zhi = fmaxf(za, zb) + fmaxf(zc, zd) + (float)G.half + 0.01f;
+      if ((float)A.z_hi <= floorf(zlo) || floorf(zhi) < (float)A.z_lo) continue;
+    }
     if (p >= n_px) continue;
     const int e = __ldg(A.table + p);
+    if (e < 0) continue;
     const int ix = e & 0xffff, iy = e >> 16;
     const int kx = ix - G.half, ky = iy - G.half;
     const Rot R = load_rot(A.rot, b);
     const Cell c = cell_of(G, R, kx, ky);
-    if (c.z0 < A.z_lo || c.z0 >= A.z_hi) continue;    // another slab's cell
+    if ((FL & F_SLAB) && (c.z0 < A.z_lo || c.z0 >= A.z_hi)) continue;   // another slab's cell
     float C = 1.f;
     if (G.ctf_on) {
       float a_hi, a_lo;
@@ -458,7 +508,8 @@ k_fused(FusedArgs A) {
   const float acc = fused_traverse<FL>(A, blockIdx.x, gridDim.x);
   if (FL & (F_GRAD | F_CURV)) {
     const double t = block_sum((double)acc);
-    if (threadIdx.x == 0) A.part[blockIdx.x] = A.part_add ? A.part[blockIdx.x] + t : t;
+    if (threadIdx.x == 0)
+      A.part[blockIdx.x] = ((FL & F_SLAB) && A.part_add) ? A.part[blockIdx.x] + t : t;
   }
 }
 
@@ -632,11 +683,16 @@ int elem_grid(int n, int num_sms) {
 
 }  // namespace
 
+// entries of the disc table (row order: <= M^2; tile order: whole tiles of
+// up to 16 x 16 over a padded grid) and tile origins (tiles of 16 x 8 at most)
+size_t table_entries(int M) { return (size_t)(M + 16) * (M + 16); }
+size_t tile_slots(int M) { return (size_t)((M + 15) / 16) * ((M + 7) / 8) + 64; }
+
 size_t fused_ws_bytes(int M) {
   const size_t n = (size_t)M * M * M;
   // E, O (complex), P (4 real buffers), pair layout, disc table, count
   return 2 * n * sizeof(float2) + 4 * n * sizeof(float) + n * sizeof(float4) +
-         (size_t)M * M * sizeof(int) + 256;
+         table_entries(M) * sizeof(int) + tile_slots(M) * sizeof(int) + 256;
 }
 
 FusedWs fused_carve(void* base, int M) {
@@ -647,13 +703,21 @@ FusedWs fused_carve(void* base, int M) {
   w.O = reinterpret_cast<float2*>(p);   p += n * sizeof(float2);
   w.P = reinterpret_cast<float*>(p);    p += 4 * n * sizeof(float);
   w.pairs = reinterpret_cast<float4*>(p); p += n * sizeof(float4);
-  w.table = reinterpret_cast<int*>(p);  p += (size_t)M * M * sizeof(int);
+  w.table = reinterpret_cast<int*>(p);  p += table_entries(M) * sizeof(int);
+  w.tile_org = reinterpret_cast<int*>(p); p += tile_slots(M) * sizeof(int);
   w.n_px = reinterpret_cast<int*>(p);
   return w;
 }
 
 cudaError_t launch_disc_table(int M, int r, const FusedWs& w, cudaStream_t s) {
   k_disc_table<<<1, 256, 0, s>>>(M, r, w.table, w.n_px);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_disc_table_tiled(int M, int r, int block, const FusedWs& w, cudaStream_t s) {
+  if (block != 128 && block != 256) return cudaErrorInvalidValue;
+  k_disc_table_tiled<<<1, 256, 0, s>>>(M, r, block, w.table, w.tile_org, w.n_px);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -717,7 +781,7 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
                          const float* df, int B, float scale, const float2* vol,
                          const float4* vp, const float* zr, const float2* img, double* part,
                          uint64_t seed, uint64_t block_host, const double* k_dev, int K,
-                         int grid, cudaStream_t s, int block, int slabs) {
+                         int grid, cudaStream_t s, int block, int slabs, bool tiled) {
   FusedArgs A;
   A.G = G;
   A.table = w.table;
@@ -741,6 +805,8 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
   A.k_dev = k_dev;
   A.cursor = nullptr;
   A.n_batches = 1;
+  A.tile_org = tiled ? w.tile_org : nullptr;
+  A.tile_h = block / 16;
   if (block != 128 && block != 256) return cudaErrorInvalidValue;
   // one launch per z-slab; the first takes cells below the grid, the last
   // those above it, so every cell is processed exactly once
@@ -749,13 +815,20 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
     A.z_lo = sl == 0 ? INT_MIN : (int)((long)G.M * sl / S);
     A.z_hi = sl == S - 1 ? INT_MAX : (int)((long)G.M * (sl + 1) / S);
     A.part_add = sl > 0;
-    switch (flags) {
+    constexpr int X = F_SLAB;
+    switch (flags | (S > 1 || tiled ? X : 0)) {
       case F_ADJ: k_fused<F_ADJ><<<grid, block, 0, s>>>(A); break;
       case F_GRAD: k_fused<F_GRAD><<<grid, block, 0, s>>>(A); break;
       case F_GRAD | F_HUTCH: k_fused<F_GRAD | F_HUTCH><<<grid, block, 0, s>>>(A); break;
       case F_HUTCH: k_fused<F_HUTCH><<<grid, block, 0, s>>>(A); break;
       case F_HVP: k_fused<F_HVP><<<grid, block, 0, s>>>(A); break;
       case F_CURV: k_fused<F_CURV><<<grid, block, 0, s>>>(A); break;
+      case F_ADJ | X: k_fused<F_ADJ | X><<<grid, block, 0, s>>>(A); break;
+      case F_GRAD | X: k_fused<F_GRAD | X><<<grid, block, 0, s>>>(A); break;
+      case F_GRAD | F_HUTCH | X: k_fused<F_GRAD | F_HUTCH | X><<<grid, block, 0, s>>>(A); break;
+      case F_HUTCH | X: k_fused<F_HUTCH | X><<<grid, block, 0, s>>>(A); break;
+      case F_HVP | X: k_fused<F_HVP | X><<<grid, block, 0, s>>>(A); break;
+      case F_CURV | X: k_fused<F_CURV | X><<<grid, block, 0, s>>>(A); break;
       default: return cudaErrorInvalidValue;
     }
     count_launches(1);

@@ -5,7 +5,10 @@
 
 namespace cs {
 
-enum FusedFlags { F_ADJ = 1, F_GRAD = 2, F_HUTCH = 4, F_HVP = 8, F_CURV = 16 };
+enum FusedFlags { F_ADJ = 1, F_GRAD = 2, F_HUTCH = 4, F_HVP = 8, F_CURV = 16,
+                  // kernel variant with the z-slab / tile-ordered table logic
+                  // (compiled out of the one-slab launches)
+                  F_SLAB = 32 };
 
 constexpr int kMaxProblems = 8;   // volumes per multi-volume launch
 
@@ -41,6 +44,10 @@ struct FusedArgs {
   // part_add: add the block partial to part[] instead of storing it
   int z_lo, z_hi;
   int part_add;
+  // tile-ordered table: chunk ch covers the 16 x tile_h pixels with origin
+  // tile_org[ch] (packed like table entries); NULL for the row-ordered table
+  const int* tile_org;
+  int tile_h;
 };
 
 struct MultiFusedArgs {
@@ -53,17 +60,24 @@ size_t fused_ws_bytes(int M);
 FusedWs fused_carve(void* base, int M);
 
 cudaError_t launch_disc_table(int M, int r, const FusedWs& w, cudaStream_t s);
+// Tile-ordered table for traversals split into z-slabs: one chunk of `block`
+// entries per 16 x (block/16) pixel tile that meets the disc, entries of
+// pixels outside the disc are -1; w.tile_org[ch] is chunk ch's origin.
+cudaError_t launch_disc_table_tiled(int M, int r, int block, const FusedWs& w, cudaStream_t s);
 // One trilinear traversal with the given flags (partials: one per block).
 // vol: natural layout, vp: its pair layout (F_GRAD, F_CURV); probe words
 // (F_HUTCH) come from (seed, block), block = *k_dev + 1 when k_dev != NULL.
 // block = threads per block (128 or 256); slabs = z-slabs (one launch each;
 // 0: slab_count).
+// tiled: the table in w is tile-ordered (launch_disc_table_tiled with the
+// same block size).
 cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float* rot,
                          const float* df, int B, float scale, const float2* vol,
                          const float4* vp, const float* zr, const float2* img, double* part,
                          uint64_t seed, uint64_t block_host, const double* k_dev, int K,
                          int grid, cudaStream_t s, int block = 256,
-                         int slabs = 0);
+                         int slabs = 0,
+                         bool tiled = false);
 // One launch over several problems (flags F_GRAD, F_GRAD|F_HUTCH or F_CURV).
 // Number of z-slabs a traversal of an M^3 grid is split into: one launch
 // per slab keeps the slab's accumulators and gathered volume in L2.

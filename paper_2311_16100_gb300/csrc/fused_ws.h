@@ -10,8 +10,9 @@ struct FusedWs {
   float2* O;      // complex accumulator shifted by one voxel along x [M^3]
   float* P;       // four real 2x2-patch accumulators [4][M^3]
   float4* pairs;  // pair layout (v[j], v[j+1]) of the gathered volume [M^3]
-  int* table;     // disc pixel table [M*M]
-  int* n_px;      // number of disc pixels
+  int* table;     // disc pixel table (row order, or tile order: see fused.cu)
+  int* tile_org;  // tile order: origin of each table chunk
+  int* n_px;      // number of table entries
 };
 
 }  // namespace cs
