@@ -31,7 +31,8 @@ size_t workspace_bytes(int M, int B) {
          align256(n * sizeof(uint32_t)) + align256(kPartSlots * sizeof(double)) +
          align256(nt * sizeof(int)) + align256(nt * (size_t)(B > 0 ? B : 1) * sizeof(int)) +
          align256((nt + 1) * sizeof(int)) + align256(sizeof(int)) +
-         2 * align256(items * sizeof(double)) + align256(fused_ws_bytes(M));
+         2 * align256(items * sizeof(double)) + align256(fused_ws_bytes(M)) +
+         align256(slab_lists_bytes(M, B));
 }
 
 Workspace carve(void* base, int M, int B) {
@@ -53,7 +54,16 @@ Workspace carve(void* base, int M, int B) {
   w.item_start = reinterpret_cast<int*>(p); p += align256((nt + 1) * sizeof(int));
   w.queue = reinterpret_cast<int*>(p);      p += align256(sizeof(int));
   w.part_items = reinterpret_cast<double*>(p); p += align256(items * sizeof(double));
-  w.part_items2 = reinterpret_cast<double*>(p);
+  w.part_items2 = reinterpret_cast<double*>(p); p += align256(items * sizeof(double));
+  {  // per-slab item lists of the slab-split traversals
+    const size_t it = (size_t)(B > 0 ? B : 1) * tile_slots(M);
+    w.fw.slab_span = reinterpret_cast<int*>(p);  p += align256(it * sizeof(int));
+    w.fw.slab_cnt = reinterpret_cast<int*>(p);
+    p += align256((size_t)kMaxSlabs * (B > 0 ? B : 1) * sizeof(int));
+    w.fw.slab_se = reinterpret_cast<int*>(p);    p += align256((kMaxSlabs + 1) * sizeof(int));
+    w.fw.slab_items = reinterpret_cast<int*>(p);
+    w.fw.slab_cap_B = B > 0 ? B : 1;
+  }
   return w;
 }
 

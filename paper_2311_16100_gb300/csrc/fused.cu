@@ -356,6 +356,122 @@ __device__ __forceinline__ void row_words(uint64_t seed, uint64_t base, size_t j
 //   F_HUTCH : P4 += scale C^2 w_j sum_l w_l Z_jl  (Eq. hutch, bit-packed probes)
 //   F_HVP   : P4 += scale C^2 w_j (P z)           (Eq. hessian)
 //   F_CURV  : part += C^2 |P d|^2                 (curvature of the Armijo step)
+// ---- per-slab item lists (deterministic, in item order)
+//
+// Item (b, t) = image b, table chunk t (a 16 x tile_h pixel tile).  Its cells
+// have z0 within [floor(zlo), floor(zhi)], zlo / zhi the extremes of
+// R[0][2] kx + R[1][2] ky + M/2 over the tile's corners with a 0.01 margin
+// (the cells' own z0 are computed in FP32 from the same products), so the
+// item is listed for every slab that range meets.
+
+__device__ __forceinline__ int slab_of(int z0, int M, int S) {
+  int sl = 0;
+  while (sl + 1 < S && z0 >= (int)((long)M * (sl + 1) / S)) ++sl;
+  return sl;
+}
+
+// one block per image: spans of its items, and counts per slab
+__global__ void __launch_bounds__(256)
+k_slab_span(Geo G, const float* __restrict__ rot, const int* __restrict__ tile_org,
+            const int* __restrict__ n_px, int bd, int tile_h, int S, int* __restrict__ span,
+            int* __restrict__ cnt, int B) {
+  __shared__ int c[kMaxSlabs];
+  const int b = blockIdx.x;
+  const int nch = *n_px / bd;
+  if (threadIdx.x < kMaxSlabs) c[threadIdx.x] = 0;
+  __syncthreads();
+  const float a = __ldg(rot + 9 * (size_t)b + 2), c2 = __ldg(rot + 9 * (size_t)b + 5);
+  for (int t = threadIdx.x; t < nch; t += blockDim.x) {
+    const int o = __ldg(tile_org + t);
+    const float x0 = (float)((o & 0xffff) - G.half), y0 = (float)((o >> 16) - G.half);
+    const float za = a * x0, zb = a * (x0 + 15.f), zc = c2 * y0, zd = c2 * (y0 + tile_h - 1);
+    const float zlo = fminf(za, zb) + fminf(zc, zd) + (float)G.half - 0.01f;
+    const float zhi = fmaxf(za, zb) + fmaxf(zc, zd) + (float)G.half + 0.01f;
+    const int s0 = slab_of((int)floorf(zlo), G.M, S), s1 = slab_of((int)floorf(zhi), G.M, S);
+    span[(size_t)b * nch + t] = s0 | (s1 << 8);
+    for (int sl = s0; sl <= s1; ++sl) atomicAdd(&c[sl], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < S) cnt[(size_t)threadIdx.x * B + b] = c[threadIdx.x];
+}
+
+// one block: se[s] = first list entry of slab s, per-image offsets off[s][b]
+// (exclusive scan of cnt in slab-major, image order), se[S] = total
+__global__ void __launch_bounds__(1024)
+k_slab_scan(int S, int B, int* __restrict__ cnt, int* __restrict__ se) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long n = (long)S * B;
+  for (long base = 0; base < n; base += blockDim.x) {
+    const long i = base + threadIdx.x;
+    const int v = i < n ? cnt[i] : 0;
+    int x = v;                                   // inclusive warp scan
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;                            // inclusive over warps
+    }
+    __syncthreads();
+    const int excl = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+    if (i < n) {
+      if (i % B == 0) se[i / B] = excl;          // first entry of slab i / B
+      cnt[i] = excl;                             // becomes the offset
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) se[S] = carry;
+}
+
+// one block per image: its items in tile order into each slab's list
+__global__ void __launch_bounds__(256)
+k_slab_fill(const int* __restrict__ n_px, int bd, int S, const int* __restrict__ span,
+            const int* __restrict__ off, int B, int* __restrict__ items) {
+  __shared__ int run[kMaxSlabs];
+  __shared__ int wcnt[kMaxSlabs][8];
+  const int b = blockIdx.x;
+  const int nch = *n_px / bd;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x < S) run[threadIdx.x] = off[(size_t)threadIdx.x * B + b];
+  __syncthreads();
+  for (int t0 = 0; t0 < nch; t0 += blockDim.x) {
+    const int t = t0 + threadIdx.x;
+    const int sp = t < nch ? span[(size_t)b * nch + t] : -1;
+    const int s0 = sp < 0 ? 1 : (sp & 0xff), s1 = sp < 0 ? 0 : (sp >> 8);
+    for (int sl = 0; sl < S; ++sl) {
+      const bool f = sl >= s0 && sl <= s1;
+      const unsigned m = __ballot_sync(0xffffffffu, f);
+      if (lane == 0) wcnt[sl][wid] = __popc(m);
+      __syncthreads();
+      int before = 0;
+      for (int q = 0; q < wid; ++q) before += wcnt[sl][q];
+      if (f) items[run[sl] + before + __popc(m & ((1u << lane) - 1u))] = b * nch + t;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += wcnt[sl][q];
+        run[sl] += tot;
+      }
+      __syncthreads();
+    }
+  }
+}
+
 template <int FL>
 __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int nblk) {
   const Geo& G = A.G;
@@ -381,30 +497,28 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
   float acc = 0.f;
   // item w = (image b, chunk ch) = (w / nch, w % nch), advanced by nblk
   // items per iteration without a division
+  // F_SLAB: this slab's items from its list; otherwise every item in order
+  const int first = (FL & F_SLAB) ? A.slab_se[0] : 0;
+  const int count = (FL & F_SLAB) ? A.slab_se[1] - first : total;
   int b_next = blk / nch, ch = blk - b_next * nch;
   const int db = nblk / nch, dch = nblk - db * nch;
-  for (int w = blk; w < total; w += nblk) {
-    const int b = b_next;
-    const int chc = ch;
+  for (int w = blk; w < count; w += nblk) {
+    int b, chc;
+    if (FL & F_SLAB) {
+      const int it = __ldg(A.slab_items + first + w);
+      b = it / nch;
+      chc = it - b * nch;
+    } else {
+      b = b_next;
+      chc = ch;
+      ch += dch;
+      b_next += db;
+      if (ch >= nch) {
+        ch -= nch;
+        ++b_next;
+      }
+    }
     const int p = chc * bd + threadIdx.x;
-    ch += dch;
-    b_next += db;
-    if (ch >= nch) {
-      ch -= nch;
-      ++b_next;
-    }
-    if ((FL & F_SLAB) && A.tile_org) {
-      // tile-ordered table: skip (block-uniformly) items whose tile cannot
-      // reach this launch's slab, and the slots outside the disc
-      const int o = __ldg(A.tile_org + chc);
-      const float x0 = (float)((o & 0xffff) - G.half), y0 = (float)((o >> 16) - G.half);
-      const float* rp = A.rot + 9 * (size_t)b;
-      const float a = __ldg(rp + 2), c2 = __ldg(rp + 5);
-      const float za = a * x0, zb = a * (x0 + 15.f), zc = c2 * y0, zd = c2 * (y0 + A.tile_h - 1);
-      const float zlo = fminf(za, zb) + fminf(zc, zd) + (float)G.half - 0.01f;
-      const float zhi = fmaxf(za, zb) + fmaxf(zc, zd) + (float)G.half + 0.01f;
-      if ((float)A.z_hi <= floorf(zlo) || floorf(zhi) < (float)A.z_lo) continue;
-    }
     if (p >= n_px) continue;
     const int e = __ldg(A.table + p);
     if (e < 0) continue;
@@ -688,6 +802,13 @@ int elem_grid(int n, int num_sms) {
 size_t table_entries(int M) { return (size_t)(M + 16) * (M + 16); }
 size_t tile_slots(int M) { return (size_t)((M + 15) / 16) * ((M + 7) / 8) + 64; }
 
+size_t slab_lists_bytes(int M, int B) {
+  const size_t items = (size_t)(B > 0 ? B : 1) * tile_slots(M);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  return al(items * sizeof(int)) + al((size_t)kMaxSlabs * (B > 0 ? B : 1) * sizeof(int)) +
+         al((kMaxSlabs + 1) * sizeof(int)) + al(3 * items * sizeof(int));
+}
+
 size_t fused_ws_bytes(int M) {
   const size_t n = (size_t)M * M * M;
   // E, O (complex), P (4 real buffers), pair layout, disc table, count
@@ -706,6 +827,8 @@ FusedWs fused_carve(void* base, int M) {
   w.table = reinterpret_cast<int*>(p);  p += table_entries(M) * sizeof(int);
   w.tile_org = reinterpret_cast<int*>(p); p += tile_slots(M) * sizeof(int);
   w.n_px = reinterpret_cast<int*>(p);
+  w.slab_span = w.slab_cnt = w.slab_se = w.slab_items = nullptr;
+  w.slab_cap_B = 0;
   return w;
 }
 
@@ -807,16 +930,32 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
   A.n_batches = 1;
   A.tile_org = tiled ? w.tile_org : nullptr;
   A.tile_h = block / 16;
+  A.slab_items = nullptr;
+  A.slab_se = nullptr;
   if (block != 128 && block != 256) return cudaErrorInvalidValue;
   // one launch per z-slab; the first takes cells below the grid, the last
-  // those above it, so every cell is processed exactly once
-  const int S = slabs > 0 ? slabs : slab_count(G.M, flags);
+  // those above it, so every cell is processed exactly once.  Slabs need the
+  // tile-ordered table; a tile spans at most 3 slabs of >= 16 voxels.
+  int S = tiled ? (slabs > 0 ? slabs : slab_count(G.M, flags)) : 1;
+  const int smax = G.M / 16 < kMaxSlabs ? G.M / 16 : kMaxSlabs;
+  if (S > smax) S = smax;
+  if (S < 1) S = 1;
+  if (tiled && B > 0) {
+    if (!w.slab_items || B > w.slab_cap_B) return cudaErrorInvalidValue;
+    k_slab_span<<<B, 256, 0, s>>>(G, rot, w.tile_org, w.n_px, block, block / 16, S, w.slab_span,
+                                  w.slab_cnt, B);
+    k_slab_scan<<<1, 1024, 0, s>>>(S, B, w.slab_cnt, w.slab_se);
+    k_slab_fill<<<B, 256, 0, s>>>(w.n_px, block, S, w.slab_span, w.slab_cnt, B, w.slab_items);
+    count_launches(3);
+    A.slab_items = w.slab_items;
+  }
   for (int sl = 0; sl < S; ++sl) {
+    if (A.slab_items) A.slab_se = w.slab_se + sl;
     A.z_lo = sl == 0 ? INT_MIN : (int)((long)G.M * sl / S);
     A.z_hi = sl == S - 1 ? INT_MAX : (int)((long)G.M * (sl + 1) / S);
     A.part_add = sl > 0;
     constexpr int X = F_SLAB;
-    switch (flags | (S > 1 || tiled ? X : 0)) {
+    switch (flags | (A.slab_items ? X : 0)) {
       case F_ADJ: k_fused<F_ADJ><<<grid, block, 0, s>>>(A); break;
       case F_GRAD: k_fused<F_GRAD><<<grid, block, 0, s>>>(A); break;
       case F_GRAD | F_HUTCH: k_fused<F_GRAD | F_HUTCH><<<grid, block, 0, s>>>(A); break;
@@ -840,17 +979,17 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
 
 // The passes with reductions touch 48 bytes per voxel at random (pair layout
 // of v, E/O, the four patch buffers), the curvature pass 16 (pair layout).
-// One launch per ~200 MB (~128 MB for the curvature) of that footprint:
-// measured at 256^3, batch 1024, the loss-gradient pass takes 6.33 / 4.86 /
-// 3.73 / 3.61 / 4.04 ms with 1 / 2 / 4 / 6 / 8 slabs and the curvature pass
-// 0.97 / 0.74 / 0.98 ms with 1 / 2 / 4; at 128^3 one slab is best (0.45 ms
-// vs 0.70 ms with two).
+// One launch per ~134 MB (128 MB for the curvature) of that footprint.
+// Measured at 256^3, batch 1024, with per-slab item lists: the
+// loss-gradient pass takes 6.33 / 2.81 / 2.44 / 2.57 / 2.87 / 3.19 ms with
+// 1 / 4 / 6 / 8 / 12 / 16 slabs, the curvature 0.97 / 0.81 / 0.84 / 0.90 ms
+// with 1 / 2 / 4 / 6; at 128^3 one slab is best.
 int slab_count(int M, int flags) {
   const double vox = (double)M * M * M;
-  const double ratio = flags == F_CURV ? 16.0 * vox / 128e6 : 48.0 * vox / 200e6;
+  const double ratio = flags == F_CURV ? 16.0 * vox / 128e6 : 48.0 * vox / 134e6;
   long S = lround(ratio);
   if (S < 1) S = 1;
-  if (S > 8) S = 8;
+  if (S > kMaxSlabs) S = kMaxSlabs;
   return (int)S;
 }
 

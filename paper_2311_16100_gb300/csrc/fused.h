@@ -48,6 +48,10 @@ struct FusedArgs {
   // tile_org[ch] (packed like table entries); NULL for the row-ordered table
   const int* tile_org;
   int tile_h;
+  // F_SLAB: this launch's items are slab_items[slab_se[0] .. slab_se[1])
+  // (item = image * chunks + chunk)
+  const int* slab_items;
+  const int* slab_se;
 };
 
 struct MultiFusedArgs {
@@ -57,6 +61,12 @@ struct MultiFusedArgs {
 };
 
 size_t fused_ws_bytes(int M);
+// tile-ordered table sizes: entries and tile origins
+size_t table_entries(int M);
+size_t tile_slots(int M);
+// per-slab item lists for batches of up to B images (bytes)
+size_t slab_lists_bytes(int M, int B);
+constexpr int kMaxSlabs = 16;
 FusedWs fused_carve(void* base, int M);
 
 cudaError_t launch_disc_table(int M, int r, const FusedWs& w, cudaStream_t s);

@@ -13,6 +13,14 @@ struct FusedWs {
   int* table;     // disc pixel table (row order, or tile order: see fused.cu)
   int* tile_org;  // tile order: origin of each table chunk
   int* n_px;      // number of table entries
+  // per-slab item lists of a slab-split traversal (single-problem workspace
+  // only; NULL otherwise): span of each (image, tile) item, per-image counts,
+  // slab starts [S+1], the lists
+  int* slab_span;
+  int* slab_cnt;
+  int* slab_se;
+  int* slab_items;
+  int slab_cap_B;
 };
 
 }  // namespace cs
