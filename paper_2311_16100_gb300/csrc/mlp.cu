@@ -186,6 +186,8 @@ __device__ __forceinline__ void warp_reduce_scatter(float (&v)[N], int lane) {
 struct FwdSmem {
   unsigned short W2[kHid * kHid];       // B operand: rows o (N), K = i
   unsigned short H1[kRows * kHid];      // A operand: rows = voxels, K = i
+  float4 L1[kHid];                      // (W1[i][0..2], b1[i]): one load per unit
+  float2 L2[kHid];                      // (b2[o], w3[o])
   float W1[192], b1[64], b2[64], w3[64], b3;
   unsigned long long bar;
   uint32_t tmem;
@@ -197,6 +199,8 @@ struct GradSmem {
   unsigned short H1[kRows * kHid];      // forward A: rows = voxels, K = i
   unsigned short DA[kRows * kHid];      // backward A: rows = voxels, K = o
   unsigned short XT[128 * kRows];       // Gram operand: rows = features (dA2 | H1), K = voxels
+  float4 L1[kHid];                      // (W1[i][0..2], b1[i])
+  float2 L2[kHid];                      // (b2[o], w3[o])
   float W1[192], b1[64], b2[64], w3[64], b3;
   float small[kSmall];                  // dW1, db1, db2, dw3, db3 of this CTA
   unsigned long long bar;
@@ -226,6 +230,11 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
   const int n = M * M * M;
   const int n_tiles = (n + kRows - 1) / kRows;
   load_params(params, S.W1, S.b1, S.b2, S.w3, &S.b3);
+  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+    S.L1[i] = make_float4(params[oW1 + 3 * i], params[oW1 + 3 * i + 1], params[oW1 + 3 * i + 2],
+                          params[ob1 + i]);
+    S.L2[i] = make_float2(params[ob2 + i], params[ow3 + i]);
+  }
   for (int e = t; e < kHid * kHid; e += kRows) {
     const int o = e / kHid, i = e % kHid;
     *reinterpret_cast<unsigned short*>(reinterpret_cast<unsigned char*>(S.W2) +
@@ -258,8 +267,8 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int i = i0 + u;
-        h[u] = gelu_f(fmaf(S.W1[3 * i + 2], x[2], fmaf(S.W1[3 * i + 1], x[1],
-                                                         fmaf(S.W1[3 * i], x[0], S.b1[i]))));
+        const float4 q = S.L1[i];
+        h[u] = gelu_f(fmaf(q.z, x[2], fmaf(q.y, x[1], fmaf(q.x, x[0], q.w))));
       }
       st_bf16x8(H1b, core_off(t, i0, kHid), h);
     }
@@ -285,7 +294,10 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
       float a2[16];
       tmem_ld16(lane_addr + c, a2);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) y = fmaf(S.w3[c + u], gelu_f(a2[u] + S.b2[c + u]), y);
+      for (int u = 0; u < 16; ++u) {
+        const float2 q = S.L2[c + u];
+        y = fmaf(q.y, gelu_f(a2[u] + q.x), y);
+      }
     }
     if (j < n) out[j] = exp_out ? expf(y) : y;
     fence_before();
@@ -313,6 +325,11 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
   const int n = M * M * M;
   const int n_tiles = (n + kRows - 1) / kRows;
   load_params(params, S.W1, S.b1, S.b2, S.w3, &S.b3);
+  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+    S.L1[i] = make_float4(params[oW1 + 3 * i], params[oW1 + 3 * i + 1], params[oW1 + 3 * i + 2],
+                          params[ob1 + i]);
+    S.L2[i] = make_float2(params[ob2 + i], params[ow3 + i]);
+  }
   for (int e = t; e < kHid * kHid; e += kRows) {
     const int o = e / kHid, i = e % kHid;
     const unsigned short w = bf16bits(params[oW2 + e]);
@@ -355,8 +372,8 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int i = i0 + u;
-        h[u] = gelu_f(fmaf(S.W1[3 * i + 2], x[2], fmaf(S.W1[3 * i + 1], x[1],
-                                                         fmaf(S.W1[3 * i], x[0], S.b1[i]))));
+        const float4 q = S.L1[i];
+        h[u] = gelu_f(fmaf(q.z, x[2], fmaf(q.y, x[1], fmaf(q.x, x[0], q.w))));
         *reinterpret_cast<unsigned short*>(XTb + core_off(64 + i, t, kRows)) = bf16bits(h[u]);
       }
       st_bf16x8(H1b, core_off(t, i0, kHid), h);
@@ -384,8 +401,9 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
     for (int c = 0; c < kHid; c += 16) tmem_ld16(d1 + lane_off + c, a2 + c);
 #pragma unroll
     for (int o = 0; o < kHid; ++o) {
-      a2[o] += S.b2[o];
-      y = fmaf(S.w3[o], gelu_f(a2[o]), y);
+      const float2 q = S.L2[o];
+      a2[o] += q.x;
+      y = fmaf(q.y, gelu_f(a2[o]), y);
     }
     const float r = inb ? y - __ldg(target + j) : 0.f;
     my_sse += (double)r * r;
@@ -399,7 +417,7 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
       for (int u = 0; u < 16; ++u) {
         const int o = c + u;
         const float h2 = gelu_f(a2[o]);
-        const float da = dy * S.w3[o] * gelu_grad_f(a2[o]);
+        const float da = dy * S.L2[o].y * gelu_grad_f(a2[o]);
         dab[u & 7] = da;
         *reinterpret_cast<unsigned short*>(XTb + core_off(o, t, kRows)) = bf16bits(da);
         if ((u & 7) == 7) st_bf16x8(DAb, core_off(t, o - 7, kHid), dab);
@@ -444,8 +462,8 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const int i = c + u;
-        const float a = fmaf(S.W1[3 * i + 2], x[2], fmaf(S.W1[3 * i + 1], x[1],
-                                                         fmaf(S.W1[3 * i], x[0], S.b1[i])));
+        const float4 q = S.L1[i];
+        const float a = fmaf(q.z, x[2], fmaf(q.y, x[1], fmaf(q.x, x[0], q.w)));
         const float da1 = dh[u] * gelu_grad_f(a);
         v[4 * u] = da1 * x[0];
         v[4 * u + 1] = da1 * x[1];
