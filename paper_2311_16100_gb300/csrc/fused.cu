@@ -111,60 +111,6 @@ __device__ __forceinline__ Cell cell_of(const Geo& G, const Rot& R, int kx, int 
   return c;
 }
 
-// trilinear gather of a complex volume at a cell (corners outside the grid read 0)
-__device__ __forceinline__ float2 gather_cell(const Geo& G, const Cell& c,
-                                              const float2* __restrict__ v) {
-  const int M = G.M;
-  float re = 0.f, im = 0.f;
-#pragma unroll
-  for (int dz = 0; dz < 2; ++dz) {
-    const int z = c.z0 + dz;
-    const float wz = dz ? c.tz : 1.f - c.tz;
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-      const int y = c.y0 + dy;
-      const float wzy = wz * (dy ? c.ty : 1.f - c.ty);
-      if ((unsigned)z >= (unsigned)M || (unsigned)y >= (unsigned)M) continue;
-      const float2* row = v + ((size_t)z * M + y) * M;
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        const int x = c.x0 + dx;
-        if ((unsigned)x >= (unsigned)M) continue;
-        const float w = wzy * (dx ? c.tx : 1.f - c.tx);
-        const float2 a = __ldg(row + x);
-        re = fmaf(w, a.x, re);
-        im = fmaf(w, a.y, im);
-      }
-    }
-  }
-  return make_float2(re, im);
-}
-
-// trilinear gather from the pair layout vp[j] = (v[j], v[j+1]): one aligned
-// 16-byte load per (y, z) corner row.  Only for cells with base_in().
-__device__ __forceinline__ float2 gather_cell_pairs(const Geo& G, const Cell& c,
-                                                    const float4* __restrict__ vp) {
-  const int M = G.M;
-  const float w0x = 1.f - c.tx, w1x = c.tx;
-  float re = 0.f, im = 0.f;
-#pragma unroll
-  for (int dz = 0; dz < 2; ++dz) {
-    const int z = c.z0 + dz;
-    const float wz = dz ? c.tz : 1.f - c.tz;
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-      const int y = c.y0 + dy;
-      if (z >= M || y >= M) continue;
-      const float wzy = wz * (dy ? c.ty : 1.f - c.ty);
-      const float4 a = __ldg(vp + ((size_t)z * M + y) * M + c.x0);
-      const float a0 = wzy * w0x, a1 = wzy * w1x;
-      re = fmaf(a0, a.x, fmaf(a1, a.z, re));
-      im = fmaf(a0, a.y, fmaf(a1, a.w, im));
-    }
-  }
-  return make_float2(re, im);
-}
-
 __device__ __forceinline__ float corner_w(const Cell& c, int k);
 __device__ __forceinline__ bool corner_in(const Geo& G, const Cell& c, int k);
 
@@ -919,7 +865,6 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
   A.E = w.E;
   A.O = w.O;
   A.part = part;
-  A.bits = nullptr;
   A.P = w.P;
   A.K = K;
   A.vp = vp;

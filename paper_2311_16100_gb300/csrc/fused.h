@@ -28,7 +28,6 @@ struct FusedArgs {
   float2* E;
   float2* O;
   double* part;         // F_GRAD: data-term partials; F_CURV: curvature partials
-  const uint32_t* bits; // unused (probe words are generated in place)
   float* P;             // F_HUTCH, F_HVP
   int K;
   const float4* vp;     // pair layout of vol (F_GRAD, F_CURV)
