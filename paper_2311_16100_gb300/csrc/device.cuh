@@ -100,11 +100,13 @@ __device__ __forceinline__ void make_stencil(const Geo& G, const Rot& R, int kx,
     return;
   }
   // trilinear: cell of s = R^T r, weights (1-t, t) per axis
-  float sx = fmaf(R.r1x, fy, R.r0x * fx) + (float)G.half;
-  float sy = fmaf(R.r1y, fy, R.r0y * fx) + (float)G.half;
-  float sz = fmaf(R.r1z, fy, R.r0z * fx) + (float)G.half;
+  // fraction of the centred coordinate (adding M/2 first would round it to
+  // the coarser float spacing near M/2 .. M)
+  float sx = fmaf(R.r1x, fy, R.r0x * fx);
+  float sy = fmaf(R.r1y, fy, R.r0y * fx);
+  float sz = fmaf(R.r1z, fy, R.r0z * fx);
   float flx = floorf(sx), fly = floorf(sy), flz = floorf(sz);
-  int x0 = (int)flx, y0 = (int)fly, z0 = (int)flz;
+  int x0 = (int)flx + G.half, y0 = (int)fly + G.half, z0 = (int)flz + G.half;
   float tx = sx - flx, ty = sy - fly, tz = sz - flz;
   S.n = 8;
 #pragma unroll

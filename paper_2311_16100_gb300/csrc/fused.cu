@@ -101,12 +101,14 @@ struct Cell {
 
 __device__ __forceinline__ Cell cell_of(const Geo& G, const Rot& R, int kx, int ky) {
   const float fx = (float)kx, fy = (float)ky;
-  const float sx = fmaf(R.r1x, fy, R.r0x * fx) + (float)G.half;
-  const float sy = fmaf(R.r1y, fy, R.r0y * fx) + (float)G.half;
-  const float sz = fmaf(R.r1z, fy, R.r0z * fx) + (float)G.half;
+  // the fraction is taken from the centred coordinate: adding M/2 first
+  // would round it to the coarser spacing of floats near M/2 .. M
+  const float sx = fmaf(R.r1x, fy, R.r0x * fx);
+  const float sy = fmaf(R.r1y, fy, R.r0y * fx);
+  const float sz = fmaf(R.r1z, fy, R.r0z * fx);
   const float flx = floorf(sx), fly = floorf(sy), flz = floorf(sz);
   Cell c;
-  c.x0 = (int)flx; c.y0 = (int)fly; c.z0 = (int)flz;
+  c.x0 = (int)flx + G.half; c.y0 = (int)fly + G.half; c.z0 = (int)flz + G.half;
   c.tx = sx - flx; c.ty = sy - fly; c.tz = sz - flz;
   return c;
 }

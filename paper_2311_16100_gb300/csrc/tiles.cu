@@ -346,11 +346,11 @@ k_tile(TileArgs A) {
               continue;
             hxx = nx - ax + 1; hyy = ny - ay + 1; hzz = nz - az + 1;
           } else {
-            const float sx = fmaf(wx, fy, ux * fx) + hf;
-            const float sy = fmaf(wy, fy, uy * fx) + hf;
-            const float sz = fmaf(wz, fy, uz * fx) + hf;
+            const float sx = fmaf(wx, fy, ux * fx);
+            const float sy = fmaf(wy, fy, uy * fx);
+            const float sz = fmaf(wz, fy, uz * fx);
             const float flx = floorf(sx), fly = floorf(sy), flz = floorf(sz);
-            const int x0 = (int)flx, y0 = (int)fly, z0 = (int)flz;
+            const int x0 = (int)flx + half, y0 = (int)fly + half, z0 = (int)flz + half;
             if (!(in_box(x0, ax - 1, ax + kT - 1) && in_box(y0, ay - 1, ay + kT - 1) &&
                   in_box(z0, az - 1, az + kT - 1)))
               continue;

@@ -103,3 +103,39 @@ def test_nearest_exact_diag_sampled_voxels_against_oracle(work):
     idx = np.concatenate([rng.choice(hit, 2000, replace=False),
                           rng.integers(0, M ** 3, 2000)])
     np.testing.assert_allclose(d[idx], count[idx] + 0.5, rtol=0, atol=1e-3)
+
+
+def test_largest_grid_slices_and_gradient():
+    """M = 512, the largest grid the library accepts: slices against the
+    oracle, and the slab-split gradient (16 slabs) against the pixel
+    algorithm (one launch, row-ordered table)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_16100_gb300 import ops
+    Mx, Bx = 512, 3
+    g = np.random.default_rng(512)
+    vol = (g.normal(size=(Mx, Mx, Mx)).astype(np.float32)
+           + 1j * g.normal(size=(Mx, Mx, Mx)).astype(np.float32)).astype(np.complex64)
+    q = synth.shoemake_quaternions(Bx, 513)
+    R = O.quat_to_rot(q).astype(np.float32)
+    df = synth.defocus_angstrom(Bx, 514).astype(np.float32)
+    d = torch.device("cuda")
+    tv, tR, tdf = torch.from_numpy(vol).to(d), torch.from_numpy(R).to(d), torch.from_numpy(df).to(d)
+    ctf = dict(kv=synth.CTF_KV, cs_mm=synth.CTF_CS_MM, amp=synth.CTF_AMP, pixel_A=synth.CTF_PIXEL_A)
+    hv, hp = ops.Handle(0), ops.Handle(0)
+    hv.set_algo("vector")
+    hp.set_algo("pixel")
+    for interp in ("nearest", "trilinear"):
+        geom = ops.Geometry(Mx, Mx // 2 - 1, interp, ops.CTF())
+        y = hv.slice_project(geom, tv, tR, tdf).cpu().numpy()
+        want = O.slice_project(vol, R, df, Mx, Mx // 2 - 1, interp, ctf)
+        assert rel_l2(y, want) <= 1e-5
+    geom = ops.Geometry(Mx, Mx // 2 - 1, "trilinear", ops.CTF())
+    images = torch.from_numpy((0.9 * want).astype(np.complex64)).to(d)
+    del want
+    lv, gv = hv.loss_grad(geom, tv, images, tR, tdf, 0.1, 10.0)
+    lp, gp = hp.loss_grad(geom, tv, images, tR, tdf, 0.1, 10.0)
+    assert rel_l2(gv.cpu().numpy(), gp.cpu().numpy()) <= 1e-5
+    assert abs(float(lv) - float(lp)) <= 1e-6 * abs(float(lp))
+    hv.close()
+    hp.close()
