@@ -125,11 +125,17 @@ __device__ __forceinline__ void make_stencil(const Geo& G, const Rot& R, int kx,
 
 // SplitMix64 (Steele, Lea & Flood 2014): output number c of the stream
 // seeded with `seed` is mix(seed + (c + 1) * golden_gamma).
-__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t c) {
-  uint64_t z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kSplitMixGamma = 0x9E3779B97F4A7C15ull;
+
+// The output function of SplitMix64 applied to the state z.
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t c) {
+  return splitmix_mix(seed + (c + 1ull) * kSplitMixGamma);
 }
 
 // Probe words: voxels (2i, 2i+1) take the low / high 32 bits of SplitMix64

@@ -282,19 +282,7 @@ __device__ __forceinline__ float gather_cell_r(const Geo& G, const Cell& c,
 
 
 
-// Probe words of the corners (x0, x0+1) of one cell row starting at linear
-// index j = row + x0: voxels (2i, 2i+1) share SplitMix64 output i.  Both
-// outputs j/2 and (j+1)/2 are evaluated (the same one when j is even) so
-// that lanes of either parity run the same instructions: a branch on the
-// parity diverges within a warp and costs three evaluations instead of two.
-__device__ __forceinline__ void row_words(uint64_t seed, uint64_t base, size_t j, uint32_t& b0,
-                                          uint32_t& b1) {
-  const uint64_t w0 = probe_pair(seed, base, (uint64_t)(j >> 1));
-  const uint64_t w1 = probe_pair(seed, base, (uint64_t)((j + 1) >> 1));
-  const bool odd = (j & 1) != 0;
-  b0 = odd ? (uint32_t)(w0 >> 32) : (uint32_t)w0;
-  b1 = odd ? (uint32_t)w1 : (uint32_t)(w1 >> 32);
-}
+
 
 // One traversal of the batch's disc pixels (trilinear).  Work item =
 // (image, 256 consecutive disc pixels); a fixed grid walks the items, so
@@ -437,10 +425,13 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
   }
   const uint32_t pmask = A.K >= 32 ? 0xffffffffu : ((1u << A.K) - 1u);
   const float invK = 1.0f / (float)(A.K > 0 ? A.K : 1);
-  uint64_t pbase = 0;
+  uint64_t pbase = 0, st_base = 0, step_y = 0, step_z = 0;
   if (FL & F_HUTCH) {
     const uint64_t blk = A.k_dev ? (uint64_t)(*A.k_dev) + 1ull : A.block_host;
     pbase = blk * (((uint64_t)G.M * G.M * G.M) >> 1);
+    st_base = A.seed + (pbase + 1ull) * kSplitMixGamma;     // state of output pbase
+    step_y = (uint64_t)(G.M / 2) * kSplitMixGamma;           // next row: M/2 outputs on
+    step_z = (uint64_t)G.M * G.M / 2 * kSplitMixGamma;       // next plane: M^2/2
   }
   float acc = 0.f;
   // item w = (image b, chunk ch) = (w / nch, w % nch), advanced by nblk
@@ -518,13 +509,26 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
 #pragma unroll
       for (int k = 0; k < 8; ++k) wsum += w8[k];
       if (inb) {
+        // SplitMix64 states of the corner rows' outputs: output i has state
+        // seed + (pbase + i + 1) gamma, so with i0 = j0 / 2 for the base
+        // corner, the row (dy, dz) starts at i0 + (dy M + dz M^2) / 2 (M is
+        // even) and its second output, for an odd x0, is one further: the
+        // eight states are 64-bit additions to one product
+        const size_t j0 = ((size_t)c.z0 * G.M + c.y0) * G.M + c.x0;
+        const uint64_t odd = j0 & 1;
+        const uint64_t s0 = st_base + (uint64_t)(j0 >> 1) * kSplitMixGamma;
 #pragma unroll
         for (int r2 = 0; r2 < 4; ++r2) {
           const int dy = r2 & 1, dz = r2 >> 1;
           const int y = c.y0 + dy, z = c.z0 + dz;
           uint32_t b0 = 0u, b1 = 0u;
-          if (y < G.M && z < G.M)
-            row_words(A.seed, pbase, ((size_t)z * G.M + y) * G.M + c.x0, b0, b1);
+          if (y < G.M && z < G.M) {
+            const uint64_t sr = s0 + (dy ? step_y : 0ull) + (dz ? step_z : 0ull);
+            const uint64_t w0 = splitmix_mix(sr);
+            const uint64_t w1 = splitmix_mix(sr + odd * kSplitMixGamma);
+            b0 = odd ? (uint32_t)(w0 >> 32) : (uint32_t)w0;
+            b1 = odd ? (uint32_t)w1 : (uint32_t)(w1 >> 32);
+          }
           bw[2 * r2] = b0;
           bw[2 * r2 + 1] = b1;
         }
