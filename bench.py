@@ -378,6 +378,32 @@ def run_gpu(args, cfg, rank, world):
                     "frac": round(red_ach / red_peak, 4),
                     "peak_source": "measured live (cs_measure_reduction_rate)",
                     "reductions_per_launch": reds[dom]}
+    # the same steps replayed as a CUDA graph (batch k mod n_batches chosen
+    # on the device), launch shape from the autotuner
+    graph = None
+    if not getattr(args, "no_graph", False) and world == 1:
+        st_g = ops.SGDState(v0, mode="hutchinson", alpha=alpha, eta0=1.0, beta=0.9,
+                            armijo_c=0.5, n_probes=cfg["K"], seed=cfg["seed"] + 11)
+        prob = ops.Problem(geom, st_g, images, quat, df if W["ctf"] else None, B, lam,
+                           W["n_img"] / B)
+        hg = ops.Handle(torch.cuda.current_device())
+        bt, bps = hg.autotune([prob])
+        gr = hg.multi_step_graph([prob])
+        for _ in range(args.warmup):
+            gr.launch(stream)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            gr.launch(stream)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1) / args.steps
+        graph = {"ms_per_step": round(gms, 4), "images_per_s": round(B / (gms / 1e3), 1),
+                 "launch_shape": {"block_threads": bt, "blocks_per_sm": bps},
+                 "api": "cs_multi_step_graph with one problem, cs_graph_launch"}
+        gr.close()
+        hg.close()
     # cs_loss_grad alone (loss and gradient, no Hutchinson, no step): median
     # over 20 passes of the per-batch time, every batch of the image set
     lg = None
@@ -407,7 +433,7 @@ def run_gpu(args, cfg, rank, world):
               "pass": f"{nb} batches of {B} (every image once), poses converted per batch"}
     return dict(ms=ms, launches=launches, phases={k: round(v, 4) for k, v in per.items()},
                 roofline=roof, red_roofline=red_roof, e2e=e2e, clocks=clk, scalars=sc, n_img=W["n_img"],
-                loss_grad_only=lg)
+                loss_grad_only=lg, graph=graph)
 
 
 # ------------------------------------------- time to relative error (metric 2)
@@ -988,6 +1014,7 @@ def main():
                 "e2e": r["e2e"], "clocks": r["clocks"],
                 "gpu_launches": r["launches"], "phases_ms_per_step": r["phases"],
                 "loss_grad_only": r["loss_grad_only"],
+                "graph_replay": r["graph"],
                 "final_scalars": {"eta": r["scalars"][0], "k": r["scalars"][1],
                                   "loss": r["scalars"][3]}}
         if world == 1 and not args.no_metric2:
