@@ -59,6 +59,8 @@ def parse():
                    help="only time the learned-preconditioner network kernels at 128^3")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-preconditioner leg")
+    p.add_argument("--no-graph", action="store_true",
+                   help="skip the single-problem CUDA-graph replay figure")
     p.add_argument("--no-loss-grad", action="store_true",
                    help="skip the cs_loss_grad-only throughput")
     p.add_argument("--no-multi", action="store_true",
@@ -381,7 +383,7 @@ def run_gpu(args, cfg, rank, world):
     # the same steps replayed as a CUDA graph (batch k mod n_batches chosen
     # on the device), launch shape from the autotuner
     graph = None
-    if not getattr(args, "no_graph", False) and world == 1:
+    if not args.no_graph and world == 1:
         st_g = ops.SGDState(v0, mode="hutchinson", alpha=alpha, eta0=1.0, beta=0.9,
                             armijo_c=0.5, n_probes=cfg["K"], seed=cfg["seed"] + 11)
         prob = ops.Problem(geom, st_g, images, quat, df if W["ctf"] else None, B, lam,
