@@ -379,9 +379,12 @@ typedef struct cs_graph cs_graph;
  * cs_graph_launch replays one step: batches advance on the device.  The
  * graph keeps the problems' device pointers and the handle's workspace; it
  * is invalid once the handle is destroyed, and cs_graph_launch returns
- * CS_ERR_ARG if the handle's multi-volume workspace was reallocated since
- * the capture.  A replay uses that workspace: do not run other calls of the
- * same handle concurrently with it (other streams), use another handle. */
+ * CS_ERR_ARG if the handle's multi-volume workspace was reallocated, or its
+ * pixel tables rebuilt (other problems, another launch shape), since the
+ * capture.  Problems whose grids are split into z-slabs (cs_set_slabs) run
+ * their traversals as their own launches inside the step.  A replay uses
+ * that workspace: do not run other calls of the same handle concurrently
+ * with it (other streams), use another handle. */
 int cs_multi_step_graph(cs_handle* h, const cs_problem* probs, int n, cs_graph** graph);
 int cs_graph_launch(cs_graph* graph, void* stream);
 int cs_graph_destroy(cs_graph* graph);

@@ -933,7 +933,7 @@ struct ProblemWs {
 
 size_t problem_ws_bytes(int M, int B) {
   return align256(fused_ws_bytes(M)) + align256((size_t)B * 9 * sizeof(float)) +
-         align256((size_t)kMultiParts * sizeof(double));
+         align256((size_t)kMultiParts * sizeof(double)) + align256(slab_lists_bytes(M, B));
 }
 
 int check_problems(cs_handle* h, const cs_problem* P, int n) {
@@ -999,6 +999,16 @@ int ensure_mws(cs_handle* h, const cs_problem* P, int n, ProblemWs* W) {
     W[p].fw = fused_carve(c, M);                c += align256(fused_ws_bytes(M));
     W[p].rot = reinterpret_cast<float*>(c);     c += align256((size_t)P[p].B * 9 * sizeof(float));
     W[p].part = reinterpret_cast<double*>(c);   c += align256((size_t)kMultiParts * sizeof(double));
+    {  // per-slab item lists (problems whose traversals are split into z-slabs)
+      const int B = P[p].B > 0 ? P[p].B : 1;
+      const size_t it = (size_t)B * tile_slots(M);
+      W[p].fw.slab_span = reinterpret_cast<int*>(c);  c += align256(it * sizeof(int));
+      W[p].fw.slab_cnt = reinterpret_cast<int*>(c);
+      c += align256((size_t)kMaxSlabs * B * sizeof(int));
+      W[p].fw.slab_se = reinterpret_cast<int*>(c);    c += align256((kMaxSlabs + 1) * sizeof(int));
+      W[p].fw.slab_items = reinterpret_cast<int*>(c); c += align256(3 * it * sizeof(int));
+      W[p].fw.slab_cap_B = B;
+    }
   }
   return CS_OK;
 }
@@ -1038,10 +1048,15 @@ void split_blocks(const cs_handle* h, const cs_problem* P, int n, int* start, in
 cudaError_t prepare_tables(cs_handle* h, const cs_problem* P, int n, const ProblemWs* W,
                            cudaStream_t s) {
   for (int p = 0; p < n; ++p) {
-    const int key = P[p].geom.M * 1024 + P[p].geom.r_max;
+    const int M = P[p].geom.M, r = P[p].geom.r_max;
+    const bool tiled = tiled_table(h, M);
+    const int key = ((tiled ? 1 + (h->block == 128) : 0) << 28) | (M << 12) | r;
     if (h->mtable_key[p] != key) {
-      cudaError_t e = launch_disc_table(P[p].geom.M, P[p].geom.r_max, W[p].fw, s);
+      cudaError_t e = tiled ? launch_disc_table_tiled(M, r, h->block, W[p].fw, s)
+                            : launch_disc_table(M, r, W[p].fw, s);
       if (e != cudaSuccess) return e;
+      // a graph captured with the previous table layout must not replay
+      if (h->mtable_key[p] != -1) ++h->mws_generation;
       h->mtable_key[p] = key;
     }
   }
@@ -1075,14 +1090,29 @@ FusedArgs problem_args(const cs_problem& q, const ProblemWs& w, const Geo& G) {
 }
 
 // Everything of one multi-volume step, enqueued on s (no allocation, no
-// host synchronisation: capturable).
+// host synchronisation: capturable).  Problems whose grid is split into
+// z-slabs (tiled_table) run their traversals as their own slab launches;
+// the others share one launch of the multi-volume kernel.
 int multi_step_enqueue(cs_handle* h, const cs_problem* P, int n, const ProblemWs* W,
                        cudaStream_t s) {
   const bool hutch = P[0].state.mode == CS_HUTCHINSON;
+  const int fl = hutch ? (F_GRAD | F_HUTCH) : F_GRAD;
+  bool big[CS_MAX_PROBLEMS];
+  int small_idx[CS_MAX_PROBLEMS], n_small = 0;
+  cs_problem small[CS_MAX_PROBLEMS];
+  for (int p = 0; p < n; ++p) {
+    big[p] = tiled_table(h, P[p].geom.M);
+    if (!big[p]) {
+      small_idx[n_small] = p;
+      small[n_small++] = P[p];
+    }
+  }
   MultiFusedArgs MA{};
-  MA.n = n;
+  MA.n = n_small;
   int total = 0;
-  split_blocks(h, P, n, MA.start, &total, h->block);
+  if (n_small > 0) split_blocks(h, small, n_small, MA.start, &total, h->block);
+  FusedArgs BA[CS_MAX_PROBLEMS];
+  int nL[CS_MAX_PROBLEMS], nQ[CS_MAX_PROBLEMS];
   for (int p = 0; p < n; ++p) {
     const cs_problem& q = P[p];
     const int M = q.geom.M;
@@ -1094,11 +1124,21 @@ int multi_step_enqueue(cs_handle* h, const cs_problem* P, int n, const ProblemWs
     CS_CUDA(launch_pairs(M, reinterpret_cast<const float2*>(q.state.v), W[p].fw.pairs,
                          h->num_sms, s),
             "pairs launch");
-    MA.a[p] = problem_args(q, W[p], make_geo(q.geom));
-    MA.a[p].part = W[p].part;                   // loss partials
+    BA[p] = problem_args(q, W[p], make_geo(q.geom));
+    BA[p].part = W[p].part;                     // loss partials
   }
-  CS_CUDA(launch_fused_multi(hutch ? (F_GRAD | F_HUTCH) : F_GRAD, MA, total, h->block, s),
-          "multi-volume traversal launch");
+  for (int i = 0; i < n_small; ++i) {
+    MA.a[i] = BA[small_idx[i]];
+    nL[small_idx[i]] = nQ[small_idx[i]] = MA.start[i + 1] - MA.start[i];
+  }
+  if (n_small > 0)
+    CS_CUDA(launch_fused_multi(fl, MA, total, h->block, s), "multi-volume traversal launch");
+  for (int p = 0; p < n; ++p) {
+    if (!big[p]) continue;
+    nL[p] = vec_grid(h, P[p].B, P[p].geom.M, fl);
+    CS_CUDA(launch_fused_args(fl, BA[p], W[p].fw, nL[p], s, h->block, h->slabs, true),
+            "slab traversal launch");
+  }
   int nd[CS_MAX_PROBLEMS];
   for (int p = 0; p < n; ++p) {
     const cs_problem& q = P[p];
@@ -1107,16 +1147,23 @@ int multi_step_enqueue(cs_handle* h, const cs_problem* P, int n, const ProblemWs
                              q.state.D_avg, W[p].part + 2 * kPartRegion, W[p].part + kPartRegion,
                              &nd[p], h->num_sms, s),
             "step_post launch");
-    MA.a[p].img = nullptr;
-    MA.a[p].part = W[p].part + 3 * kPartRegion;   // curvature partials
+    BA[p].img = nullptr;
+    BA[p].part = W[p].part + 3 * kPartRegion;   // curvature partials
   }
-  CS_CUDA(launch_fused_multi(F_CURV, MA, total, h->block, s), "multi-volume curvature launch");
+  for (int i = 0; i < n_small; ++i) MA.a[i] = BA[small_idx[i]];
+  if (n_small > 0)
+    CS_CUDA(launch_fused_multi(F_CURV, MA, total, h->block, s), "multi-volume curvature launch");
+  for (int p = 0; p < n; ++p) {
+    if (!big[p]) continue;
+    nQ[p] = vec_grid(h, P[p].B, P[p].geom.M, F_CURV);
+    CS_CUDA(launch_fused_args(F_CURV, BA[p], W[p].fw, nQ[p], s, h->block, h->slabs, true),
+            "slab curvature launch");
+  }
   for (int p = 0; p < n; ++p) {
     const cs_problem& q = P[p];
-    const int nb = MA.start[p + 1] - MA.start[p];
     double* pD = W[p].part + 2 * kPartRegion;
-    CS_CUDA(launch_eta(q.state.scalars, W[p].part, nb, W[p].part + kPartRegion, nd[p], pD,
-                       pD + nd[p], nd[p], W[p].part + 3 * kPartRegion, nb, nullptr, q.lambda,
+    CS_CUDA(launch_eta(q.state.scalars, W[p].part, nL[p], W[p].part + kPartRegion, nd[p], pD,
+                       pD + nd[p], nd[p], W[p].part + 3 * kPartRegion, nQ[p], nullptr, q.lambda,
                        q.scale, q.state.c, q.state.max_halvings, s),
             "eta launch");
     CS_CUDA(launch_update_pairs(q.geom.M, reinterpret_cast<float2*>(q.state.v), W[p].fw,
@@ -1250,16 +1297,22 @@ int cs_autotune(cs_handle* h, const cs_problem* probs, int n, int* block_out, in
   CS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
   const bool hutch = probs[0].state.mode == CS_HUTCHINSON;
   cudaError_t e = prepare_tables(h, probs, n, W, s);
+  // the shape of the shared multi-volume launch is tuned on the problems it
+  // carries (those not split into z-slabs)
+  cs_problem small[CS_MAX_PROBLEMS];
+  int n_small = 0;
   MultiFusedArgs MA{};
-  MA.n = n;
   for (int p = 0; p < n && e == cudaSuccess; ++p) {
     const cs_problem& q = probs[p];
+    if (tiled_table(h, q.geom.M)) continue;
     e = launch_quat_to_rot_cursor(q.quat, q.B, q.n_batches, q.state.scalars + CS_S_K, W[p].rot, s);
     if (e == cudaSuccess) e = launch_pairs(q.geom.M, reinterpret_cast<const float2*>(q.state.v),
                                            W[p].fw.pairs, h->num_sms, s);
-    MA.a[p] = problem_args(q, W[p], make_geo(q.geom));
-    MA.a[p].part = W[p].part;
+    MA.a[n_small] = problem_args(q, W[p], make_geo(q.geom));
+    MA.a[n_small].part = W[p].part;
+    small[n_small++] = q;
   }
+  MA.n = n_small;
   cudaEvent_t a = nullptr, b = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
@@ -1270,11 +1323,11 @@ int cs_autotune(cs_handle* h, const cs_problem* probs, int n, int* block_out, in
   float best = 1e30f;
   Shape pick = {old_block, old_bps};
   for (const Shape& c : cands) {
-    if (e != cudaSuccess) break;
+    if (e != cudaSuccess || n_small == 0) break;
     h->block = c.block;
     h->blocks_per_sm = c.bps;
     int total = 0;
-    split_blocks(h, probs, n, MA.start, &total, c.block);
+    split_blocks(h, small, n_small, MA.start, &total, c.block);
     if (total > kPartRegion) continue;
     float tmin = 1e30f;
     for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {

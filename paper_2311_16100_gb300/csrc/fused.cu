@@ -879,6 +879,14 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
   A.k_dev = k_dev;
   A.cursor = nullptr;
   A.n_batches = 1;
+  return launch_fused_args(flags, A, w, grid, s, block, slabs, tiled);
+}
+
+cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid, cudaStream_t s,
+                              int block, int slabs, bool tiled) {
+  const Geo& G = A.G;
+  const int B = A.B;
+  const float* rot = A.rot;
   A.tile_org = tiled ? w.tile_org : nullptr;
   A.tile_h = block / 16;
   A.slab_items = nullptr;

@@ -91,6 +91,11 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
 // Number of z-slabs a traversal of an M^3 grid is split into: one launch
 // per slab keeps the slab's accumulators and gathered volume in L2.
 int slab_count(int M, int flags);
+// launch_fused with the kernel arguments already filled in (the slab fields
+// are set here): used by the multi-volume step for its large volumes, whose
+// arguments select the batch on the device (cursor).
+cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid, cudaStream_t s,
+                              int block, int slabs, bool tiled);
 // Blocks of a traversal kernel (flags, block size; multi: the multi-volume
 // kernel) that fit on one SM at once.  A traversal grid larger than
 // num_sms x this would run in more than one wave, the last one part-empty.

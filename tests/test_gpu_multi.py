@@ -147,3 +147,36 @@ def test_multi_step_rejects_mixed_modes(env):
     probs = [sets[0].problem(ops, "hutchinson"), sets[1].problem(ops, "plain")]
     with pytest.raises(CryoSGDError):
         h.multi_step(probs)
+
+
+def test_multi_step_with_slab_split_problems(env):
+    """Problems whose grids are split into z-slabs (forced here with three
+    slabs) run their own slab launches inside the multi-volume step: each
+    problem still follows the oracle, eagerly and replayed as a graph."""
+    ops, h, sets = env
+    hs = ops.Handle(0)
+    hs.set_slabs(3)
+    probs = [ds.problem(ops) for ds in sets]
+    ref = [oracle_run(ds, 2) for ds in sets]
+    for k in range(2):
+        hs.multi_step(probs)
+        for p, ds in enumerate(sets):
+            sc = probs[p].state.scalars.cpu().numpy()
+            o = ref[p][k]
+            assert sc[0] == o["eta"] and sc[6] == o["halvings"]
+            assert abs(sc[3] - o["loss"]) <= 1e-5 * abs(o["loss"])
+            assert rel_l2(probs[p].state.v.cpu().numpy(), o["v"]) <= 1e-4
+    graphed = [ds.problem(ops) for ds in sets]
+    eager = [ds.problem(ops) for ds in sets]
+    hg = ops.Handle(0)
+    hg.set_slabs(3)
+    g = hg.multi_step_graph(graphed)
+    for _ in range(2):
+        hs.multi_step(eager)
+        g.launch()
+    torch.cuda.synchronize()
+    for a, b in zip(eager, graphed):
+        assert rel_l2(b.state.v.cpu().numpy(), a.state.v.cpu().numpy()) <= 1e-5
+    g.close()
+    hg.close()
+    hs.close()
