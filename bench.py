@@ -800,14 +800,17 @@ def conditioning(args, torch, ops, synth):
 
 
 def multi_volume(args, torch, ops, synth):
-    """Throughput of the multi-volume step (grids 64/96/128/160, 10k-40k
-    images each, batch 1024 per volume), autotuned, replayed as a CUDA graph."""
+    """Throughput of the multi-volume step, replayed as a CUDA graph: grids
+    64/96/128/160 (10k-40k images each, batch 1024 per volume) in one
+    autotuned launch; then the same four with the 256^3 problem of 102 400
+    images added to the graph (its traversals split into z-slabs)."""
     h = ops.Handle(torch.cuda.current_device())
     specs = [(64, 10240, 200), (96, 20480, 600), (128, 30720, 1000), (160, 40960, 1500)]
     probs, keep = [], []
-    for i, (M, n_img, blobs) in enumerate(specs):
+
+    def add(M, n_img, blobs, seed):
         cfg = dict(M=M, n_img=n_img, B=1024, interp="trilinear", K=32, df=(1.0, 3.0),
-                   snr=0.05, blobs=blobs, seed=7000 + 10 * i)
+                   snr=0.05, blobs=blobs, seed=seed)
         W = build_workload(cfg, 0, h, torch, ops, synth)
         lam = W["sigma2"]
         alpha = h.threshold_alpha(W["geom"], W["df"], W["n_img"], lam)
@@ -816,26 +819,35 @@ def multi_volume(args, torch, ops, synth):
         probs.append(ops.Problem(W["geom"], st, W["images"], W["quat"], W["df"], 1024, lam,
                                  W["n_img"] / 1024))
         keep.append(W)
-    bt, bps = h.autotune(probs)
-    g = h.multi_step_graph(probs)
-    s = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        g.launch(s)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    steps = max(args.steps, 10)
-    for _ in range(steps):
-        g.launch(s)
-    e1.record(s)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    imgs = 1024 * len(specs) * steps
-    out = {"volumes": [f"{M}^3 x {n} images" for M, n, _ in specs], "batch_per_volume": 1024,
-           "launch_shape": {"block_threads": bt, "blocks_per_sm": bps},
-           "ms_per_step": round(ms / steps, 4), "images_per_s": round(imgs / (ms / 1e3), 1),
-           "cuda_graph": True}
-    g.close()
+
+    def run(label_volumes):
+        bt, bps = h.autotune(probs)
+        g = h.multi_step_graph(probs)
+        s = torch.cuda.current_stream()
+        for _ in range(args.warmup):
+            g.launch(s)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        steps = max(args.steps, 10)
+        for _ in range(steps):
+            g.launch(s)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        imgs = 1024 * len(probs) * steps
+        g.close()
+        return {"volumes": label_volumes, "batch_per_volume": 1024,
+                "launch_shape": {"block_threads": bt, "blocks_per_sm": bps},
+                "ms_per_step": round(ms / steps, 4), "images_per_s": round(imgs / (ms / 1e3), 1),
+                "cuda_graph": True}
+
+    for i, (M, n_img, blobs) in enumerate(specs):
+        add(M, n_img, blobs, 7000 + 10 * i)
+    out = run([f"{M}^3 x {n} images" for M, n, _ in specs])
+    add(256, 102400, 5000, 7040)
+    out["with_256"] = run([f"{M}^3 x {n} images" for M, n, _ in specs] +
+                          ["256^3 x 102400 images (z-slab launches)"])
     h.close()
     return out
 
