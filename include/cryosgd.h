@@ -438,6 +438,14 @@ int cs_mlp_grad(cs_handle* h, int M, int r_ball, const float* params, const floa
  * zeroes them before step 1); grad is read and zeroed.  step >= 1. */
 int cs_mlp_adam_step(cs_handle* h, float* params, float* m, float* v, float* grad, int step,
                      float lr, float beta1, float beta2, float eps, void* stream);
+/* Failure-handling self-test (no counterpart in the paper): launches one
+ * block whose mbarrier wait can never complete; the wait gives up after
+ * `spins` polls (1 .. 2^24) and records the expiry in the handle's device
+ * status word exactly as the tensor-core kernels do, so the next
+ * cs_check_device_status returns CS_ERR_TIMEOUT (and clears the word).
+ * Nothing faults or traps and the context stays usable; it lets a caller
+ * verify its error path.  Asynchronous on `stream`. */
+int cs_selftest_wait_timeout(cs_handle* h, long long spins, void* stream);
 /* Synchronises the handle's device and reports whether a bounded
  * device-side wait ran out since the last check (CS_ERR_TIMEOUT, and the
  * word is cleared) or not (CS_OK). */

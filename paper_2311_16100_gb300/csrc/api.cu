@@ -1504,6 +1504,16 @@ int cs_mlp_adam_step(cs_handle* h, float* params, float* m, float* v, float* gra
   return CS_OK;
 }
 
+int cs_selftest_wait_timeout(cs_handle* h, long long spins, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  if (spins < 1 || spins > (1ll << 24))
+    return fail(h, CS_ERR_ARG, "spins=%lld must be in [1, 2^24]", spins);
+  CS_SCOPE(h);
+  CS_TRY(ensure_status(h));
+  CS_CUDA(launch_wait_selftest(spins, h->status, S(stream)), "wait self-test launch");
+  return CS_OK;
+}
+
 int cs_check_device_status(cs_handle* h) {
   if (!h) return CS_ERR_ARG;
   if (!h->status) return CS_OK;

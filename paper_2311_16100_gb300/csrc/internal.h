@@ -164,6 +164,8 @@ cudaError_t launch_mlp_forward(int M, const float* params, const float* cov, con
 cudaError_t launch_mlp_grad(int M, int r2, float inv_n, const float* params, const float* cov,
                             const float* c2w, const float* target, float* grad, double* sse,
                             bool tc, int* err, int num_sms, cudaStream_t s);
+// Failure-handling self-test: a bounded mbarrier wait that runs out.
+cudaError_t launch_wait_selftest(long long limit, int* err, cudaStream_t s);
 cudaError_t launch_adam(float* p, float* m, float* v, float* g, int step, float lr, float b1,
                         float b2, float eps, cudaStream_t s);
 

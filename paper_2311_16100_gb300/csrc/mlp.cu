@@ -119,8 +119,9 @@ __device__ __forceinline__ void bar_init(uint32_t bar) {
 }
 
 // waits for phase `parity` of the barrier; false if the wait ran out
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity,
+                                         long long limit = kWaitLimit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -658,6 +659,27 @@ __global__ void k_adam(int np, float* __restrict__ p, float* __restrict__ m, flo
 
 size_t mlp_fwd_smem() { return sizeof(FwdSmem); }
 size_t mlp_grad_smem() { return sizeof(GradSmem); }
+
+namespace {
+
+// One block whose mbarrier wait can never complete (one arrival expected,
+// none made): the wait gives up after `limit` polls and records the expiry
+// in the status word, as the tensor-core kernels do.
+__global__ void k_wait_selftest(long long limit, int* __restrict__ err) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) bar_init(smem_u32(&bar));
+  __syncthreads();
+  const bool ok = bar_wait(smem_u32(&bar), 0u, limit);
+  if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_wait_selftest(long long limit, int* err, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(limit, err);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mlp_forward(int M, const float* params, const float* cov, const float* c2w,
                                float* out, int exp_out, bool tc, int* err, int num_sms,

@@ -7,7 +7,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_size_t, c_uint64, c_void_p
+from ctypes import c_longlong, POINTER, c_char_p, c_double, c_float, c_int, c_size_t, c_uint64, c_void_p
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libcryosgd.so")
@@ -74,6 +74,7 @@ SIGNATURES = {
                                              c_uint64, P, P]),
     "cs_phase_shift": (c_int, [P, c_int, P, P, c_int, c_int, P]),
     "cs_set_slabs": (c_int, [P, c_int]),
+    "cs_selftest_wait_timeout": (c_int, [P, c_longlong, P]),
     "cs_fsc": (c_int, [P, c_int, P, P, c_int, P, P, P]),
     "cs_shell_minmax": (c_int, [P, c_int, P, c_int, P, P, P, P]),
     "cs_exact_diag": (c_int, [P, G, P, P, c_int, c_float, c_float, P, P, P, P]),

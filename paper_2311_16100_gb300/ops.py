@@ -355,6 +355,12 @@ class Handle:
     def check_device_status(self):
         self._check("cs_check_device_status", self.lib.cs_check_device_status(self.h))
 
+    def selftest_wait_timeout(self, spins=1000, stream=None):
+        """A bounded device-side wait that runs out: the next
+        check_device_status raises with CS_ERR_TIMEOUT."""
+        self._check("cs_selftest_wait_timeout",
+                    self.lib.cs_selftest_wait_timeout(self.h, int(spins), _stream(stream)))
+
     def phase_shift(self, images, shifts, sign=-1, stream=None):
         """In place: images[i] *= T_i (sign +1) or conj(T_i) (sign -1)."""
         B, M = images.shape[0], images.shape[1]
