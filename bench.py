@@ -956,7 +956,29 @@ def cpu_baseline(cfg, n):
                       f"Hutchinson, literal Armijo loop) per host core, {max(1, n // 8)} images "
                       f"each of the {cfg['M']}^3 workload, {cores} single-threaded replicas "
                       f"started together, {wall:.1f} s wall",
-            "single_core": single, "host_cores": cores}
+            "single_core": single, "host_cores": cores,
+            "operators_single_core": oracle_operators(cfg)}
+
+
+def oracle_operators(cfg):
+    """The oracle's loss + gradient and Hutchinson estimate alone, one core:
+    16 images of this workload, and 4 images of the 256^3 one."""
+    import oracle as O
+    out = {}
+    for label, c, n in (("%d^3" % cfg["M"], cfg, 16), ("256^3", CONFIGS["m256"], 4)):
+        S = oracle_sample(c, n, c["seed"] + 600)
+        t0 = time.perf_counter()
+        O.loss_grad(S["v0"], S["x"], S["R"], S["df"], c["M"], S["r"], c["interp"], S["ctf"],
+                    S["lam"], 1.0)
+        t1 = time.perf_counter()
+        out[label] = {"loss_grad_images_per_s": round(n / (t1 - t0), 3)}
+        if c is cfg:
+            t0 = time.perf_counter()
+            O.hutchinson_diag(S["R"], S["df"], c["M"], S["r"], c["interp"], S["ctf"], S["lam"],
+                              1.0, c["K"], 1, 1)
+            t1 = time.perf_counter()
+            out[label]["hutchinson_images_per_s"] = round(n / (t1 - t0), 3)
+    return out
 
 
 def run_reference(args, cfg, rank, world):
