@@ -448,6 +448,34 @@ class SGDState:
         self._cs = s
         return s
 
+    # ------------------------------------------------------ checkpointing
+    def state_dict(self) -> dict:
+        """Everything Algorithm 1 carries between iterations: v, D, D_avg,
+        the scalar block (eta, iteration count k, alpha, ...) and the
+        hyper-parameters.  Probes are counter-based (iteration k uses probe
+        block k + 1), so restoring this resumes the same trajectory."""
+        return {"v": self.v.detach().cpu(), "D": self.D.detach().cpu(),
+                "D_avg": self.D_avg.detach().cpu(), "scalars": self.scalars.detach().cpu(),
+                "mode": self.mode, "n_probes": self.n_probes, "seed": self.seed,
+                "beta": self.beta, "armijo_c": self.armijo_c, "max_halvings": self.max_halvings}
+
+    @classmethod
+    def from_state_dict(cls, sd: dict, device=None) -> "SGDState":
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+        st = cls(sd["v"].to(dev), mode=sd["mode"], n_probes=sd["n_probes"], seed=sd["seed"],
+                 beta=sd["beta"], armijo_c=sd["armijo_c"], max_halvings=sd["max_halvings"],
+                 D=sd["D"].to(dev))
+        st.D_avg.copy_(sd["D_avg"].to(dev))
+        st.scalars.copy_(sd["scalars"].to(dev))
+        return st
+
+    def save(self, path: str):
+        torch.save(self.state_dict(), path)
+
+    @classmethod
+    def load(cls, path: str, device=None) -> "SGDState":
+        return cls.from_state_dict(torch.load(path, map_location="cpu"), device)
+
 
 class Problem:
     """One refinement problem of a multi-volume step: geometry, SGD state and
