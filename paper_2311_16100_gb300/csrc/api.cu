@@ -191,8 +191,6 @@ int ensure_ws(cs_handle* h, int M, int B, Workspace* w) {
   return CS_OK;
 }
 
-// Disc pixel table of the vector passes for grid M, disc r (rebuilt on the
-// stream when the grid, the disc or the workspace changed).
 // The traversals of grids split into z-slabs use the tile-ordered disc
 // table (whole items outside a slab are skipped); one slab keeps the
 // row-ordered table (no idle lanes on the disc's edge tiles).
@@ -201,7 +199,8 @@ bool tiled_table(const cs_handle* h, int M) {
   return S > 1;
 }
 
-// Builds the disc table the handle's traversals of (M, r) need, once.
+// Disc pixel table of the vector passes for grid M, disc r: rebuilt on the
+// stream when the grid, the disc, the layout or the workspace changed.
 cudaError_t prepare_vector(cs_handle* h, const Workspace& w, int M, int r, cudaStream_t s) {
   const bool tiled = tiled_table(h, M);
   const int key = ((tiled ? 1 + (h->block == 128) : 0) << 28) | (M << 12) | r;
@@ -216,7 +215,6 @@ cudaError_t prepare_vector(cs_handle* h, const Workspace& w, int M, int r, cudaS
 
 bool use_tiles(const cs_handle* h) { return h->algo == CS_ALGO_TILED; }
 
-// grid of the single-problem trilinear traversals (launch shape of the handle)
 // Grid of a vector traversal: one block per item up to num_sms x the blocks
 // per SM of the handle's launch shape.  The gather-only curvature pass is
 // capped at the blocks resident at once (one wave: measured 9% faster at
