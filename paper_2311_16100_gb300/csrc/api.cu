@@ -743,10 +743,9 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
     int nvv = 0, nd = 0;
     prof_mark(h, 0, s);
     CS_CUDA(prepare_vector(h, w, g->M, g->r_max, s), "vector pass set-up");
-    if (hutch) CS_CUDA(launch_zero_r4(g->M, w.fw, s), "zero accumulators");
-    CS_CUDA(launch_zero_c2(g->M, w.fw, s), "zero accumulators");
-    CS_CUDA(launch_pairs(g->M, reinterpret_cast<const float2*>(st->v), w.fw.pairs, h->num_sms, s),
-            "pairs launch");
+    CS_CUDA(launch_step_prep(g->M, reinterpret_cast<const float2*>(st->v), w.fw, hutch,
+                             h->num_sms, s),
+            "step set-up launch");
     prof_mark(h, CS_PH_LOSS_GRAD, s);
     CS_CUDA(launch_fused(hutch ? (F_GRAD | F_HUTCH) : F_GRAD, G, w.fw, rot, defocus, B, scale,
                          reinterpret_cast<const float2*>(st->v), w.fw.pairs, nullptr,
@@ -1117,11 +1116,9 @@ int multi_step_enqueue(cs_handle* h, const cs_problem* P, int n, const ProblemWs
     CS_CUDA(launch_quat_to_rot_cursor(q.quat, q.B, q.n_batches, q.state.scalars + CS_S_K,
                                       W[p].rot, s),
             "quat_to_rot launch");
-    if (hutch) CS_CUDA(launch_zero_r4(M, W[p].fw, s), "zero accumulators");
-    CS_CUDA(launch_zero_c2(M, W[p].fw, s), "zero accumulators");
-    CS_CUDA(launch_pairs(M, reinterpret_cast<const float2*>(q.state.v), W[p].fw.pairs,
-                         h->num_sms, s),
-            "pairs launch");
+    CS_CUDA(launch_step_prep(M, reinterpret_cast<const float2*>(q.state.v), W[p].fw, hutch,
+                             h->num_sms, s),
+            "step set-up launch");
     BA[p] = problem_args(q, W[p], make_geo(q.geom));
     BA[p].part = W[p].part;                     // loss partials
   }

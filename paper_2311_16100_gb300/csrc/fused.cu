@@ -607,6 +607,26 @@ k_pairs(int M, const float2* __restrict__ v, float4* __restrict__ vp) {
   }
 }
 
+// Set-up of a step's traversal in one pass over the voxels: E = O = 0,
+// the four patch buffers P = 0 (zero_p), vp = pair layout of v.
+__global__ void __launch_bounds__(256)
+k_step_prep(int M, const float2* __restrict__ v, float2* __restrict__ E, float2* __restrict__ O,
+            float* __restrict__ P, float4* __restrict__ vp, int zero_p) {
+  const int n = M * M * M;
+  const float2 z2 = make_float2(0.f, 0.f);
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
+    E[j] = z2;
+    O[j] = z2;
+    if (zero_p) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) P[(size_t)b * n + j] = 0.f;
+    }
+    const float2 a = v[j];
+    const float2 c = (j % M) != M - 1 ? v[j + 1] : z2;
+    vp[j] = make_float4(a.x, a.y, c.x, c.y);
+  }
+}
+
 // g = lambda v + E + shift(O), and |v|^2 partials
 __global__ void __launch_bounds__(256)
 k_combine_c2(int M, const float2* v, float lambda, float2* __restrict__ E,
@@ -981,6 +1001,14 @@ cudaError_t launch_update_pairs(int M, float2* v, const FusedWs& w, const double
                                 int num_sms, cudaStream_t s) {
   const int n = M * M * M;
   k_update_pairs<<<elem_grid(n, num_sms), 256, 0, s>>>(n, v, w.pairs, scalars);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_prep(int M, const float2* v, const FusedWs& w, bool zero_p, int num_sms,
+                             cudaStream_t s) {
+  k_step_prep<<<elem_grid(M * M * M, num_sms), 256, 0, s>>>(M, v, w.E, w.O, w.P, w.pairs,
+                                                           zero_p ? 1 : 0);
   count_launches(1);
   return cudaGetLastError();
 }

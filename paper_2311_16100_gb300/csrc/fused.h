@@ -115,6 +115,9 @@ cudaError_t launch_update_pairs(int M, float2* v, const FusedWs& w, const double
                                 int num_sms, cudaStream_t s);
 // vp[j] = (v[j], v[j+1]), 0 past each row's end.
 cudaError_t launch_pairs(int M, const float2* v, float4* vp, int num_sms, cudaStream_t s);
+// zero E, O (and P when zero_p) and write the pair layout of v, in one pass
+cudaError_t launch_step_prep(int M, const float2* v, const FusedWs& w, bool zero_p, int num_sms,
+                             cudaStream_t s);
 cudaError_t launch_zero_c2(int M, const FusedWs& w, cudaStream_t s);
 cudaError_t launch_zero_r4(int M, const FusedWs& w, cudaStream_t s);
 // g = lambda v + E + shift(O) (v may be NULL); |v|^2 partials if part_vv.
