@@ -694,7 +694,9 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
   const double k = sc[CS_S_K] + 1.0;
   const float wold = (float)((k - 1.0) / k), wnew = (float)(1.0 / k);
   const float alpha = (float)sc[CS_S_ALPHA];
-  double aG = 0.0, aD = 0.0, aV = 0.0;
+  // per-thread partial sums of a few voxels in FP32 (FP64 arithmetic is a
+  // small fraction of the FP32 rate), combined across the block in FP64
+  float aG = 0.f, aD = 0.f, aV = 0.f;
   for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
     const int x = j % M, y = (j / M) % M, z = j / (M * M);
     float dh = 1.0f;
@@ -735,13 +737,13 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
     dp2[2 * (size_t)j] = d;
     if (x >= 1) dp2[2 * (size_t)j - 1] = d;
     if (x == M - 1) dp2[2 * (size_t)j + 1] = make_float2(0.f, 0.f);
-    aG += (double)(fmaf(g.x, g.x, g.y * g.y) * inv);
-    aD += (double)fmaf(d.x, d.x, d.y * d.y);
-    aV += (double)fmaf(vv.x, vv.x, vv.y * vv.y);
+    aG += fmaf(g.x, g.x, g.y * g.y) * inv;
+    aD += fmaf(d.x, d.x, d.y * d.y);
+    aV += fmaf(vv.x, vv.x, vv.y * vv.y);
   }
-  const double tG = block_sum(aG);
-  const double tD = block_sum(aD);
-  const double tV = block_sum(aV);
+  const double tG = block_sum((double)aG);
+  const double tD = block_sum((double)aD);
+  const double tV = block_sum((double)aV);
   if (threadIdx.x == 0) {
     partG[blockIdx.x] = tG;
     partG[nb + blockIdx.x] = tD;
