@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(256)
 k_combine_c2(int M, const float2* v, float lambda, float2* __restrict__ E,
              float2* __restrict__ O, float2* g, double* __restrict__ part) {
   const int n = M * M * M;
-  double accv = 0.0;
+  float accv = 0.f;     // a few voxels per thread in FP32; the block sum in FP64
   for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
     const int x = j % M;
     float2 a = v ? v[j] : make_float2(0.f, 0.f);
@@ -643,10 +643,10 @@ k_combine_c2(int M, const float2* v, float lambda, float2* __restrict__ E,
       r.y += o.y;
     }
     g[j] = make_float2(fmaf(lambda, a.x, r.x), fmaf(lambda, a.y, r.y));
-    accv += (double)fmaf(a.x, a.x, a.y * a.y);
+    accv += fmaf(a.x, a.x, a.y * a.y);
   }
   if (part) {
-    const double t = block_sum(accv);
+    const double t = block_sum((double)accv);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
   }
 }

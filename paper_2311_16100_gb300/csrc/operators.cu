@@ -126,13 +126,13 @@ k_backproject(Geo G, const float2* __restrict__ img, const float* __restrict__ r
 __global__ void __launch_bounds__(kBlock)
 k_init_grad(int n, const float2* __restrict__ v, float lambda, float2* __restrict__ g,
             double* __restrict__ part) {
-  double acc = 0.0;
+  float acc = 0.f;     // a few voxels per thread in FP32; the block sum in FP64
   for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) {
     float2 x = v[j];
     g[j] = make_float2(lambda * x.x, lambda * x.y);
-    acc += (double)fmaf(x.x, x.x, x.y * x.y);
+    acc += fmaf(x.x, x.x, x.y * x.y);
   }
-  double t = block_sum(acc);
+  double t = block_sum((double)acc);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 

@@ -93,17 +93,17 @@ k_running_mean(int n, const float* __restrict__ est, float* __restrict__ D, floa
 __global__ void __launch_bounds__(kBlock)
 k_direction(int n, const float2* __restrict__ g, const float* __restrict__ dhat,
             float2* __restrict__ d, double* __restrict__ part) {
-  double aG = 0.0, aD = 0.0;
+  float aG = 0.f, aD = 0.f;   // a few voxels per thread in FP32; block sums in FP64
   for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) {
     float2 x = g[j];
     float inv = dhat ? 1.0f / dhat[j] : 1.0f;
     float2 y = make_float2(x.x * inv, x.y * inv);
     d[j] = y;
-    aG += (double)(fmaf(x.x, x.x, x.y * x.y) * inv);
-    aD += (double)fmaf(y.x, y.x, y.y * y.y);
+    aG += fmaf(x.x, x.x, x.y * x.y) * inv;
+    aD += fmaf(y.x, y.x, y.y * y.y);
   }
-  double tG = block_sum(aG);
-  double tD = block_sum(aD);
+  double tG = block_sum((double)aG);
+  double tD = block_sum((double)aD);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = tG;
     part[gridDim.x + blockIdx.x] = tD;
@@ -186,18 +186,18 @@ __global__ void __launch_bounds__(kBlock)
 k_rel_err_part(Geo G, const float2* __restrict__ v, const float2* __restrict__ r,
                double* __restrict__ part) {
   const int n = G.M * G.M * G.M;
-  double e = 0.0, t = 0.0;
+  float e = 0.f, t = 0.f;     // a few voxels per thread in FP32; block sums in FP64
   for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) {
     int x = j % G.M, y = (j / G.M) % G.M, z = j / (G.M * G.M);
     int kx = x - G.half, ky = y - G.half, kz = z - G.half;
     if (kx * kx + ky * ky + kz * kz > G.r2max) continue;
     float2 a = v[j], b = r[j];
     float dx = a.x - b.x, dy = a.y - b.y;
-    e += (double)fmaf(dx, dx, dy * dy);
-    t += (double)fmaf(b.x, b.x, b.y * b.y);
+    e += fmaf(dx, dx, dy * dy);
+    t += fmaf(b.x, b.x, b.y * b.y);
   }
-  double se = block_sum(e);
-  double st = block_sum(t);
+  double se = block_sum((double)e);
+  double st = block_sum((double)t);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = se;
     part[gridDim.x + blockIdx.x] = st;
