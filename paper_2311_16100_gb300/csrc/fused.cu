@@ -460,7 +460,7 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
     const int p = chc * bd + threadIdx.x;
     if (p >= n_px) continue;
     const int e = __ldg(A.table + p);
-    if (e < 0) continue;
+    if ((FL & F_SLAB) && e < 0) continue;    // only the tile-ordered table has holes
     const int ix = e & 0xffff, iy = e >> 16;
     const int kx = ix - G.half, ky = iy - G.half;
     const Rot R = load_rot(A.rot, b);
