@@ -168,4 +168,44 @@ __device__ __forceinline__ double block_sum(double v) {
   return t;
 }
 
+// Sum of p[0 .. n) by one warp in a fixed order: lane l adds p[l], p[l + 32],
+// ... in four FP64 chains, then the warp adds its lanes.  FP64 arithmetic runs
+// at a small fraction of the FP32 rate on this part: a warp per array, instead
+// of a block-wide FP64 tree, keeps the count of FP64 warp instructions low.
+// Every lane must call; the result is valid in every lane.
+__device__ __forceinline__ double warp_sum_array(const double* p, int n) {
+  const int lane = threadIdx.x & 31;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int i = lane;
+  for (; i + 96 < n; i += 128) {
+    s0 += p[i];
+    s1 += p[i + 32];
+    s2 += p[i + 64];
+    s3 += p[i + 96];
+  }
+  for (; i < n; i += 32) s0 += p[i];
+  return warp_sum((s0 + s1) + (s2 + s3));
+}
+
+// Block-wide sum of FP32 per-thread values: each warp adds its lanes in
+// FP32 (a fixed butterfly), and thread 0 adds the warp sums in FP64 in warp
+// order.  FP64 arithmetic runs at a small fraction of the FP32 rate on this
+// part, so only that last level uses it.  Deterministic; every thread must
+// call; result valid in thread 0.  blockDim.x a multiple of 32, <= 1024.
+__device__ __forceinline__ double block_sum_f(float v) {
+  __shared__ double redf[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) redf[wid] = (double)v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int q = 0; q < nw; ++q) t += redf[q];
+  }
+  return t;
+}
+
 }  // namespace cs

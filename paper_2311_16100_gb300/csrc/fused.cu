@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(256)
 k_fused(FusedArgs A) {
   const float acc = fused_traverse<FL>(A, blockIdx.x, gridDim.x);
   if (FL & (F_GRAD | F_CURV)) {
-    const double t = block_sum((double)acc);
+    const double t = block_sum_f(acc);
     if (threadIdx.x == 0)
       A.part[blockIdx.x] = ((FL & F_SLAB) && A.part_add) ? A.part[blockIdx.x] + t : t;
   }
@@ -591,7 +591,7 @@ k_fused_multi(MultiFusedArgs MA) {
   const int nb = MA.start[p + 1] - MA.start[p];
   const float acc = fused_traverse<FL>(MA.a[p], lb, nb);
   if (FL & (F_GRAD | F_CURV)) {
-    const double t = block_sum((double)acc);
+    const double t = block_sum_f(acc);
     if (threadIdx.x == 0) MA.a[p].part[lb] = t;
   }
 }
@@ -632,7 +632,8 @@ __global__ void __launch_bounds__(256)
 k_combine_c2(int M, const float2* v, float lambda, float2* __restrict__ E,
              float2* __restrict__ O, float2* g, double* __restrict__ part) {
   const int n = M * M * M;
-  float accv = 0.f;     // a few voxels per thread in FP32; the block sum in FP64
+  // a few voxels per thread in FP32, warp sums in FP32, the block sum in FP64
+  float accv = 0.f;
   for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
     const int x = j % M;
     float2 a = v ? v[j] : make_float2(0.f, 0.f);
@@ -646,7 +647,7 @@ k_combine_c2(int M, const float2* v, float lambda, float2* __restrict__ E,
     accv += fmaf(a.x, a.x, a.y * a.y);
   }
   if (part) {
-    const double t = block_sum((double)accv);
+    const double t = block_sum_f(accv);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
   }
 }
@@ -695,7 +696,8 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
   const float wold = (float)((k - 1.0) / k), wnew = (float)(1.0 / k);
   const float alpha = (float)sc[CS_S_ALPHA];
   // per-thread partial sums of a few voxels in FP32 (FP64 arithmetic is a
-  // small fraction of the FP32 rate), combined across the block in FP64
+  // small fraction of the FP32 rate), warp sums in FP32, the block's warp
+  // sums added in FP64
   float aG = 0.f, aD = 0.f, aV = 0.f;
   for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
     const int x = j % M, y = (j / M) % M, z = j / (M * M);
@@ -741,9 +743,9 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
     aD += fmaf(d.x, d.x, d.y * d.y);
     aV += fmaf(vv.x, vv.x, vv.y * vv.y);
   }
-  const double tG = block_sum((double)aG);
-  const double tD = block_sum((double)aD);
-  const double tV = block_sum((double)aV);
+  const double tG = block_sum_f(aG);
+  const double tD = block_sum_f(aD);
+  const double tV = block_sum_f(aV);
   if (threadIdx.x == 0) {
     partG[blockIdx.x] = tG;
     partG[nb + blockIdx.x] = tD;

@@ -126,13 +126,14 @@ k_backproject(Geo G, const float2* __restrict__ img, const float* __restrict__ r
 __global__ void __launch_bounds__(kBlock)
 k_init_grad(int n, const float2* __restrict__ v, float lambda, float2* __restrict__ g,
             double* __restrict__ part) {
-  float acc = 0.f;     // a few voxels per thread in FP32; the block sum in FP64
+  // a few voxels per thread in FP32, warp sums in FP32, the block sum in FP64
+  float acc = 0.f;
   for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) {
     float2 x = v[j];
     g[j] = make_float2(lambda * x.x, lambda * x.y);
     acc += fmaf(x.x, x.x, x.y * x.y);
   }
-  double t = block_sum((double)acc);
+  double t = block_sum_f(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -157,22 +158,23 @@ k_loss_grad(Geo G, const float2* __restrict__ vol, const float2* __restrict__ im
     float sc = scale * C;
     scatter<I>(S, make_float2(sc * rr, sc * ri), grad);
   }
-  double t = block_sum((double)acc);
+  double t = block_sum_f(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// loss = scale/2 * sum(pl) + lambda/2 * sum(pv), fixed summation order
-__global__ void __launch_bounds__(1024)
+// loss = scale/2 * sum(pl) + lambda/2 * sum(pv), fixed summation order (one
+// warp per array)
+__global__ void __launch_bounds__(64)
 k_finalize_loss(const double* __restrict__ pl, int nl, const int* __restrict__ nl_dev,
                 const double* __restrict__ pv, int nv, float lambda, float scale,
                 double* loss) {
+  __shared__ double st[2];
   if (nl_dev) nl = *nl_dev;
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < nl; i += blockDim.x) a += pl[i];
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) b += pv[i];
-  a = block_sum(a);
-  b = block_sum(b);
-  if (threadIdx.x == 0) *loss = 0.5 * (double)scale * a + 0.5 * (double)lambda * b;
+  const int a = threadIdx.x >> 5;
+  const double v = a == 0 ? warp_sum_array(pl, nl) : warp_sum_array(pv, nv);
+  if ((threadIdx.x & 31) == 0) st[a] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) *loss = 0.5 * (double)scale * st[0] + 0.5 * (double)lambda * st[1];
 }
 
 __global__ void __launch_bounds__(kBlock)
@@ -299,7 +301,7 @@ k_curvature(Geo G, const float2* __restrict__ d, const float* __restrict__ rot,
     float C = image_ctf(G, df, it.b, it.q);
     acc = fmaf(C * C, fmaf(a.x, a.x, a.y * a.y), acc);
   }
-  double t = block_sum((double)acc);
+  double t = block_sum_f(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -344,7 +346,7 @@ cudaError_t launch_loss_grad(const Geo& G, const float2* vol, const float2* img,
   count_launches(1);
   if (B > 0) { CS_DISPATCH(G, k_loss_grad, G, vol, img, rot, df, B, scale, grad, part_loss); count_launches(1); }
   if (loss) {
-    k_finalize_loss<<<1, 1024, 0, s>>>(part_loss, B > 0 ? grid : 0, nullptr, part_vv, gi,
+    k_finalize_loss<<<1, 64, 0, s>>>(part_loss, B > 0 ? grid : 0, nullptr, part_vv, gi,
                                        lambda, scale, loss);
     count_launches(1);
   }
@@ -416,7 +418,7 @@ cudaError_t launch_init_grad(int n, const float2* vol, float lambda, float2* gra
 cudaError_t launch_finalize_loss(const double* pl, int n, const int* n_dev, const double* pv,
                                  int nv, float lambda, float scale, double* loss,
                                  cudaStream_t s) {
-  k_finalize_loss<<<1, 1024, 0, s>>>(pl, n, n_dev, pv, nv, lambda, scale, loss);
+  k_finalize_loss<<<1, 64, 0, s>>>(pl, n, n_dev, pv, nv, lambda, scale, loss);
   count_launches(1);
   return cudaGetLastError();
 }

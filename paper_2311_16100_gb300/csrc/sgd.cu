@@ -93,7 +93,8 @@ k_running_mean(int n, const float* __restrict__ est, float* __restrict__ D, floa
 __global__ void __launch_bounds__(kBlock)
 k_direction(int n, const float2* __restrict__ g, const float* __restrict__ dhat,
             float2* __restrict__ d, double* __restrict__ part) {
-  float aG = 0.f, aD = 0.f;   // a few voxels per thread in FP32; block sums in FP64
+  // a few voxels per thread in FP32, warp sums in FP32, block sums in FP64
+  float aG = 0.f, aD = 0.f;
   for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) {
     float2 x = g[j];
     float inv = dhat ? 1.0f / dhat[j] : 1.0f;
@@ -102,37 +103,36 @@ k_direction(int n, const float2* __restrict__ g, const float* __restrict__ dhat,
     aG += fmaf(x.x, x.x, x.y * x.y) * inv;
     aD += fmaf(y.x, y.x, y.y * y.y);
   }
-  double tG = block_sum((double)aG);
-  double tD = block_sum((double)aD);
+  double tG = block_sum_f(aG);
+  double tD = block_sum_f(aD);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = tG;
     part[gridDim.x + blockIdx.x] = tD;
   }
 }
 
-__device__ double sum_fixed(const double* p, int n) {
-  double a = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a += p[i];
-  return block_sum(a);
-}
-
 // Closed-form stochastic Armijo: f_I(v - eta d) = f_I(v) - eta G + eta^2 Q/2
 // (f_I quadratic), so the halving loop of Algorithm 1 stops at the first
 // eta = eta_prev 2^-m with eta <= 2 (1 - c) G / Q.
-__global__ void __launch_bounds__(1024)
+// The five partial arrays (data term, |v|^2, G, |d|^2, curvature) are
+// summed one per warp (warp_sum_array).
+__global__ void __launch_bounds__(160)
 k_eta(double* sc, const double* pl, int nl, const double* pv, int nv, const double* pG,
       const double* pD, int nd, const double* pQ, int nq, const int* n_dev, float lambda,
       float scale, float c, int max_halvings) {
+  __shared__ double sum5[5];
   if (n_dev) {
     nl = *n_dev;
     nq = *n_dev;
   }
-  double L = sum_fixed(pl, nl);
-  double V = sum_fixed(pv, nv);
-  double G = sum_fixed(pG, nd);
-  double DD = sum_fixed(pD, nd);
-  double Qd = sum_fixed(pQ, nq);
+  const int lane = threadIdx.x & 31, a = threadIdx.x >> 5;
+  const double* p = a == 0 ? pl : a == 1 ? pv : a == 2 ? pG : a == 3 ? pD : pQ;
+  const int n = a == 0 ? nl : a == 1 ? nv : a == 4 ? nq : nd;
+  const double t = warp_sum_array(p, n);
+  if (lane == 0) sum5[a] = t;
+  __syncthreads();
   if (threadIdx.x != 0) return;
+  const double L = sum5[0], V = sum5[1], G = sum5[2], DD = sum5[3], Qd = sum5[4];
   double Q = (double)scale * Qd + (double)lambda * DD;
   double eta = sc[CS_S_ETA];
   int h = 0;
@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(kBlock)
 k_rel_err_part(Geo G, const float2* __restrict__ v, const float2* __restrict__ r,
                double* __restrict__ part) {
   const int n = G.M * G.M * G.M;
-  float e = 0.f, t = 0.f;     // a few voxels per thread in FP32; block sums in FP64
+  // a few voxels per thread in FP32, warp sums in FP32, block sums in FP64
+  float e = 0.f, t = 0.f;
   for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) {
     int x = j % G.M, y = (j / G.M) % G.M, z = j / (G.M * G.M);
     int kx = x - G.half, ky = y - G.half, kz = z - G.half;
@@ -196,19 +197,23 @@ k_rel_err_part(Geo G, const float2* __restrict__ v, const float2* __restrict__ r
     e += fmaf(dx, dx, dy * dy);
     t += fmaf(b.x, b.x, b.y * b.y);
   }
-  double se = block_sum((double)e);
-  double st = block_sum((double)t);
+  double se = block_sum_f(e);
+  double st = block_sum_f(t);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = se;
     part[gridDim.x + blockIdx.x] = st;
   }
 }
 
-__global__ void __launch_bounds__(1024)
+// two warps: the error and reference partials
+__global__ void __launch_bounds__(64)
 k_rel_err_final(const double* part, int nb, double* out) {
-  double e = sum_fixed(part, nb);
-  double t = sum_fixed(part + nb, nb);
-  if (threadIdx.x == 0) *out = t > 0.0 ? sqrt(e / t) : 0.0;
+  __shared__ double st[2];
+  const int a = threadIdx.x >> 5;
+  const double v = warp_sum_array(part + a * nb, nb);
+  if ((threadIdx.x & 31) == 0) st[a] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) *out = st[1] > 0.0 ? sqrt(st[0] / st[1]) : 0.0;
 }
 
 }  // namespace
@@ -265,7 +270,7 @@ cudaError_t launch_eta(double* scalars, const double* part_loss, int n_loss,
                        const double* part_dd, int n_dir, const double* part_Q, int n_Q,
                        const int* n_dev, float lambda, float scale, float c,
                        int max_halvings, cudaStream_t s) {
-  k_eta<<<1, 1024, 0, s>>>(scalars, part_loss, n_loss, part_vv, n_vv, part_G, part_dd,
+  k_eta<<<1, 160, 0, s>>>(scalars, part_loss, n_loss, part_vv, n_vv, part_G, part_dd,
                            n_dir, part_Q, n_Q, n_dev, lambda, scale, c, max_halvings);
   count_launches(1);
   return cudaGetLastError();
@@ -293,7 +298,7 @@ cudaError_t launch_rel_err(const Geo& G, const float2* v, const float2* vref,
   const int gb = elem_grid(n, num_sms);
   k_rel_err_part<<<gb, kBlock, 0, s>>>(G, v, vref, part);
   count_launches(1);
-  k_rel_err_final<<<1, 1024, 0, s>>>(part, gb, out);
+  k_rel_err_final<<<1, 64, 0, s>>>(part, gb, out);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -441,7 +441,7 @@ k_tile(TileArgs A) {
       }
     }
     if (Tr::kSum) {
-      const double s = block_sum((double)part);
+      const double s = block_sum_f(part);
       if (threadIdx.x == 0) A.part[item] = s;
     }
     __syncthreads();
