@@ -608,22 +608,36 @@ k_pairs(int M, const float2* __restrict__ v, float4* __restrict__ vp) {
 }
 
 // Set-up of a step's traversal in one pass over the voxels: E = O = 0,
-// the four patch buffers P = 0 (zero_p), vp = pair layout of v.
+// the four patch buffers P = 0 (zero_p), vp = pair layout of v.  Thread q
+// handles voxels q + k n/4, k = 0..3 (M is even, so n = M^3 is a multiple of
+// 4): the zeroing is done with 16-byte stores, and every access of a warp
+// stays contiguous across its lanes.
 __global__ void __launch_bounds__(256)
 k_step_prep(int M, const float2* __restrict__ v, float2* __restrict__ E, float2* __restrict__ O,
             float* __restrict__ P, float4* __restrict__ vp, int zero_p) {
-  const int n = M * M * M;
-  const float2 z2 = make_float2(0.f, 0.f);
-  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
-    E[j] = z2;
-    O[j] = z2;
+  const int n = M * M * M, n4 = n / 4;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4* E4 = reinterpret_cast<float4*>(E);
+  float4* O4 = reinterpret_cast<float4*>(O);
+  float4* P4 = reinterpret_cast<float4*>(P);
+  for (int q = blockIdx.x * 256 + threadIdx.x; q < n4; q += gridDim.x * 256) {
+    E4[q] = z4;
+    E4[q + n4] = z4;
+    O4[q] = z4;
+    O4[q + n4] = z4;
     if (zero_p) {
 #pragma unroll
-      for (int b = 0; b < 4; ++b) P[(size_t)b * n + j] = 0.f;
+      for (int b = 0; b < 4; ++b) P4[q + b * n4] = z4;
     }
-    const float2 a = v[j];
-    const float2 c = (j % M) != M - 1 ? v[j + 1] : z2;
-    vp[j] = make_float4(a.x, a.y, c.x, c.y);
+    float2 a[4], c[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int j = q + k * n4;
+      a[k] = v[j];
+      c[k] = (j % M) != M - 1 ? v[j + 1] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) vp[q + k * n4] = make_float4(a[k].x, a[k].y, c[k].x, c[k].y);
   }
 }
 
@@ -753,15 +767,24 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
   }
 }
 
-// v -= eta d, with d read from its pair layout
+// v -= eta d, with d read from its pair layout; thread q handles voxels
+// q + k n/4, k = 0..3, all loads issued before the stores
 __global__ void __launch_bounds__(256)
 k_update_pairs(int n, float2* __restrict__ v, const float4* __restrict__ dp,
                const double* __restrict__ sc) {
   const float eta = (float)sc[CS_S_ETA];
-  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
-    const float4 d = dp[j];
-    const float2 a = v[j];
-    v[j] = make_float2(fmaf(-eta, d.x, a.x), fmaf(-eta, d.y, a.y));
+  const int n4 = n / 4;
+  for (int q = blockIdx.x * 256 + threadIdx.x; q < n4; q += gridDim.x * 256) {
+    float4 d[4];
+    float2 a[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      d[k] = dp[q + k * n4];
+      a[k] = v[q + k * n4];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      v[q + k * n4] = make_float2(fmaf(-eta, d[k].x, a[k].x), fmaf(-eta, d[k].y, a[k].y));
   }
 }
 
@@ -1004,15 +1027,15 @@ cudaError_t launch_step_post(int M, int mode, const float2* v, float lambda, flo
 cudaError_t launch_update_pairs(int M, float2* v, const FusedWs& w, const double* scalars,
                                 int num_sms, cudaStream_t s) {
   const int n = M * M * M;
-  k_update_pairs<<<elem_grid(n, num_sms), 256, 0, s>>>(n, v, w.pairs, scalars);
+  k_update_pairs<<<elem_grid(n / 4, num_sms), 256, 0, s>>>(n, v, w.pairs, scalars);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_step_prep(int M, const float2* v, const FusedWs& w, bool zero_p, int num_sms,
                              cudaStream_t s) {
-  k_step_prep<<<elem_grid(M * M * M, num_sms), 256, 0, s>>>(M, v, w.E, w.O, w.P, w.pairs,
-                                                           zero_p ? 1 : 0);
+  k_step_prep<<<elem_grid(M * M * M / 4, num_sms), 256, 0, s>>>(M, v, w.E, w.O, w.P, w.pairs,
+                                                               zero_p ? 1 : 0);
   count_launches(1);
   return cudaGetLastError();
 }
