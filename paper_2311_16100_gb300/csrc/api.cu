@@ -224,7 +224,9 @@ int vec_grid(const cs_handle* h, int B, int M, int flags) {
   const long items = (long)B * (((long)M * M + h->block - 1) / h->block);
   int per_sm = h->blocks_per_sm;
   if (flags == F_CURV) {
-    const int res = fused_resident(flags, h->block, false);
+    // one wave of the kernel that will run (slab-split grids have their own)
+    const int f = tiled_table(h, M) ? (F_CURV | F_SLAB) : F_CURV;
+    const int res = fused_resident(f, h->block, false);
     if (res < per_sm) per_sm = res;
   }
   const long cap = (long)h->num_sms * per_sm;

@@ -97,7 +97,8 @@ int slab_count(int M, int flags);
 cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid, cudaStream_t s,
                               int block, int slabs, bool tiled);
 // Blocks of a traversal kernel (flags, block size; multi: the multi-volume
-// kernel) that fit on one SM at once.  A traversal grid larger than
+// kernel; F_CURV | F_SLAB: the slab-split curvature kernel) that fit on one
+// SM at once.  A traversal grid larger than
 // num_sms x this would run in more than one wave, the last one part-empty.
 int fused_resident(int flags, int block, bool multi);
 cudaError_t launch_fused_multi(int flags, const MultiFusedArgs& MA, int grid, int block,

@@ -53,7 +53,8 @@ def env():
         pytest.skip("no CUDA device")
     from paper_2311_16100_gb300 import ops
     h = ops.Handle(0)
-    sets = [Dataset(24, 8, 2, 11), Dataset(32, 12, 2, 22), Dataset(40, 6, 3, 33)]
+    # 38: x rows of a length that is not a multiple of 4
+    sets = [Dataset(24, 8, 2, 11), Dataset(32, 12, 2, 22), Dataset(38, 6, 3, 33)]
     yield ops, h, sets
     h.close()
 

@@ -231,13 +231,17 @@ def test_threshold_alpha(h):
 
 
 # ------------------------------------------------------------- Algorithm 1
-@pytest.mark.parametrize("mode,interp", [("hutchinson", "trilinear"), ("plain", "trilinear"),
-                                         ("hutchinson", "nearest"), ("fixed", "trilinear")])
-def test_precond_sgd_steps_follow_oracle(h, mode, interp):
+@pytest.mark.parametrize("mode,interp,M", [("hutchinson", "trilinear", 24),
+                                           ("plain", "trilinear", 24),
+                                           ("hutchinson", "nearest", 24),
+                                           ("fixed", "trilinear", 24),
+                                           ("hutchinson", "trilinear", 26)])
+def test_precond_sgd_steps_follow_oracle(h, mode, interp, M):
     """Three iterations of Algorithm 1 on consecutive mini-batches: the same
-    eta choices as the literal oracle loop and iterates within tolerance."""
+    eta choices as the literal oracle loop and iterates within tolerance
+    (M = 26: x rows of a length that is not a multiple of 4)."""
     from paper_2311_16100_gb300.ops import SGDState
-    M, B, nb = 24, 12, 3
+    B, nb = 12, 3
     c = Case(M, B * nb, interp=interp, ctf=True, seed=29)
     g = c.to_gpu()
     geom = c.gpu_geometry()
