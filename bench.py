@@ -341,10 +341,26 @@ def run_gpu(args, cfg, rank, world):
         ems = a0.elapsed_time(a1)
         ems, wall = max_over_ranks([ems, wall], world)
         assert bool(torch.isfinite(out_loss[: args.steps]).all()) and float(out_loss[0]) != 0.0
+        # the host-to-device rate alone: the same batches copied back to back
+        # with nothing else running bounds the end-to-end rate from above
+        dev_img = torch.empty_like(images[:B])
+        cs_ = torch.cuda.Stream()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(cs_):
+            dev_img.copy_(pin_img[0], non_blocking=True)
+            c0.record(cs_)
+            for i in range(args.steps):
+                dev_img.copy_(pin_img[i % nh], non_blocking=True)
+            c1.record(cs_)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1) / args.steps
+        del dev_img
         e2e = {"value": job_value(world, B, args.steps, ems), "unit": "images/s",
                "h2d_bytes_per_step": B * M * M * 8 + B * 16 + B * 4,
                "d2h_bytes_per_step": 8,
                "host_wall_value": round(job_value(world, B, args.steps, wall), 1),
+               "h2d_copy_only": {"GB_per_s": round(B * M * M * 8 / (cms / 1e3) / 1e9, 1),
+                                 "images_per_s_bound": round(world * B / (cms / 1e3), 1)},
                "api": "cs_precond_sgd_step_host (double-buffered staging, copy stream)"}
 
     # --- roofline of the dominant phase
