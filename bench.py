@@ -47,7 +47,7 @@ CONFIGS = {
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     p.add_argument("--config", choices=sorted(CONFIGS), default="m128")
