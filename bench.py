@@ -325,22 +325,31 @@ def run_gpu(args, cfg, rank, world):
                                     pin_df[j] if W["ctf"] else None, lam, scale,
                                     loss_host=out_loss[i])
 
-        for s in range(args.warmup):
-            e2e_step(s, s)
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        w0 = time.perf_counter()
-        a0.record(stream)
-        for i in range(args.steps):
-            e2e_step(i, i)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        wall = (time.perf_counter() - w0) * 1e3
-        ems = a0.elapsed_time(a1)
-        ems, wall = max_over_ranks([ems, wall], world)
-        assert bool(torch.isfinite(out_loss[: args.steps]).all()) and float(out_loss[0]) != 0.0
+        def e2e_run(mode):
+            h.set_host_mode(mode)
+            for s in range(args.warmup):
+                e2e_step(s, s)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            w0 = time.perf_counter()
+            a0.record(stream)
+            for i in range(args.steps):
+                e2e_step(i, i)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            wall_ = (time.perf_counter() - w0) * 1e3
+            ems_ = a0.elapsed_time(a1)
+            ems_, wall_ = max_over_ranks([ems_, wall_], world)
+            assert bool(torch.isfinite(out_loss[: args.steps]).all()) and float(out_loss[0]) != 0.0
+            return ems_, wall_
+
+        # the default (staged copies), then the direct reads of the images
+        # from the pinned buffers over the host link
+        ems, wall = e2e_run("staged")
+        ems_dir, _ = e2e_run("direct")
+        h.set_host_mode("staged")
         # the host-to-device rate alone: the same batches copied back to back
         # with nothing else running bounds the end-to-end rate from above
         dev_img = torch.empty_like(images[:B])
@@ -361,7 +370,10 @@ def run_gpu(args, cfg, rank, world):
                "host_wall_value": round(job_value(world, B, args.steps, wall), 1),
                "h2d_copy_only": {"GB_per_s": round(B * M * M * 8 / (cms / 1e3) / 1e9, 1),
                                  "images_per_s_bound": round(world * B / (cms / 1e3), 1)},
-               "api": "cs_precond_sgd_step_host (double-buffered staging, copy stream)"}
+               "direct_value": job_value(world, B, args.steps, ems_dir),
+               "api": "cs_precond_sgd_step_host (double-buffered staging copies on a copy "
+                      "stream; direct_value: the traversal reading the disc pixels from the "
+                      "pinned host buffer instead)"}
 
     # --- roofline of the dominant phase
     n_px = n_disc_pixels(M, M // 2 - 1)

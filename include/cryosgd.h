@@ -288,18 +288,26 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
 
 /* cs_precond_sgd_step on a batch held in HOST memory: images_host
  * complex64[B][M][M], quat_host float[B][4] (unit quaternions, w first),
- * defocus_host float[B] (NULL without CTF).  The batch is copied into one
- * of two device staging slots owned by the handle, on the handle's own copy
- * stream, after the step that last used that slot has finished; the step
- * (quaternions -> rotations, then Algorithm 1) runs on `stream` once its
- * copy is done, and if loss_host is not NULL the batch loss is copied to
- * *loss_host (a host double) after it.  Everything is asynchronous: the
- * call returns at once, so issuing step n+1 while step n runs overlaps the
- * copy of batch n+1 with the compute of step n.  Host buffers should be
- * page-locked (pinned) for the copies to be asynchronous; they must stay
- * valid and unmodified, and *loss_host unread, until `stream` has completed
- * the step.  Issue all steps of one handle on one stream.  Staging grows on
- * demand (device synchronisation, CS_ERR_ALLOC on failure).  Errors as
+ * defocus_host float[B] (NULL without CTF).  Two ways to move the batch
+ * (cs_set_host_mode; staged by default):
+ *   staged: the batch is copied into one of two device staging slots owned
+ *     by the handle, on the handle's own copy stream, after the step that
+ *     last used that slot has finished; the step runs on `stream` once its
+ *     copy is done, so issuing step n+1 while step n runs overlaps the copy
+ *     of batch n+1 with the compute of step n;
+ *   direct: when images_host is page-locked memory that the runtime maps
+ *     into the device's address space (cudaPointerGetAttributes reports a
+ *     host allocation with a device pointer), the traversal reads each disc
+ *     pixel straight from it over the host link (every pixel once, outside
+ *     the disc nothing), and only the poses and defoci are copied, on
+ *     `stream`; otherwise the staged path is taken.
+ * The step (quaternions -> rotations, then Algorithm 1) runs on `stream`;
+ * if loss_host is not NULL the batch loss is copied to *loss_host (a host
+ * double) after it.  Everything is asynchronous: the call returns at once.
+ * Host buffers should be page-locked (pinned); they must stay valid and
+ * unmodified, and *loss_host unread, until `stream` has completed the step.
+ * Issue all steps of one handle on one stream.  Staging grows on demand
+ * (device synchronisation, CS_ERR_ALLOC on failure).  Errors as
  * cs_precond_sgd_step, plus CS_ERR_ARG for NULL host pointers. */
 int cs_precond_sgd_step_host(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
                              const float* images_host, const float* quat_host,
@@ -402,6 +410,14 @@ int cs_set_launch_shape(cs_handle* h, int block_threads, int blocks_per_sm);
  * At most M/16 slabs are used.  Results are the same sums in another
  * order.  0 <= slabs <= 16. */
 int cs_set_slabs(cs_handle* h, int slabs);
+/* How cs_precond_sgd_step_host moves a batch: CS_HOST_STAGED (default:
+ * double-buffered staging copies) or CS_HOST_DIRECT (the traversal reads
+ * the images from the host buffer when it is device-mapped page-locked
+ * memory, staged copies otherwise).  Measured on GB300 at 128^3, batch 1024:
+ * staged 1.54 M images/s, direct 1.21 M (the link reads stall the
+ * traversal); at 256^3 the two are equal.  CS_ERR_ARG for another value. */
+enum { CS_HOST_STAGED = 0, CS_HOST_DIRECT = 1 };
+int cs_set_host_mode(cs_handle* h, int mode);
 /* Autotuner: times the fused traversal of these problems (without changing
  * their state) for a set of launch shapes, keeps the fastest on the handle
  * and returns it.  Synchronous. */

@@ -1273,6 +1273,14 @@ int cs_set_slabs(cs_handle* h, int slabs) {
   return CS_OK;
 }
 
+int cs_set_host_mode(cs_handle* h, int mode) {
+  if (!h) return CS_ERR_ARG;
+  if (mode != CS_HOST_STAGED && mode != CS_HOST_DIRECT)
+    return fail(h, CS_ERR_ARG, "host mode %d is not CS_HOST_STAGED or CS_HOST_DIRECT", mode);
+  h->host_mode = mode;
+  return CS_OK;
+}
+
 int cs_set_launch_shape(cs_handle* h, int block, int bps) {
   if (!h) return CS_ERR_ARG;
   if (block != 128 && block != 256)
@@ -1564,6 +1572,21 @@ StageSlot stage_slot(const cs_handle* h, int slot) {
   return s;
 }
 
+// Device address of page-locked host memory that the runtime has mapped
+// into the device's address space, or NULL (pageable or device memory, or
+// a host allocation without a device mapping).
+const float* mapped_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  // unified addressing: the device address of mapped host memory is the
+  // host address; anything else takes the staged path
+  if (a.type != cudaMemoryTypeHost || a.devicePointer != p) return nullptr;
+  return static_cast<const float*>(a.devicePointer);
+}
+
 int ensure_stage(cs_handle* h, int M, int B) {
   if (!h->copy_stream) {
     CS_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
@@ -1612,6 +1635,29 @@ int cs_precond_sgd_step_host(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
   const int slot = (int)(h->stage_calls & 1u);
   const StageSlot d = stage_slot(h, slot);
   cudaStream_t cs = S(stream), cp = h->copy_stream;
+  const float* dimg =
+      h->host_mode == CS_HOST_DIRECT ? mapped_device_pointer(images_host) : nullptr;
+  if (dimg) {
+    // direct: the traversal reads the images from host memory; the poses
+    // and defoci (a few KB) are copied on the compute stream
+    CS_CUDA(cudaMemcpyAsync(d.quat, quat_host, (size_t)B * 16, cudaMemcpyHostToDevice, cs),
+            "pose copy");
+    if (defocus_host)
+      CS_CUDA(cudaMemcpyAsync(d.defocus, defocus_host, (size_t)B * 4, cudaMemcpyHostToDevice, cs),
+              "defocus copy");
+    CS_TRY(cs_quat_to_rot(h, d.quat, B, d.rot, stream));
+    CS_TRY(cs_precond_sgd_step(h, g, st, dimg, d.rot, defocus_host ? d.defocus : nullptr, B,
+                               lambda, scale, stream));
+    if (loss_host)
+      CS_CUDA(cudaMemcpyAsync(loss_host, st->scalars + CS_S_LOSS, sizeof(double),
+                              cudaMemcpyDeviceToHost, cs),
+              "loss read-back");
+    // the staged slots are not touched, but keep the slot events ordered
+    // after this step so that a later staged call waits for it
+    CS_CUDA(cudaEventRecord(h->compute_done[slot], cs), "compute event");
+    ++h->stage_calls;
+    return CS_OK;
+  }
   const size_t nimg = (size_t)B * g->M * g->M * 8;
   CS_CUDA(cudaStreamWaitEvent(cp, h->compute_done[slot], 0), "copy stream wait");
   CS_CUDA(cudaMemcpyAsync(d.images, images_host, nimg, cudaMemcpyHostToDevice, cp), "image copy");

@@ -40,6 +40,7 @@ struct cs_handle {
   int prof_steps = 0;
   std::vector<cudaEvent_t> prof_events;
   // double-buffered staging of host batches (cs_precond_sgd_step_host)
+  int host_mode = 0;          // CS_HOST_STAGED / CS_HOST_DIRECT
   void* stage = nullptr;
   int stage_M = 0, stage_B = 0;
   unsigned long long stage_calls = 0;

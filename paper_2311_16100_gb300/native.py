@@ -16,6 +16,7 @@ CS_OK, CS_ERR_ARG, CS_ERR_SHAPE, CS_ERR_CUDA, CS_ERR_TIMEOUT, CS_ERR_INTERNAL, C
 CS_NEAREST, CS_TRILINEAR = 0, 1
 CS_PLAIN, CS_HUTCHINSON, CS_FIXED = 0, 1, 2
 CS_ALGO_AUTO, CS_ALGO_PIXEL, CS_ALGO_TILED, CS_ALGO_VECTOR = 0, 1, 2, 3
+CS_HOST_STAGED, CS_HOST_DIRECT = 0, 1
 (CS_S_ETA, CS_S_K, CS_S_ALPHA, CS_S_LOSS, CS_S_G, CS_S_Q, CS_S_HALVINGS,
  CS_S_STATUS, CS_NSCALARS) = range(9)
 CS_MAX_M = 512
@@ -74,6 +75,7 @@ SIGNATURES = {
                                              c_uint64, P, P]),
     "cs_phase_shift": (c_int, [P, c_int, P, P, c_int, c_int, P]),
     "cs_set_slabs": (c_int, [P, c_int]),
+    "cs_set_host_mode": (c_int, [P, c_int]),
     "cs_selftest_wait_timeout": (c_int, [P, c_longlong, P]),
     "cs_fsc": (c_int, [P, c_int, P, P, c_int, P, P, P]),
     "cs_shell_minmax": (c_int, [P, c_int, P, c_int, P, P, P, P]),

@@ -314,6 +314,13 @@ class Handle:
         """z-slabs per vector traversal (0: chosen from the grid's footprint)."""
         self._check("cs_set_slabs", self.lib.cs_set_slabs(self.h, int(slabs)))
 
+    def set_host_mode(self, mode: str):
+        """How precond_sgd_step_host moves a batch: "staged" (default) or
+        "direct" (the traversal reads the images from device-mapped pinned
+        memory; staged copies for other buffers)."""
+        m = {"staged": N.CS_HOST_STAGED, "direct": N.CS_HOST_DIRECT}[mode]
+        self._check("cs_set_host_mode", self.lib.cs_set_host_mode(self.h, m))
+
     def set_launch_shape(self, block_threads: int, blocks_per_sm: int):
         self._check("cs_set_launch_shape",
                     self.lib.cs_set_launch_shape(self.h, block_threads, blocks_per_sm))

@@ -1,6 +1,7 @@
-"""Steps fed from host memory (cs_precond_sgd_step_host): double-buffered
-staging on the handle's copy stream must give the same iterates as steps on
-device-resident batches, and the loss read back into host memory."""
+"""Steps fed from host memory (cs_precond_sgd_step_host): direct reads from
+mapped pinned memory and double-buffered staging on the handle's copy stream
+must give the same iterates as steps on device-resident batches, and the
+loss read back into host memory."""
 import numpy as np
 import pytest
 
@@ -16,8 +17,10 @@ def make_state(ops, c, alpha):
                         n_probes=8, seed=5)
 
 
-@pytest.mark.parametrize("pinned", [True, False])
-def test_host_steps_match_device_steps(pinned):
+@pytest.mark.parametrize("pinned,mode", [(True, "direct"), (True, "staged"), (False, "direct")])
+def test_host_steps_match_device_steps(pinned, mode):
+    """pinned + direct: the traversal reads the images from host memory;
+    pinned + staged, and pageable memory in either mode: staged copies."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2311_16100_gb300 import ops
@@ -25,6 +28,7 @@ def test_host_steps_match_device_steps(pinned):
     c = Case(32, B * nb, interp="trilinear", ctf=True, seed=81)
     geom = c.gpu_geometry()
     h_dev, h_host = ops.Handle(0), ops.Handle(0)
+    h_host.set_host_mode(mode)
     g = c.to_gpu()
     alpha = float(h_dev.threshold_alpha(geom, g["df"], B * nb, 0.01))
     st_dev, st_host = make_state(ops, c, alpha), make_state(ops, c, alpha)
@@ -69,4 +73,8 @@ def test_host_step_rejects_bad_arguments():
         h.precond_sgd_step_host(c.gpu_geometry(), st, img, q, None, 0.01, 1.0)
     with pytest.raises(ValueError):            # device tensor where host memory is required
         h.precond_sgd_step_host(c.gpu_geometry(), st, img.cuda(), q, None, 0.01, 1.0)
+    with pytest.raises(KeyError):
+        h.set_host_mode("zero-copy")
+    with pytest.raises(CryoSGDError):
+        h._check("cs_set_host_mode", h.lib.cs_set_host_mode(h.h, 7))
     h.close()
