@@ -55,15 +55,7 @@ Workspace carve(void* base, int M, int B) {
   w.queue = reinterpret_cast<int*>(p);      p += align256(sizeof(int));
   w.part_items = reinterpret_cast<double*>(p); p += align256(items * sizeof(double));
   w.part_items2 = reinterpret_cast<double*>(p); p += align256(items * sizeof(double));
-  {  // per-slab item lists of the slab-split traversals
-    const size_t it = (size_t)(B > 0 ? B : 1) * tile_slots(M);
-    w.fw.slab_span = reinterpret_cast<int*>(p);  p += align256(it * sizeof(int));
-    w.fw.slab_cnt = reinterpret_cast<int*>(p);
-    p += align256((size_t)kMaxSlabs * (B > 0 ? B : 1) * sizeof(int));
-    w.fw.slab_se = reinterpret_cast<int*>(p);    p += align256((kMaxSlabs + 1) * sizeof(int));
-    w.fw.slab_items = reinterpret_cast<int*>(p);
-    w.fw.slab_cap_B = B > 0 ? B : 1;
-  }
+  slab_carve(p, M, B, w.fw);   // per-slab item lists of the slab-split traversals
   return w;
 }
 
@@ -998,16 +990,9 @@ int ensure_mws(cs_handle* h, const cs_problem* P, int n, ProblemWs* W) {
     W[p].fw = fused_carve(c, M);                c += align256(fused_ws_bytes(M));
     W[p].rot = reinterpret_cast<float*>(c);     c += align256((size_t)P[p].B * 9 * sizeof(float));
     W[p].part = reinterpret_cast<double*>(c);   c += align256((size_t)kMultiParts * sizeof(double));
-    {  // per-slab item lists (problems whose traversals are split into z-slabs)
-      const int B = P[p].B > 0 ? P[p].B : 1;
-      const size_t it = (size_t)B * tile_slots(M);
-      W[p].fw.slab_span = reinterpret_cast<int*>(c);  c += align256(it * sizeof(int));
-      W[p].fw.slab_cnt = reinterpret_cast<int*>(c);
-      c += align256((size_t)kMaxSlabs * B * sizeof(int));
-      W[p].fw.slab_se = reinterpret_cast<int*>(c);    c += align256((kMaxSlabs + 1) * sizeof(int));
-      W[p].fw.slab_items = reinterpret_cast<int*>(c); c += align256(3 * it * sizeof(int));
-      W[p].fw.slab_cap_B = B;
-    }
+    // per-slab item lists (problems whose traversals are split into z-slabs)
+    slab_carve(c, M, P[p].B, W[p].fw);
+    c += align256(slab_lists_bytes(M, P[p].B));
   }
   return CS_OK;
 }

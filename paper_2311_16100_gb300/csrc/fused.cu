@@ -292,13 +292,23 @@ __device__ __forceinline__ float gather_cell_r(const Geo& G, const Cell& c,
 //   F_HUTCH : P4 += scale C^2 w_j sum_l w_l Z_jl  (Eq. hutch, bit-packed probes)
 //   F_HVP   : P4 += scale C^2 w_j (P z)           (Eq. hessian)
 //   F_CURV  : part += C^2 |P d|^2                 (curvature of the Armijo step)
-// ---- per-slab item lists (deterministic, in item order)
+// ---- per-slab item lists (deterministic)
 //
 // Item (b, t) = image b, table chunk t (a 16 x tile_h pixel tile).  Its cells
 // have z0 within [floor(zlo), floor(zhi)], zlo / zhi the extremes of
 // R[0][2] kx + R[1][2] ky + M/2 over the tile's corners with a 0.01 margin
 // (the cells' own z0 are computed in FP32 from the same products), so the
 // item is listed for every slab that range meets.
+//
+// Within a slab the items are grouped by the region of the slab their tile
+// centre falls in (kSlabQ x kSlabQ columns of the grid in x, y), region by
+// region, each region's items image by image.  The blocks of a launch then
+// work on the items of one or two regions at a time, and the accumulators
+// and volume they touch (a few MB) stay in L2 until the region is done,
+// instead of every image's band across the whole slab being touched at once.
+
+constexpr int kSlabQ = 4;                      // regions per axis (x, y)
+constexpr int kSlabKeys = kSlabQ * kSlabQ;     // regions per slab
 
 __device__ __forceinline__ int slab_of(int z0, int M, int S) {
   int sl = 0;
@@ -306,17 +316,20 @@ __device__ __forceinline__ int slab_of(int z0, int M, int S) {
   return sl;
 }
 
-// one block per image: spans of its items, and counts per slab
+// one block per image: span and region of each of its items, and counts per
+// (slab, region): cnt[(s kSlabKeys + q) B + b]
 __global__ void __launch_bounds__(256)
 k_slab_span(Geo G, const float* __restrict__ rot, const int* __restrict__ tile_org,
             const int* __restrict__ n_px, int bd, int tile_h, int S, int* __restrict__ span,
             int* __restrict__ cnt, int B) {
-  __shared__ int c[kMaxSlabs];
+  __shared__ int c[kMaxSlabs * kSlabKeys];
   const int b = blockIdx.x;
   const int nch = *n_px / bd;
-  if (threadIdx.x < kMaxSlabs) c[threadIdx.x] = 0;
+  for (int k = threadIdx.x; k < kMaxSlabs * kSlabKeys; k += blockDim.x) c[k] = 0;
   __syncthreads();
-  const float a = __ldg(rot + 9 * (size_t)b + 2), c2 = __ldg(rot + 9 * (size_t)b + 5);
+  const float* R = rot + 9 * (size_t)b;
+  const float ax = __ldg(R + 0), ay = __ldg(R + 1), a = __ldg(R + 2);
+  const float cx = __ldg(R + 3), cy = __ldg(R + 4), c2 = __ldg(R + 5);
   for (int t = threadIdx.x; t < nch; t += blockDim.x) {
     const int o = __ldg(tile_org + t);
     const float x0 = (float)((o & 0xffff) - G.half), y0 = (float)((o >> 16) - G.half);
@@ -324,27 +337,36 @@ k_slab_span(Geo G, const float* __restrict__ rot, const int* __restrict__ tile_o
     const float zlo = fminf(za, zb) + fminf(zc, zd) + (float)G.half - 0.01f;
     const float zhi = fmaxf(za, zb) + fmaxf(zc, zd) + (float)G.half + 0.01f;
     const int s0 = slab_of((int)floorf(zlo), G.M, S), s1 = slab_of((int)floorf(zhi), G.M, S);
-    span[(size_t)b * nch + t] = s0 | (s1 << 8);
-    for (int sl = s0; sl <= s1; ++sl) atomicAdd(&c[sl], 1);
+    // region of the tile centre's cell
+    const float xc = x0 + 7.5f, yc = y0 + 0.5f * (float)(tile_h - 1);
+    const int gx = (int)floorf(fmaf(cx, yc, ax * xc)) + G.half;
+    const int gy = (int)floorf(fmaf(cy, yc, ay * xc)) + G.half;
+    const int qx = min(max(gx * kSlabQ / G.M, 0), kSlabQ - 1);
+    const int qy = min(max(gy * kSlabQ / G.M, 0), kSlabQ - 1);
+    const int q = qy * kSlabQ + qx;
+    span[(size_t)b * nch + t] = s0 | (s1 << 8) | (q << 16);
+    for (int sl = s0; sl <= s1; ++sl) atomicAdd(&c[sl * kSlabKeys + q], 1);
   }
   __syncthreads();
-  if (threadIdx.x < S) cnt[(size_t)threadIdx.x * B + b] = c[threadIdx.x];
+  for (int k = threadIdx.x; k < S * kSlabKeys; k += blockDim.x)
+    cnt[(size_t)k * B + b] = c[k];
 }
 
-// one block: se[s] = first list entry of slab s, per-image offsets off[s][b]
-// (exclusive scan of cnt in slab-major, image order), se[S] = total
-__global__ void __launch_bounds__(1024)
-k_slab_scan(int S, int B, int* __restrict__ cnt, int* __restrict__ se) {
-  __shared__ int wsum[32];
+// one block per (slab, region) key: exclusive scan of its per-image counts
+// in place (image order), and the key's total
+__global__ void __launch_bounds__(256)
+k_slab_rows(int B, int* __restrict__ cnt, int* __restrict__ tot) {
+  __shared__ int wsum[8];
   __shared__ int carry;
+  const int k = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int* row = cnt + (size_t)k * B;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long n = (long)S * B;
-  for (long base = 0; base < n; base += blockDim.x) {
-    const long i = base + threadIdx.x;
-    const int v = i < n ? cnt[i] : 0;
-    int x = v;                                   // inclusive warp scan
+  for (int base = 0; base < B; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < B ? row[i] : 0;
+    int x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -352,56 +374,73 @@ k_slab_scan(int S, int B, int* __restrict__ cnt, int* __restrict__ se) {
     }
     if (lane == 31) wsum[wid] = x;
     __syncthreads();
-    if (wid == 0) {
-      int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      wsum[lane] = w;                            // inclusive over warps
-    }
+    int before = carry;
+    for (int q = 0; q < wid; ++q) before += wsum[q];
+    if (i < B) row[i] = before + x - v;
     __syncthreads();
-    const int excl = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - v;
-    if (i < n) {
-      if (i % B == 0) se[i / B] = excl;          // first entry of slab i / B
-      cnt[i] = excl;                             // becomes the offset
-    }
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    if (threadIdx.x == blockDim.x - 1) carry = before + x;
     __syncthreads();
   }
-  if (threadIdx.x == 0) se[S] = carry;
+  if (threadIdx.x == 0) tot[k] = carry;
 }
 
-// one block per image: its items in tile order into each slab's list
+// one block: base[k] = first list entry of key k (exclusive scan of the key
+// totals, slab-major), se[s] = first entry of slab s, se[S] = total
+__global__ void __launch_bounds__(256)
+k_slab_bases(int S, const int* __restrict__ tot, int* __restrict__ base, int* __restrict__ se) {
+  if (threadIdx.x != 0) return;
+  int run = 0;
+  for (int k = 0; k < S * kSlabKeys; ++k) {
+    if (k % kSlabKeys == 0) se[k / kSlabKeys] = run;
+    base[k] = run;
+    run += tot[k];
+  }
+  se[S] = run;
+}
+
+// one block per image: its items into the lists, at base[k] + (the key's
+// items of earlier images) + (its earlier items with that key in this pass:
+// ranks within a warp from matching keys, warps in order)
 __global__ void __launch_bounds__(256)
 k_slab_fill(const int* __restrict__ n_px, int bd, int S, const int* __restrict__ span,
-            const int* __restrict__ off, int B, int* __restrict__ items) {
-  __shared__ int run[kMaxSlabs];
-  __shared__ int wcnt[kMaxSlabs][8];
+            const int* __restrict__ off, const int* __restrict__ base, int B,
+            int* __restrict__ items) {
+  __shared__ int run[kMaxSlabs * kSlabKeys];
+  __shared__ int wcnt[8][kMaxSlabs * kSlabKeys];
   const int b = blockIdx.x;
   const int nch = *n_px / bd;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x < S) run[threadIdx.x] = off[(size_t)threadIdx.x * B + b];
+  const int nk = S * kSlabKeys;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    run[k] = base[k] + off[(size_t)k * B + b];
+    for (int w = 0; w < nw; ++w) wcnt[w][k] = 0;
+  }
   __syncthreads();
   for (int t0 = 0; t0 < nch; t0 += blockDim.x) {
     const int t = t0 + threadIdx.x;
     const int sp = t < nch ? span[(size_t)b * nch + t] : -1;
-    const int s0 = sp < 0 ? 1 : (sp & 0xff), s1 = sp < 0 ? 0 : (sp >> 8);
-    for (int sl = 0; sl < S; ++sl) {
-      const bool f = sl >= s0 && sl <= s1;
-      const unsigned m = __ballot_sync(0xffffffffu, f);
-      if (lane == 0) wcnt[sl][wid] = __popc(m);
+    const int s0 = sp < 0 ? 1 : (sp & 0xff), s1 = sp < 0 ? 0 : ((sp >> 8) & 0xff);
+    const int q = sp < 0 ? 0 : (sp >> 16);
+    for (int j = 0; j < 3; ++j) {                // a tile spans at most 3 slabs
+      const int sl = s0 + j;
+      const int key = sl <= s1 ? sl * kSlabKeys + q : -1;
+      const unsigned m = __match_any_sync(0xffffffffu, key);
+      const int rank = __popc(m & ((1u << lane) - 1u));
+      if (key >= 0 && rank == 0) wcnt[wid][key] = __popc(m);
       __syncthreads();
-      int before = 0;
-      for (int q = 0; q < wid; ++q) before += wcnt[sl][q];
-      if (f) items[run[sl] + before + __popc(m & ((1u << lane) - 1u))] = b * nch + t;
+      if (key >= 0) {
+        int before = 0;
+        for (int w = 0; w < wid; ++w) before += wcnt[w][key];
+        items[run[key] + before + rank] = b * nch + t;
+      }
       __syncthreads();
-      if (threadIdx.x == 0) {
+      for (int k = threadIdx.x; k < nk; k += blockDim.x) {
         int tot = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += wcnt[sl][q];
-        run[sl] += tot;
+        for (int w = 0; w < nw; ++w) {
+          tot += wcnt[w][k];
+          wcnt[w][k] = 0;
+        }
+        run[k] += tot;
       }
       __syncthreads();
     }
@@ -814,10 +853,25 @@ size_t table_entries(int M) { return (size_t)(M + 16) * (M + 16); }
 size_t tile_slots(int M) { return (size_t)((M + 15) / 16) * ((M + 7) / 8) + 64; }
 
 size_t slab_lists_bytes(int M, int B) {
-  const size_t items = (size_t)(B > 0 ? B : 1) * tile_slots(M);
+  const size_t b = (size_t)(B > 0 ? B : 1), items = b * tile_slots(M);
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  return al(items * sizeof(int)) + al((size_t)kMaxSlabs * (B > 0 ? B : 1) * sizeof(int)) +
+  const size_t keys = (size_t)kMaxSlabs * kSlabKeys;
+  return al(items * sizeof(int)) + al(keys * b * sizeof(int)) + 2 * al(keys * sizeof(int)) +
          al((kMaxSlabs + 1) * sizeof(int)) + al(3 * items * sizeof(int));
+}
+
+void slab_carve(void* region, int M, int B, FusedWs& w) {
+  const size_t b = (size_t)(B > 0 ? B : 1), items = b * tile_slots(M);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t keys = (size_t)kMaxSlabs * kSlabKeys;
+  char* p = static_cast<char*>(region);
+  w.slab_span = reinterpret_cast<int*>(p);  p += al(items * sizeof(int));
+  w.slab_cnt = reinterpret_cast<int*>(p);   p += al(keys * b * sizeof(int));
+  w.slab_tot = reinterpret_cast<int*>(p);   p += al(keys * sizeof(int));
+  w.slab_base = reinterpret_cast<int*>(p);  p += al(keys * sizeof(int));
+  w.slab_se = reinterpret_cast<int*>(p);    p += al((kMaxSlabs + 1) * sizeof(int));
+  w.slab_items = reinterpret_cast<int*>(p);
+  w.slab_cap_B = (int)b;
 }
 
 size_t fused_ws_bytes(int M) {
@@ -838,7 +892,7 @@ FusedWs fused_carve(void* base, int M) {
   w.table = reinterpret_cast<int*>(p);  p += table_entries(M) * sizeof(int);
   w.tile_org = reinterpret_cast<int*>(p); p += tile_slots(M) * sizeof(int);
   w.n_px = reinterpret_cast<int*>(p);
-  w.slab_span = w.slab_cnt = w.slab_se = w.slab_items = nullptr;
+  w.slab_span = w.slab_cnt = w.slab_tot = w.slab_base = w.slab_se = w.slab_items = nullptr;
   w.slab_cap_B = 0;
   return w;
 }
@@ -964,9 +1018,11 @@ cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid
     if (!w.slab_items || B > w.slab_cap_B) return cudaErrorInvalidValue;
     k_slab_span<<<B, 256, 0, s>>>(G, rot, w.tile_org, w.n_px, block, block / 16, S, w.slab_span,
                                   w.slab_cnt, B);
-    k_slab_scan<<<1, 1024, 0, s>>>(S, B, w.slab_cnt, w.slab_se);
-    k_slab_fill<<<B, 256, 0, s>>>(w.n_px, block, S, w.slab_span, w.slab_cnt, B, w.slab_items);
-    count_launches(3);
+    k_slab_rows<<<S * kSlabKeys, 256, 0, s>>>(B, w.slab_cnt, w.slab_tot);
+    k_slab_bases<<<1, 32, 0, s>>>(S, w.slab_tot, w.slab_base, w.slab_se);
+    k_slab_fill<<<B, 256, 0, s>>>(w.n_px, block, S, w.slab_span, w.slab_cnt, w.slab_base, B,
+                                  w.slab_items);
+    count_launches(4);
     A.slab_items = w.slab_items;
   }
   for (int sl = 0; sl < S; ++sl) {

@@ -63,8 +63,10 @@ size_t fused_ws_bytes(int M);
 // tile-ordered table sizes: entries and tile origins
 size_t table_entries(int M);
 size_t tile_slots(int M);
-// per-slab item lists for batches of up to B images (bytes)
+// per-slab item lists for batches of up to B images: bytes, and the carving
+// of a region of that size into w's slab fields
 size_t slab_lists_bytes(int M, int B);
+void slab_carve(void* region, int M, int B, FusedWs& w);
 constexpr int kMaxSlabs = 16;
 FusedWs fused_carve(void* base, int M);
 

@@ -13,11 +13,14 @@ struct FusedWs {
   int* table;     // disc pixel table (row order, or tile order: see fused.cu)
   int* tile_org;  // tile order: origin of each table chunk
   int* n_px;      // number of table entries
-  // per-slab item lists of a slab-split traversal (single-problem workspace
-  // only; NULL otherwise): span of each (image, tile) item, per-image counts,
-  // slab starts [S+1], the lists
+  // per-slab item lists of a slab-split traversal (NULL in workspaces
+  // without a slab region): span and region of each (image, tile) item,
+  // per-(slab, region, image) counts (then offsets), per-(slab, region)
+  // totals and list starts, slab starts [S+1], the lists
   int* slab_span;
   int* slab_cnt;
+  int* slab_tot;
+  int* slab_base;
   int* slab_se;
   int* slab_items;
   int slab_cap_B;
