@@ -1067,8 +1067,6 @@ FusedArgs problem_args(const cs_problem& q, const ProblemWs& w, const Geo& G) {
   A.k_dev = q.state.scalars + CS_S_K;
   A.cursor = q.state.scalars + CS_S_K;
   A.n_batches = q.n_batches;
-  A.z_lo = INT_MIN;
-  A.z_hi = INT_MAX;
   A.part_add = 0;
   return A;
 }

@@ -294,11 +294,13 @@ __device__ __forceinline__ float gather_cell_r(const Geo& G, const Cell& c,
 //   F_CURV  : part += C^2 |P d|^2                 (curvature of the Armijo step)
 // ---- per-slab item lists (deterministic)
 //
-// Item (b, t) = image b, table chunk t (a 16 x tile_h pixel tile).  Its cells
-// have z0 within [floor(zlo), floor(zhi)], zlo / zhi the extremes of
-// R[0][2] kx + R[1][2] ky + M/2 over the tile's corners with a 0.01 margin
-// (the cells' own z0 are computed in FP32 from the same products), so the
-// item is listed for every slab that range meets.
+// Item (b, t) = image b, table chunk t (a 16 x tile_h pixel tile).  Each
+// item belongs to exactly one slab launch, that of the z coordinate of its
+// tile's centre (R[0][2] kx + R[1][2] ky + M/2 at the middle of the tile's
+// range), and that launch processes all of its pixels, so every pixel is
+// processed once.  A tile spans at most ~23 voxels in z, so a launch also
+// touches accumulators up to about half a tile beyond its slab: every lane
+// stays busy, at the price of a slightly larger L2 footprint per launch.
 //
 // Within a slab the items are grouped by the region of the slab their tile
 // centre falls in (kSlabQ x kSlabQ columns of the grid in x, y), region by
@@ -316,7 +318,7 @@ __device__ __forceinline__ int slab_of(int z0, int M, int S) {
   return sl;
 }
 
-// one block per image: span and region of each of its items, and counts per
+// one block per image: slab and region of each of its items, and counts per
 // (slab, region): cnt[(s kSlabKeys + q) B + b]
 __global__ void __launch_bounds__(256)
 k_slab_span(Geo G, const float* __restrict__ rot, const int* __restrict__ tile_org,
@@ -333,19 +335,17 @@ k_slab_span(Geo G, const float* __restrict__ rot, const int* __restrict__ tile_o
   for (int t = threadIdx.x; t < nch; t += blockDim.x) {
     const int o = __ldg(tile_org + t);
     const float x0 = (float)((o & 0xffff) - G.half), y0 = (float)((o >> 16) - G.half);
-    const float za = a * x0, zb = a * (x0 + 15.f), zc = c2 * y0, zd = c2 * (y0 + tile_h - 1);
-    const float zlo = fminf(za, zb) + fminf(zc, zd) + (float)G.half - 0.01f;
-    const float zhi = fmaxf(za, zb) + fmaxf(zc, zd) + (float)G.half + 0.01f;
-    const int s0 = slab_of((int)floorf(zlo), G.M, S), s1 = slab_of((int)floorf(zhi), G.M, S);
-    // region of the tile centre's cell
+    // the tile's centre: its slab and its region in x, y
     const float xc = x0 + 7.5f, yc = y0 + 0.5f * (float)(tile_h - 1);
+    const int gz = (int)floorf(fmaf(c2, yc, a * xc)) + G.half;
     const int gx = (int)floorf(fmaf(cx, yc, ax * xc)) + G.half;
     const int gy = (int)floorf(fmaf(cy, yc, ay * xc)) + G.half;
+    const int sl = slab_of(gz, G.M, S);
     const int qx = min(max(gx * kSlabQ / G.M, 0), kSlabQ - 1);
     const int qy = min(max(gy * kSlabQ / G.M, 0), kSlabQ - 1);
     const int q = qy * kSlabQ + qx;
-    span[(size_t)b * nch + t] = s0 | (s1 << 8) | (q << 16);
-    for (int sl = s0; sl <= s1; ++sl) atomicAdd(&c[sl * kSlabKeys + q], 1);
+    span[(size_t)b * nch + t] = sl * kSlabKeys + q;
+    atomicAdd(&c[sl * kSlabKeys + q], 1);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < S * kSlabKeys; k += blockDim.x)
@@ -399,8 +399,8 @@ k_slab_bases(int S, const int* __restrict__ tot, int* __restrict__ base, int* __
 }
 
 // one block per image: its items into the lists, at base[k] + (the key's
-// items of earlier images) + (its earlier items with that key in this pass:
-// ranks within a warp from matching keys, warps in order)
+// items of earlier images) + (its earlier items with that key: ranks within
+// a warp from matching keys, warps in order, chunks in order)
 __global__ void __launch_bounds__(256)
 k_slab_fill(const int* __restrict__ n_px, int bd, int S, const int* __restrict__ span,
             const int* __restrict__ off, const int* __restrict__ base, int B,
@@ -418,32 +418,26 @@ k_slab_fill(const int* __restrict__ n_px, int bd, int S, const int* __restrict__
   __syncthreads();
   for (int t0 = 0; t0 < nch; t0 += blockDim.x) {
     const int t = t0 + threadIdx.x;
-    const int sp = t < nch ? span[(size_t)b * nch + t] : -1;
-    const int s0 = sp < 0 ? 1 : (sp & 0xff), s1 = sp < 0 ? 0 : ((sp >> 8) & 0xff);
-    const int q = sp < 0 ? 0 : (sp >> 16);
-    for (int j = 0; j < 3; ++j) {                // a tile spans at most 3 slabs
-      const int sl = s0 + j;
-      const int key = sl <= s1 ? sl * kSlabKeys + q : -1;
-      const unsigned m = __match_any_sync(0xffffffffu, key);
-      const int rank = __popc(m & ((1u << lane) - 1u));
-      if (key >= 0 && rank == 0) wcnt[wid][key] = __popc(m);
-      __syncthreads();
-      if (key >= 0) {
-        int before = 0;
-        for (int w = 0; w < wid; ++w) before += wcnt[w][key];
-        items[run[key] + before + rank] = b * nch + t;
-      }
-      __syncthreads();
-      for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-        int tot = 0;
-        for (int w = 0; w < nw; ++w) {
-          tot += wcnt[w][k];
-          wcnt[w][k] = 0;
-        }
-        run[k] += tot;
-      }
-      __syncthreads();
+    const int key = t < nch ? span[(size_t)b * nch + t] : -1;   // slab * kSlabKeys + region
+    const unsigned m = __match_any_sync(0xffffffffu, key);
+    const int rank = __popc(m & ((1u << lane) - 1u));
+    if (key >= 0 && rank == 0) wcnt[wid][key] = __popc(m);
+    __syncthreads();
+    if (key >= 0) {
+      int before = 0;
+      for (int w = 0; w < wid; ++w) before += wcnt[w][key];
+      items[run[key] + before + rank] = b * nch + t;
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+      int tot = 0;
+      for (int w = 0; w < nw; ++w) {
+        tot += wcnt[w][k];
+        wcnt[w][k] = 0;
+      }
+      run[k] += tot;
+    }
+    __syncthreads();
   }
 }
 
@@ -504,7 +498,6 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
     const int kx = ix - G.half, ky = iy - G.half;
     const Rot R = load_rot(A.rot, b);
     const Cell c = cell_of(G, R, kx, ky);
-    if ((FL & F_SLAB) && (c.z0 < A.z_lo || c.z0 >= A.z_hi)) continue;   // another slab's cell
     float C = 1.f;
     if (G.ctf_on) {
       float a_hi, a_lo;
@@ -857,7 +850,7 @@ size_t slab_lists_bytes(int M, int B) {
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t keys = (size_t)kMaxSlabs * kSlabKeys;
   return al(items * sizeof(int)) + al(keys * b * sizeof(int)) + 2 * al(keys * sizeof(int)) +
-         al((kMaxSlabs + 1) * sizeof(int)) + al(3 * items * sizeof(int));
+         al((kMaxSlabs + 1) * sizeof(int)) + al(items * sizeof(int));
 }
 
 void slab_carve(void* region, int M, int B, FusedWs& w) {
@@ -1007,9 +1000,9 @@ cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid
   A.slab_items = nullptr;
   A.slab_se = nullptr;
   if (block != 128 && block != 256) return cudaErrorInvalidValue;
-  // one launch per z-slab; the first takes cells below the grid, the last
-  // those above it, so every cell is processed exactly once.  Slabs need the
-  // tile-ordered table; a tile spans at most 3 slabs of >= 16 voxels.
+  // one launch per z-slab, each walking the items (tiles) whose centre lies
+  // in its slab, so every pixel is processed exactly once; slabs need the
+  // tile-ordered table
   int S = tiled ? (slabs > 0 ? slabs : slab_count(G.M, flags)) : 1;
   const int smax = G.M / 16 < kMaxSlabs ? G.M / 16 : kMaxSlabs;
   if (S > smax) S = smax;
@@ -1027,8 +1020,6 @@ cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid
   }
   for (int sl = 0; sl < S; ++sl) {
     if (A.slab_items) A.slab_se = w.slab_se + sl;
-    A.z_lo = sl == 0 ? INT_MIN : (int)((long)G.M * sl / S);
-    A.z_hi = sl == S - 1 ? INT_MAX : (int)((long)G.M * (sl + 1) / S);
     A.part_add = sl > 0;
     constexpr int X = F_SLAB;
     switch (flags | (A.slab_items ? X : 0)) {

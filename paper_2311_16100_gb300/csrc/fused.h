@@ -39,9 +39,8 @@ struct FusedArgs {
   // is used, k = iterations done (*cursor)
   const double* cursor;
   int n_batches;
-  // z-slab of this launch: only cells with z0 in [z_lo, z_hi) are processed;
-  // part_add: add the block partial to part[] instead of storing it
-  int z_lo, z_hi;
+  // part_add: add the block partial to part[] instead of storing it (slab
+  // launches after the first)
   int part_add;
   // tile-ordered table: chunk ch covers the 16 x tile_h pixels with origin
   // tile_org[ch] (packed like table entries); NULL for the row-ordered table
