@@ -405,10 +405,10 @@ int cs_set_launch_shape(cs_handle* h, int block_threads, int blocks_per_sm);
  * `slabs` launches, launch s processing the pixels whose cell lies in the
  * s-th slab of the grid along z, so that the accumulators and the gathered
  * volume a launch touches stay in L2 on large grids.  0 (default): chosen
- * from the grid's footprint (1 slab up to 160^3, 3 at 192^3, 6 for the
- * loss-gradient and Hutchinson passes and 2 for the curvature at 256^3).
- * At most M/16 slabs are used.  Results are the same sums in another
- * order.  0 <= slabs <= 16. */
+ * from the grid's footprint (1 slab up to 128^3; for the passes with
+ * reductions 2 at 160^3, 3 at 192^3 and 6 at 256^3; for the curvature 1 up
+ * to 192^3 and 2 at 256^3).  At most M/16 slabs are used.  Results are the
+ * same sums in another order.  0 <= slabs <= 16. */
 int cs_set_slabs(cs_handle* h, int slabs);
 /* How cs_precond_sgd_step_host moves a batch: CS_HOST_STAGED (default:
  * double-buffered staging copies) or CS_HOST_DIRECT (the traversal reads

@@ -216,8 +216,9 @@ int vec_grid(const cs_handle* h, int B, int M, int flags) {
   const long items = (long)B * (((long)M * M + h->block - 1) / h->block);
   int per_sm = h->blocks_per_sm;
   if (flags == F_CURV) {
-    // one wave of the kernel that will run (slab-split grids have their own)
-    const int f = tiled_table(h, M) ? (F_CURV | F_SLAB) : F_CURV;
+    // one wave of the kernel that will run (slab-split passes have their own)
+    const bool split = tiled_table(h, M) && pass_slabs(M, F_CURV, h->slabs) > 1;
+    const int f = split ? (F_CURV | F_SLAB) : F_CURV;
     const int res = fused_resident(f, h->block, false);
     if (res < per_sm) per_sm = res;
   }

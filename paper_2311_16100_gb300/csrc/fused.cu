@@ -493,7 +493,7 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
     const int p = chc * bd + threadIdx.x;
     if (p >= n_px) continue;
     const int e = __ldg(A.table + p);
-    if ((FL & F_SLAB) && e < 0) continue;    // only the tile-ordered table has holes
+    if ((FL & (F_SLAB | F_HOLES)) && e < 0) continue;   // holes of the tile-ordered table
     const int ix = e & 0xffff, iy = e >> 16;
     const int kx = ix - G.half, ky = iy - G.half;
     const Rot R = load_rot(A.rot, b);
@@ -1003,11 +1003,11 @@ cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid
   // one launch per z-slab, each walking the items (tiles) whose centre lies
   // in its slab, so every pixel is processed exactly once; slabs need the
   // tile-ordered table
-  int S = tiled ? (slabs > 0 ? slabs : slab_count(G.M, flags)) : 1;
-  const int smax = G.M / 16 < kMaxSlabs ? G.M / 16 : kMaxSlabs;
-  if (S > smax) S = smax;
-  if (S < 1) S = 1;
-  if (tiled && B > 0) {
+  const int S = tiled ? pass_slabs(G.M, flags, slabs) : 1;
+  // one slab on a tile-ordered table: the one-slab kernel variant that
+  // skips the table's holes
+  const int holes = (tiled && S == 1) ? F_HOLES : 0;
+  if (tiled && B > 0 && S > 1) {
     if (!w.slab_items || B > w.slab_cap_B) return cudaErrorInvalidValue;
     k_slab_span<<<B, 256, 0, s>>>(G, rot, w.tile_org, w.n_px, block, block / 16, S, w.slab_span,
                                   w.slab_cnt, B);
@@ -1021,8 +1021,8 @@ cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid
   for (int sl = 0; sl < S; ++sl) {
     if (A.slab_items) A.slab_se = w.slab_se + sl;
     A.part_add = sl > 0;
-    constexpr int X = F_SLAB;
-    switch (flags | (A.slab_items ? X : 0)) {
+    constexpr int X = F_SLAB, Y = F_HOLES;
+    switch (flags | (A.slab_items ? X : 0) | holes) {
       case F_ADJ: k_fused<F_ADJ><<<grid, block, 0, s>>>(A); break;
       case F_GRAD: k_fused<F_GRAD><<<grid, block, 0, s>>>(A); break;
       case F_GRAD | F_HUTCH: k_fused<F_GRAD | F_HUTCH><<<grid, block, 0, s>>>(A); break;
@@ -1035,6 +1035,12 @@ cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid
       case F_HUTCH | X: k_fused<F_HUTCH | X><<<grid, block, 0, s>>>(A); break;
       case F_HVP | X: k_fused<F_HVP | X><<<grid, block, 0, s>>>(A); break;
       case F_CURV | X: k_fused_curv_slab<<<grid, block, 0, s>>>(A); break;
+      case F_ADJ | Y: k_fused<F_ADJ | Y><<<grid, block, 0, s>>>(A); break;
+      case F_GRAD | Y: k_fused<F_GRAD | Y><<<grid, block, 0, s>>>(A); break;
+      case F_GRAD | F_HUTCH | Y: k_fused<F_GRAD | F_HUTCH | Y><<<grid, block, 0, s>>>(A); break;
+      case F_HUTCH | Y: k_fused<F_HUTCH | Y><<<grid, block, 0, s>>>(A); break;
+      case F_HVP | Y: k_fused<F_HVP | Y><<<grid, block, 0, s>>>(A); break;
+      case F_CURV | Y: k_fused<F_CURV | Y><<<grid, block, 0, s>>>(A); break;
       default: return cudaErrorInvalidValue;
     }
     count_launches(1);
@@ -1046,18 +1052,28 @@ cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid
 
 // The passes with reductions touch 48 bytes per voxel at random (pair layout
 // of v, E/O, the four patch buffers), the curvature pass 16 (pair layout).
-// One launch per ~134 MB (128 MB for the curvature) of that footprint.
-// Measured at 256^3, batch 1024, with per-slab item lists: the
-// loss-gradient pass takes 6.33 / 2.81 / 2.44 / 2.57 / 2.87 / 3.19 ms with
-// 1 / 4 / 6 / 8 / 12 / 16 slabs, the curvature 0.97 / 0.81 / 0.84 / 0.90 ms
-// with 1 / 2 / 4 / 6; at 128^3 one slab is best.
+// About one launch per ~134 MB (128 MB for the curvature) of that footprint.
+// Measured at 256^3, batch 1024 (tiles owned by the slab of their centre):
+// the loss-gradient pass takes 1.98 / 1.96 / 1.96 / 1.98 / 2.01 / 2.06 ms
+// with 4 / 5 / 6 / 8 / 12 / 16 slabs (6.33 ms in one launch), the curvature
+// 0.71 / 0.71 / 0.74 ms with 2 / 4 / 8; at 160^3 the loss-gradient pass
+// takes 0.87 / 0.77 / 0.78 ms with 1 / 2 / 3 slabs; at 128^3 one is best.
 int slab_count(int M, int flags) {
   const double vox = (double)M * M * M;
   const double ratio = flags == F_CURV ? 16.0 * vox / 128e6 : 48.0 * vox / 134e6;
-  long S = lround(ratio);
+  // passes with reductions: 2 slabs from 1.25 x the footprint on (measured
+  // at 160^3: loss-gradient pass 0.87 -> 0.77 ms)
+  long S = flags == F_CURV ? lround(ratio) : (ratio >= 1.25 ? lround(ratio + 0.25) : 1);
   if (S < 1) S = 1;
   if (S > kMaxSlabs) S = kMaxSlabs;
   return (int)S;
+}
+
+int pass_slabs(int M, int flags, int slabs) {
+  int S = slabs > 0 ? slabs : slab_count(M, flags);
+  const int smax = M / 16 < kMaxSlabs ? M / 16 : kMaxSlabs;
+  if (S > smax) S = smax;
+  return S < 1 ? 1 : S;
 }
 
 cudaError_t launch_fused_multi(int flags, const MultiFusedArgs& MA, int grid, int block,

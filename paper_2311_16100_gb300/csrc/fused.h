@@ -8,7 +8,9 @@ namespace cs {
 enum FusedFlags { F_ADJ = 1, F_GRAD = 2, F_HUTCH = 4, F_HVP = 8, F_CURV = 16,
                   // kernel variant with the z-slab / tile-ordered table logic
                   // (compiled out of the one-slab launches)
-                  F_SLAB = 32 };
+                  F_SLAB = 32,
+                  // one-slab launch over the tile-ordered table (skips its holes)
+                  F_HOLES = 64 };
 
 constexpr int kMaxProblems = 8;   // volumes per multi-volume launch
 
@@ -92,6 +94,9 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
 // Number of z-slabs a traversal of an M^3 grid is split into: one launch
 // per slab keeps the slab's accumulators and gathered volume in L2.
 int slab_count(int M, int flags);
+// Slabs a split traversal actually uses: the override `slabs` (> 0) or
+// slab_count, at most M/16 and kMaxSlabs.
+int pass_slabs(int M, int flags, int slabs);
 // launch_fused with the kernel arguments already filled in (the slab fields
 // are set here): used by the multi-volume step for its large volumes, whose
 // arguments select the batch on the device (cursor).
