@@ -351,7 +351,7 @@ def run_gpu(args, cfg, rank, world):
         ems_dir, _ = e2e_run("direct")
         h.set_host_mode("staged")
         # the host-to-device rate alone: the same batches copied back to back
-        # with nothing else running bounds the end-to-end rate from above
+        # with nothing else running (the rate the end-to-end steps depend on)
         dev_img = torch.empty_like(images[:B])
         cs_ = torch.cuda.Stream()
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -369,7 +369,7 @@ def run_gpu(args, cfg, rank, world):
                "d2h_bytes_per_step": 8,
                "host_wall_value": round(job_value(world, B, args.steps, wall), 1),
                "h2d_copy_only": {"GB_per_s": round(B * M * M * 8 / (cms / 1e3) / 1e9, 1),
-                                 "images_per_s_bound": round(world * B / (cms / 1e3), 1)},
+                                 "images_per_s_at_that_rate": round(world * B / (cms / 1e3), 1)},
                "direct_value": job_value(world, B, args.steps, ems_dir),
                "api": "cs_precond_sgd_step_host (double-buffered staging copies on a copy "
                       "stream; direct_value: the traversal reading the disc pixels from the "
