@@ -986,7 +986,37 @@ def cpu_baseline(cfg, n):
                       f"each of the {cfg['M']}^3 workload, {cores} single-threaded replicas "
                       f"started together, {wall:.1f} s wall",
             "single_core": single, "host_cores": cores,
-            "operators_single_core": oracle_operators(cfg)}
+            "operators_single_core": oracle_operators(cfg),
+            "config1_alg1_run": oracle_config1_run()}
+
+
+def oracle_config1_run():
+    """The whole 32^3 nearest-interpolation run of the oracle on one core:
+    1000 images, batch 100, 5 epochs of Algorithm 1 with 16-probe Hutchinson
+    estimates (50 steps); compare with the GPU's time for the same run
+    (time_to_rel_err.m32_nearest.hutchinson.total_ms)."""
+    import numpy as np
+    import oracle as O
+    from paper_2311_16100_gb300 import synth
+    cfg = CONFIGS["m32"]
+    M, B, n_img = cfg["M"], cfg["B"], cfg["n_img"]
+    S = oracle_sample(cfg, n_img, cfg["seed"] + 950)
+    v, D, Da, eta = S["v0"].astype(np.complex128), np.ones((M, M, M)), np.zeros((M, M, M)), 1.0
+    k = 0
+    t0 = time.perf_counter()
+    for ep in range(5):
+        perm = synth.permutation(n_img, cfg["seed"] + 31 + ep)
+        for b in range(n_img // B):
+            idx = perm[b * B:(b + 1) * B]
+            k += 1
+            out = O.alg1_step(v, D, Da, eta, k, S["x"][idx], S["R"][idx], S["df"][idx], M,
+                              S["r"], cfg["interp"], S["ctf"], S["lam"], n_img / B, S["alpha"],
+                              0.9, 0.5, "hutchinson", n_probes=cfg["K"], seed=cfg["seed"] + 11)
+            v, D, Da, eta = out["v"], out["D"], out["D_avg"], out["eta"]
+    t = time.perf_counter() - t0
+    return {"steps": k, "seconds": round(t, 2), "images_per_s": round(k * B / t, 2),
+            "cores": 1, "workload": "32^3, 1000 images, batch 100, 5 epochs, nearest, no CTF, "
+                                    "16 probes"}
 
 
 def oracle_operators(cfg):
