@@ -45,7 +45,14 @@ __device__ __forceinline__ float gelu_sig(float x) {
   const float c = 0.7978845608028654f;           // sqrt(2/pi)
   return fmaf(0.5f, tanh_hw(c * fmaf(0.044715f * x * x, x, x)), 0.5f);
 }
-__device__ __forceinline__ float gelu_f(float x) { return x * gelu_sig(x); }
+// GELU(x) = x s = 0.5 x + 0.5 x tanh(u), with u = x (c + c 0.044715 x^2):
+// six operations (the same u up to rounding)
+__device__ __forceinline__ float gelu_f(float x) {
+  const float c = 0.7978845608028654f, c3 = 0.7978845608028654f * 0.044715f;
+  const float t = tanh_hw(x * fmaf(c3, x * x, c));
+  const float hx = 0.5f * x;
+  return fmaf(hx, t, hx);
+}
 // d/dx GELU = s + x s (1 - s) 2c (1 + 3 * 0.044715 x^2), s = 0.5 (1 + tanh(u))
 __device__ __forceinline__ float gelu_grad_f(float x) {
   const float c = 0.7978845608028654f;
