@@ -54,11 +54,11 @@ __device__ __forceinline__ float gelu_f(float x) {
   return fmaf(hx, t, hx);
 }
 // d/dx GELU = s + x s (1 - s) 2c (1 + 3 * 0.044715 x^2), s = 0.5 (1 + tanh(u))
-__device__ __forceinline__ float gelu_grad_f(float x) {
+__device__ __forceinline__ float gelu_grad_s(float x, float s) {
   const float c = 0.7978845608028654f;
-  const float s = gelu_sig(x);
   return fmaf(x * s * (1.f - s), 2.f * c * fmaf(3.f * 0.044715f, x * x, 1.f), s);
 }
+__device__ __forceinline__ float gelu_grad_f(float x) { return gelu_grad_s(x, gelu_sig(x)); }
 __device__ __forceinline__ float bf16r(float x) {
   return __bfloat162float(__float2bfloat16_rn(x));
 }
@@ -427,8 +427,9 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const int o = c + u;
-        const float h2 = gelu_f(a2[o]);
-        const float da = dy * S.L2[o].y * gelu_grad_f(a2[o]);
+        const float sg = gelu_sig(a2[o]);        // one tanh for GELU and GELU'
+        const float h2 = a2[o] * sg;
+        const float da = dy * S.L2[o].y * gelu_grad_s(a2[o], sg);
         dab[u & 7] = da;
         *reinterpret_cast<unsigned short*>(XTb + core_off(o, t, kRows)) = bf16bits(da);
         if ((u & 7) == 7) st_bf16x8(DAb, core_off(t, o - 7, kHid), dab);
