@@ -150,6 +150,12 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the kernel before it in the stream is still
+// running; it waits here, before touching anything, until that kernel has
+// completed and its writes are visible (a no-op for an ordinary launch).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Block-wide sum in a fixed order (deterministic); every thread must call.
 // Result valid in thread 0.  Needs blockDim.x a multiple of 32, <= 1024.
 __device__ __forceinline__ double block_sum(double v) {

@@ -602,6 +602,7 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
 
 template <int FL>
 __device__ __forceinline__ void fused_body(const FusedArgs& A) {
+  grid_dep_wait();
   const float acc = fused_traverse<FL>(A, blockIdx.x, gridDim.x);
   if (FL & (F_GRAD | F_CURV)) {
     const double t = block_sum_f(acc);
@@ -659,6 +660,7 @@ k_pairs(int M, const float2* __restrict__ v, float4* __restrict__ vp) {
 __global__ void __launch_bounds__(256)
 k_step_prep(int M, const float2* __restrict__ v, float2* __restrict__ E, float2* __restrict__ O,
             float* __restrict__ P, float4* __restrict__ vp, int zero_p) {
+  grid_dep_wait();
   const int n = M * M * M, n4 = n / 4;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   float4* E4 = reinterpret_cast<float4*>(E);
@@ -748,6 +750,7 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
             float* __restrict__ P, float* __restrict__ D, float* __restrict__ Davg,
             float4* __restrict__ dp, double* __restrict__ partG, double* __restrict__ partV,
             int nb) {
+  grid_dep_wait();
   const int n = M * M * M, Mh = M / 2;
   const size_t nbuf = (size_t)n;
   const double k = sc[CS_S_K] + 1.0;
@@ -816,6 +819,7 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
 __global__ void __launch_bounds__(256)
 k_update_pairs(int n, float2* __restrict__ v, const float4* __restrict__ dp,
                const double* __restrict__ sc) {
+  grid_dep_wait();
   const float eta = (float)sc[CS_S_ETA];
   const int n4 = n / 4;
   for (int q = blockIdx.x * 256 + threadIdx.x; q < n4; q += gridDim.x * 256) {
@@ -1022,28 +1026,30 @@ cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid
     if (A.slab_items) A.slab_se = w.slab_se + sl;
     A.part_add = sl > 0;
     constexpr int X = F_SLAB, Y = F_HOLES;
+    cudaError_t e0 = cudaSuccess;
     switch (flags | (A.slab_items ? X : 0) | holes) {
-      case F_ADJ: k_fused<F_ADJ><<<grid, block, 0, s>>>(A); break;
-      case F_GRAD: k_fused<F_GRAD><<<grid, block, 0, s>>>(A); break;
-      case F_GRAD | F_HUTCH: k_fused<F_GRAD | F_HUTCH><<<grid, block, 0, s>>>(A); break;
-      case F_HUTCH: k_fused<F_HUTCH><<<grid, block, 0, s>>>(A); break;
-      case F_HVP: k_fused<F_HVP><<<grid, block, 0, s>>>(A); break;
-      case F_CURV: k_fused<F_CURV><<<grid, block, 0, s>>>(A); break;
-      case F_ADJ | X: k_fused<F_ADJ | X><<<grid, block, 0, s>>>(A); break;
-      case F_GRAD | X: k_fused<F_GRAD | X><<<grid, block, 0, s>>>(A); break;
-      case F_GRAD | F_HUTCH | X: k_fused<F_GRAD | F_HUTCH | X><<<grid, block, 0, s>>>(A); break;
-      case F_HUTCH | X: k_fused<F_HUTCH | X><<<grid, block, 0, s>>>(A); break;
-      case F_HVP | X: k_fused<F_HVP | X><<<grid, block, 0, s>>>(A); break;
-      case F_CURV | X: k_fused_curv_slab<<<grid, block, 0, s>>>(A); break;
-      case F_ADJ | Y: k_fused<F_ADJ | Y><<<grid, block, 0, s>>>(A); break;
-      case F_GRAD | Y: k_fused<F_GRAD | Y><<<grid, block, 0, s>>>(A); break;
-      case F_GRAD | F_HUTCH | Y: k_fused<F_GRAD | F_HUTCH | Y><<<grid, block, 0, s>>>(A); break;
-      case F_HUTCH | Y: k_fused<F_HUTCH | Y><<<grid, block, 0, s>>>(A); break;
-      case F_HVP | Y: k_fused<F_HVP | Y><<<grid, block, 0, s>>>(A); break;
-      case F_CURV | Y: k_fused<F_CURV | Y><<<grid, block, 0, s>>>(A); break;
+      case F_ADJ: e0 = launch_pdl(k_fused<F_ADJ>, grid, block, s, A); break;
+      case F_GRAD: e0 = launch_pdl(k_fused<F_GRAD>, grid, block, s, A); break;
+      case F_GRAD | F_HUTCH: e0 = launch_pdl(k_fused<F_GRAD | F_HUTCH>, grid, block, s, A); break;
+      case F_HUTCH: e0 = launch_pdl(k_fused<F_HUTCH>, grid, block, s, A); break;
+      case F_HVP: e0 = launch_pdl(k_fused<F_HVP>, grid, block, s, A); break;
+      case F_CURV: e0 = launch_pdl(k_fused<F_CURV>, grid, block, s, A); break;
+      case F_ADJ | X: e0 = launch_pdl(k_fused<F_ADJ | X>, grid, block, s, A); break;
+      case F_GRAD | X: e0 = launch_pdl(k_fused<F_GRAD | X>, grid, block, s, A); break;
+      case F_GRAD | F_HUTCH | X: e0 = launch_pdl(k_fused<F_GRAD | F_HUTCH | X>, grid, block, s, A); break;
+      case F_HUTCH | X: e0 = launch_pdl(k_fused<F_HUTCH | X>, grid, block, s, A); break;
+      case F_HVP | X: e0 = launch_pdl(k_fused<F_HVP | X>, grid, block, s, A); break;
+      case F_CURV | X: e0 = launch_pdl(k_fused_curv_slab, grid, block, s, A); break;
+      case F_ADJ | Y: e0 = launch_pdl(k_fused<F_ADJ | Y>, grid, block, s, A); break;
+      case F_GRAD | Y: e0 = launch_pdl(k_fused<F_GRAD | Y>, grid, block, s, A); break;
+      case F_GRAD | F_HUTCH | Y: e0 = launch_pdl(k_fused<F_GRAD | F_HUTCH | Y>, grid, block, s, A); break;
+      case F_HUTCH | Y: e0 = launch_pdl(k_fused<F_HUTCH | Y>, grid, block, s, A); break;
+      case F_HVP | Y: e0 = launch_pdl(k_fused<F_HVP | Y>, grid, block, s, A); break;
+      case F_CURV | Y: e0 = launch_pdl(k_fused<F_CURV | Y>, grid, block, s, A); break;
       default: return cudaErrorInvalidValue;
     }
     count_launches(1);
+    if (e0 != cudaSuccess) return e0;
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1095,26 +1101,27 @@ cudaError_t launch_step_post(int M, int mode, const float2* v, float lambda, flo
                              cudaStream_t s) {
   const int g = elem_grid(M * M * M, num_sms);
   *nb = g;
-  k_step_post<<<g, 256, 0, s>>>(M, mode, v, lambda, beta, scalars, w.E, w.O, w.P, D, Davg,
-                                w.pairs, partG, partV, g);
+  const cudaError_t e = launch_pdl(k_step_post, g, 256, s, M, mode, v, lambda, beta, scalars,
+                                   w.E, w.O, w.P, D, Davg, w.pairs, partG, partV, g);
   count_launches(1);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_update_pairs(int M, float2* v, const FusedWs& w, const double* scalars,
                                 int num_sms, cudaStream_t s) {
   const int n = M * M * M;
-  k_update_pairs<<<elem_grid(n / 4, num_sms), 256, 0, s>>>(n, v, w.pairs, scalars);
+  const cudaError_t e =
+      launch_pdl(k_update_pairs, elem_grid(n / 4, num_sms), 256, s, n, v, w.pairs, scalars);
   count_launches(1);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_step_prep(int M, const float2* v, const FusedWs& w, bool zero_p, int num_sms,
                              cudaStream_t s) {
-  k_step_prep<<<elem_grid(M * M * M / 4, num_sms), 256, 0, s>>>(M, v, w.E, w.O, w.P, w.pairs,
-                                                               zero_p ? 1 : 0);
+  const cudaError_t e = launch_pdl(k_step_prep, elem_grid(M * M * M / 4, num_sms), 256, s, M, v,
+                                   w.E, w.O, w.P, w.pairs, zero_p ? 1 : 0);
   count_launches(1);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_pairs(int M, const float2* v, float4* vp, int num_sms, cudaStream_t s) {

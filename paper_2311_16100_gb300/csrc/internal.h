@@ -3,6 +3,7 @@
 #pragma once
 
 #include <atomic>
+#include <utility>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -54,6 +55,24 @@ namespace cs {
 // Kernel launches made by the library (reported by cs_kernel_launches).
 extern std::atomic<uint64_t> g_launches;
 inline void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// Launch with programmatic stream serialisation: the kernel's blocks may be
+// scheduled while the previous kernel in the stream finishes; the kernel
+// must call grid_dep_wait() before its first access to memory.
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 // Workspace layout for a grid of side M and batches of up to B images:
 // offsets are 256-byte aligned.

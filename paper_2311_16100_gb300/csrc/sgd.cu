@@ -121,6 +121,7 @@ k_eta(double* sc, const double* pl, int nl, const double* pv, int nv, const doub
       const double* pD, int nd, const double* pQ, int nq, const int* n_dev, float lambda,
       float scale, float c, int max_halvings) {
   __shared__ double sum5[5];
+  grid_dep_wait();
   if (n_dev) {
     nl = *n_dev;
     nq = *n_dev;
@@ -270,10 +271,11 @@ cudaError_t launch_eta(double* scalars, const double* part_loss, int n_loss,
                        const double* part_dd, int n_dir, const double* part_Q, int n_Q,
                        const int* n_dev, float lambda, float scale, float c,
                        int max_halvings, cudaStream_t s) {
-  k_eta<<<1, 160, 0, s>>>(scalars, part_loss, n_loss, part_vv, n_vv, part_G, part_dd,
-                           n_dir, part_Q, n_Q, n_dev, lambda, scale, c, max_halvings);
+  const cudaError_t e = launch_pdl(k_eta, 1, 160, s, scalars, part_loss, n_loss, part_vv, n_vv,
+                                   part_G, part_dd, n_dir, part_Q, n_Q, n_dev, lambda, scale, c,
+                                   max_halvings);
   count_launches(1);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_update(int n, float2* v, const float2* d, const double* scalars,
