@@ -630,6 +630,7 @@ k_fused_curv_slab(FusedArgs A) {
 template <int FL>
 __global__ void __launch_bounds__(256)
 k_fused_multi(MultiFusedArgs MA) {
+  grid_dep_wait();
   int p = 0;
   while (p + 1 < MA.n && (int)blockIdx.x >= MA.start[p + 1]) ++p;
   const int lb = blockIdx.x - MA.start[p];
@@ -1085,14 +1086,15 @@ int pass_slabs(int M, int flags, int slabs) {
 cudaError_t launch_fused_multi(int flags, const MultiFusedArgs& MA, int grid, int block,
                                cudaStream_t s) {
   if (block != 128 && block != 256) return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
   switch (flags) {
-    case F_GRAD: k_fused_multi<F_GRAD><<<grid, block, 0, s>>>(MA); break;
-    case F_GRAD | F_HUTCH: k_fused_multi<F_GRAD | F_HUTCH><<<grid, block, 0, s>>>(MA); break;
-    case F_CURV: k_fused_multi<F_CURV><<<grid, block, 0, s>>>(MA); break;
+    case F_GRAD: e = launch_pdl(k_fused_multi<F_GRAD>, grid, block, s, MA); break;
+    case F_GRAD | F_HUTCH: e = launch_pdl(k_fused_multi<F_GRAD | F_HUTCH>, grid, block, s, MA); break;
+    case F_CURV: e = launch_pdl(k_fused_multi<F_CURV>, grid, block, s, MA); break;
     default: return cudaErrorInvalidValue;
   }
   count_launches(1);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_step_post(int M, int mode, const float2* v, float lambda, float beta,
