@@ -402,8 +402,9 @@ int cs_graph_destroy(cs_graph* graph);
  * Default 256 x 8. */
 int cs_set_launch_shape(cs_handle* h, int block_threads, int blocks_per_sm);
 /* z-slabs of the trilinear vector traversals: each pass is split into
- * `slabs` launches, launch s processing the pixels whose cell lies in the
- * s-th slab of the grid along z, so that the accumulators and the gathered
+ * `slabs` launches, launch s processing the 16 x 16 pixel tiles (of every
+ * image) whose centre's cell lies in the s-th slab of the grid along z,
+ * grouped by region of the slab, so that the accumulators and the gathered
  * volume a launch touches stay in L2 on large grids.  0 (default): chosen
  * from the grid's footprint (1 slab up to 128^3; for the passes with
  * reductions 2 at 160^3, 3 at 192^3 and 6 at 256^3; for the curvature 1 up
