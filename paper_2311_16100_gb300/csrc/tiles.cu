@@ -35,23 +35,23 @@ constexpr int kWarps = kTileThreads / 32;
 template <int OP> struct OpTraits;
 template <> struct OpTraits<OP_ADJOINT> {
   using Halo = float; using Acc = float2;
-  static constexpr bool kGather = false, kScatter = true, kImage = true, kSum = false;
+  static constexpr bool kGather = false, kScatter = true, kSum = false;
 };
 template <> struct OpTraits<OP_LOSS_GRAD> {
   using Halo = float2; using Acc = float2;
-  static constexpr bool kGather = true, kScatter = true, kImage = true, kSum = true;
+  static constexpr bool kGather = true, kScatter = true, kSum = true;
 };
 template <> struct OpTraits<OP_HVP> {
   using Halo = float; using Acc = float;
-  static constexpr bool kGather = true, kScatter = true, kImage = false, kSum = false;
+  static constexpr bool kGather = true, kScatter = true, kSum = false;
 };
 template <> struct OpTraits<OP_HUTCH> {
   using Halo = uint32_t; using Acc = float;
-  static constexpr bool kGather = true, kScatter = true, kImage = false, kSum = false;
+  static constexpr bool kGather = true, kScatter = true, kSum = false;
 };
 template <> struct OpTraits<OP_CURVATURE> {
   using Halo = float2; using Acc = float;
-  static constexpr bool kGather = true, kScatter = false, kImage = false, kSum = true;
+  static constexpr bool kGather = true, kScatter = false, kSum = true;
 };
 
 template <int OP>
