@@ -4,7 +4,6 @@ usable), and a workspace allocation failure (injected on the host) is
 reported as CS_ERR_ALLOC and leaves the handle usable."""
 import os
 
-import numpy as np
 import pytest
 
 import oracle as O

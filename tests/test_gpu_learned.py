@@ -9,8 +9,7 @@ relative volume error of SGD preconditioned by each after one epoch.
 import numpy as np
 import pytest
 
-import oracle as O
-from cryo_cases import CTF_DICT, rel_l2
+from cryo_cases import rel_l2
 from paper_2311_16100_gb300 import synth
 
 torch = pytest.importorskip("torch")

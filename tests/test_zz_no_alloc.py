@@ -11,7 +11,6 @@ is taken from the caller's allocator.  It is collected last on purpose.
 """
 import ctypes
 
-import numpy as np
 import pytest
 
 from cryo_cases import Case, rel_l2
