@@ -29,3 +29,23 @@ def test_reference_arm_prints_contract_line():
     for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"):
         assert k in d["e2e"], k
     assert d["e2e"]["value"] == d["value"]
+
+
+def test_disc_pixel_counts_and_job_value():
+    """Disc pixel counts used for the algorithmic bytes and reductions (the
+    disc kx^2 + ky^2 <= (M/2 - 1)^2: lattice points of a disc of radius r,
+    counted row by row as sum over |ky| <= r of 2 floor(sqrt(r^2 - ky^2)) + 1),
+    and the whole-job value (all ranks' images over the slowest rank's time)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    import oracle as O
+    import math
+    for M in (32, 64, 128, 256):
+        r = M // 2 - 1
+        n = sum(2 * math.isqrt(r * r - ky * ky) + 1 for ky in range(-r, r + 1))
+        assert bench.n_disc_pixels(M, r) == n
+        assert int(np.count_nonzero(O.disc_mask(M, r))) == n
+    assert [bench.n_disc_pixels(M, M // 2 - 1) for M in (32, 64, 128, 256)] == [709, 3001, 12453,
+                                                                               50617]
+    assert bench.job_value(4, 1024, 50, 1000.0) == 4 * 1024 * 50
