@@ -139,3 +139,40 @@ def test_largest_grid_slices_and_gradient():
     assert abs(float(lv) - float(lp)) <= 1e-6 * abs(float(lp))
     hv.close()
     hp.close()
+
+
+@pytest.mark.parametrize("Mg", [160, 192])
+def test_slab_policy_steps_match_one_slab(Mg):
+    """At 160^3 the reduction pass runs in 2 z-slabs and the curvature as one
+    pass over the tile-ordered table (skipping its holes); at 192^3 in 3
+    slabs.  Three Algorithm-1 steps from the same state must match those of a
+    handle with one slab (row-ordered table) up to summation order."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_16100_gb300 import ops
+    Bg, nb = 96, 3
+    d = torch.device("cuda")
+    geom = ops.Geometry(Mg, Mg // 2 - 1, "trilinear", ops.CTF())
+    h_def, h_one = ops.Handle(0), ops.Handle(0)
+    h_one.set_slabs(1)
+    vol = torch.from_numpy(synth.blob_volume(Mg, 400, seed=Mg)).to(d)
+    q = torch.from_numpy(synth.shoemake_quaternions(Bg * nb, Mg + 1).astype(np.float32)).to(d)
+    rot = h_def.quat_to_rot(q)
+    df = torch.from_numpy(synth.defocus_angstrom(Bg * nb, Mg + 2).astype(np.float32)).to(d)
+    images = h_def.slice_project(geom, vol, rot, df)
+    alpha = float(h_def.threshold_alpha(geom, df, Bg * nb, 0.05))
+    st = [ops.SGDState((0.5 * vol).contiguous(), mode="hutchinson", alpha=alpha, eta0=1.0,
+                       n_probes=16, seed=3) for _ in range(2)]
+    for k in range(nb):
+        sl = slice(k * Bg, (k + 1) * Bg)
+        for h, s in ((h_def, st[0]), (h_one, st[1])):
+            h.precond_sgd_step(geom, s, images[sl].contiguous(), rot[sl].contiguous(),
+                               df[sl].contiguous(), 0.05, float(nb))
+    torch.cuda.synchronize()
+    a, b = st[0].scalars.cpu().numpy(), st[1].scalars.cpu().numpy()
+    assert a[0] == b[0]                                   # same step sizes
+    assert abs(a[3] - b[3]) <= 1e-6 * abs(b[3])           # batch loss
+    assert rel_l2(st[0].v.cpu().numpy(), st[1].v.cpu().numpy()) <= 1e-5
+    assert rel_l2(st[0].D.cpu().numpy(), st[1].D.cpu().numpy()) <= 1e-5
+    h_def.close()
+    h_one.close()
