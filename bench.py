@@ -456,10 +456,17 @@ def run_gpu(args, cfg, rank, world):
         torch.cuda.synchronize()
         per_pass = sorted(a.elapsed_time(b_) for a, b_ in ev)
         med = per_pass[len(per_pass) // 2]
+        ips = nb * B / (med / 1e3)
+        npx = n_disc_pixels(M, M // 2 - 1)
+        # byte rates the images/s stand for: per image, its disc pixels and
+        # pose from HBM; in L2 the trilinear gathers (8 corners x 8 bytes)
+        # and the adjoint's additions (8 corners x 8 bytes) per pixel
         lg = {"metric": "cs_loss_grad images/s (loss + gradient only)",
-              "value": round(nb * B / (med / 1e3), 1), "unit": "images/s",
+              "value": round(ips, 1), "unit": "images/s",
               "ms_per_pass_median": round(med, 4), "passes": 20,
-              "pass": f"{nb} batches of {B} (every image once), poses converted per batch"}
+              "pass": f"{nb} batches of {B} (every image once), poses converted per batch",
+              "hbm_GB_per_s_equivalent": round(ips * (8 * npx + 20) / 1e9, 1),
+              "l2_GB_per_s_equivalent": round(ips * (64 + 64) * npx / 1e9, 1)}
     return dict(ms=ms, launches=launches, phases={k: round(v, 4) for k, v in per.items()},
                 roofline=roof, red_roofline=red_roof, e2e=e2e, clocks=clk, scalars=sc, n_img=W["n_img"],
                 loss_grad_only=lg, graph=graph)
