@@ -32,13 +32,13 @@ sys.path.insert(0, ROOT)
 METRIC = "grad images/s at N=128"
 CONFIGS = {
     # name: grid side, images in HBM, batch, interpolation, probes, defocus (um), SNR, blobs
-    "m128": dict(M=128, n_img=49152, B=1024, interp="trilinear", K=32, df=(1.0, 3.0),
+    "m128": dict(M=128, n_img=50000, B=1024, interp="trilinear", K=32, df=(1.0, 3.0),
                  snr=0.05, blobs=1000, seed=3000),
-    "m64": dict(M=64, n_img=20480, B=256, interp="trilinear", K=32, df=(1.0, 3.0),
+    "m64": dict(M=64, n_img=20000, B=256, interp="trilinear", K=32, df=(1.0, 3.0),
                 snr=0.05, blobs=200, seed=2000),
     "m32": dict(M=32, n_img=1000, B=100, interp="nearest", K=16, df=None, snr=0.1,
                 blobs=20, seed=1000),
-    "m256": dict(M=256, n_img=102400, B=1024, interp="trilinear", K=32, df=(1.0, 3.0),
+    "m256": dict(M=256, n_img=100000, B=1024, interp="trilinear", K=32, df=(1.0, 3.0),
                  snr=0.05, blobs=5000, seed=5000),
 }
 
@@ -212,10 +212,18 @@ def job_value(world, batch, steps, ms):
 
 
 # ------------------------------------------------------------------ GPU arm
+def batches(n_img, B):
+    """(start, size) of each mini-batch over a dataset of n_img images taken in
+    order: full batches of B and, when B does not divide n_img, a short last
+    one (its step uses the scale n_img / size, the batch reading of Eq. optim
+    cp)."""
+    return [(s, min(B, n_img - s)) for s in range(0, n_img, B)]
+
+
 def build_workload(cfg, rank, h, torch, ops, synth):
     M, B = cfg["M"], cfg["B"]
-    nb = cfg["n_img"] // B
-    n_img = nb * B
+    n_img = cfg["n_img"]
+    bl = batches(n_img, B)
     dev = torch.device("cuda", torch.cuda.current_device())
     ctf = ops.CTF() if cfg["df"] else None
     geom = ops.Geometry(M, M // 2 - 1, cfg["interp"], ctf)
@@ -233,17 +241,18 @@ def build_workload(cfg, rank, h, torch, ops, synth):
     gen.manual_seed(seed + 3)
     disc = torch.from_numpy(synth.ball_mask(M, M // 2 - 1)[M // 2]).to(dev)
     sig2 = None
-    for b in range(nb):
-        sl = slice(b * B, (b + 1) * B)
-        h.quat_to_rot(quat[sl], rot)
-        clean = h.slice_project(geom, v_true, rot, df[sl] if ctf else None, out=images[sl])
+    for start, size in bl:
+        sl = slice(start, start + size)
+        h.quat_to_rot(quat[sl], rot[:size])
+        clean = h.slice_project(geom, v_true, rot[:size], df[sl] if ctf else None,
+                                out=images[sl])
         if sig2 is None:
             sig2 = float((clean.abs() ** 2)[:, disc].mean()) / cfg["snr"]
-        noise = torch.randn((B, M, M), dtype=torch.complex64, device=dev, generator=gen)
+        noise = torch.randn((size, M, M), dtype=torch.complex64, device=dev, generator=gen)
         images[sl] += noise * (sig2 ** 0.5) * disc.to(torch.complex64)
     torch.cuda.synchronize()
-    return dict(geom=geom, v_true=v_true, quat=quat, df=df, images=images, rot=rot, nb=nb,
-                n_img=n_img, sigma2=sig2, ctf=ctf)
+    return dict(geom=geom, v_true=v_true, quat=quat, df=df, images=images, rot=rot, nb=len(bl),
+                batches=bl, n_img=n_img, sigma2=sig2, ctf=ctf)
 
 
 def run_gpu(args, cfg, rank, world):
@@ -255,7 +264,7 @@ def run_gpu(args, cfg, rank, world):
     h = ops.Handle(torch.cuda.current_device())
     h.set_algo(args.algo)
     W = build_workload(cfg, rank, h, torch, ops, synth)
-    M, B, nb = cfg["M"], cfg["B"], W["nb"]
+    M, B, nb, bl = cfg["M"], cfg["B"], W["nb"], W["batches"]
     geom, images, quat, df, rot = W["geom"], W["images"], W["quat"], W["df"], W["rot"]
     lam = W["sigma2"]                       # lambda = sigma^2 / tau^2 with tau^2 = 1
     scale = W["n_img"] / B
@@ -267,9 +276,11 @@ def run_gpu(args, cfg, rank, world):
     dfs = (lambda sl: df[sl]) if W["ctf"] else (lambda sl: None)
 
     def step(s):
-        sl = slice((s % nb) * B, (s % nb + 1) * B)
-        h.quat_to_rot(quat[sl], rot)
-        h.precond_sgd_step(geom, st, images[sl], rot, dfs(sl), lam, scale)
+        start, size = bl[s % nb]
+        sl = slice(start, start + size)
+        h.quat_to_rot(quat[sl], rot[:size])
+        h.precond_sgd_step(geom, st, images[sl], rot[:size], dfs(sl), lam, W["n_img"] / size)
+        return size
 
     stream = torch.cuda.current_stream()
     for s in range(args.warmup):
@@ -286,8 +297,9 @@ def run_gpu(args, cfg, rank, world):
         dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    timed_images = 0
     for s in range(args.warmup, args.warmup + args.steps):
-        step(s)
+        timed_images += step(s)
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -298,8 +310,9 @@ def run_gpu(args, cfg, rank, world):
     # phase breakdown from a second run of as many steps with the library's
     # event profiler on (kept out of the timed loop above)
     h.profile_enable(True, args.steps)
+    prof_images = 0
     for s in range(args.warmup + args.steps, args.warmup + 2 * args.steps):
-        step(s)
+        prof_images += step(s)
     torch.cuda.synchronize()
     phases = h.profile_read()
     h.profile_enable(False)
@@ -377,18 +390,19 @@ def run_gpu(args, cfg, rank, world):
     # --- roofline of the dominant phase
     n_px = n_disc_pixels(M, M // 2 - 1)
     hutch = cfg["K"] > 0
+    Bp = prof_images / args.steps           # images per launch, averaged over the profiled steps
     alg_bytes = {   # algorithmic DRAM bytes of one launch of each phase
         # fused traversal: images + poses read once, volume read, gradient
         # (and Hutchinson diagonal) written once
-        "loss_grad": B * (8 * n_px + 36 + 4) + M ** 3 * (8 + 8 + (4 if hutch else 0)),
+        "loss_grad": round(Bp * (8 * n_px + 36 + 4)) + M ** 3 * (8 + 8 + (4 if hutch else 0)),
         "precond": M ** 3 * (8 + 16),
         "direction": M ** 3 * (8 + 8 + 4 * 5 + 16),
-        "curvature": B * (36 + 4) + 16 * M ** 3,
+        "curvature": round(Bp * (36 + 4)) + 16 * M ** 3,
         "update": M ** 3 * (16 + 8 + 8),
     }
     # 16-byte reductions per pixel of the trilinear fused pass: 4 for the
     # complex gradient, 2 for the Hutchinson diagonal
-    reds = {"loss_grad": B * n_px * (4 + (2 if hutch else 0))}
+    reds = {"loss_grad": round(Bp * n_px * (4 + (2 if hutch else 0)))}
     per = {k: v[0] / max(v[1], 1) for k, v in phases.items()}
     dom = max(per, key=per.get)
     peaks, peak_src = measured_peaks()
@@ -405,7 +419,7 @@ def run_gpu(args, cfg, rank, world):
         red_roof = {"bound": "l2_reductions", "kernel": dom, "achieved": round(red_ach, 1),
                     "peak": round(red_peak, 1), "unit": "G reductions/s",
                     "frac": round(red_ach / red_peak, 4),
-                    "peak_source": "measured live (cs_measure_reduction_rate)",
+                    "peak_source": "cs_measure_reduction_rate, live",
                     "reductions_per_launch": reds[dom]}
     # the same steps replayed as a CUDA graph (batch k mod n_batches chosen
     # on the device), launch shape from the autotuner
@@ -413,8 +427,9 @@ def run_gpu(args, cfg, rank, world):
     if not args.no_graph and world == 1:
         st_g = ops.SGDState(v0, mode="hutchinson", alpha=alpha, eta0=1.0, beta=0.9,
                             armijo_c=0.5, n_probes=cfg["K"], seed=cfg["seed"] + 11)
-        prob = ops.Problem(geom, st_g, images, quat, df if W["ctf"] else None, B, lam,
-                           W["n_img"] / B)
+        n_full = W["n_img"] // B * B        # the device-side batch cursor takes full batches
+        prob = ops.Problem(geom, st_g, images[:n_full], quat[:n_full],
+                           df[:n_full] if W["ctf"] else None, B, lam, W["n_img"] / B)
         hg = ops.Handle(torch.cuda.current_device())
         bt, bps = hg.autotune([prob])
         gr = hg.multi_step_graph([prob])
@@ -429,6 +444,7 @@ def run_gpu(args, cfg, rank, world):
         torch.cuda.synchronize()
         gms = g0.elapsed_time(g1) / args.steps
         graph = {"ms_per_step": round(gms, 4), "images_per_s": round(B / (gms / 1e3), 1),
+                 "batches": f"{n_full // B} full batches of {B}",
                  "launch_shape": {"block_threads": bt, "blocks_per_sm": bps},
                  "api": "cs_multi_step_graph with one problem, cs_graph_launch"}
         gr.close()
@@ -447,16 +463,16 @@ def run_gpu(args, cfg, rank, world):
         per_pass = []
         for i in range(20):
             ev[i][0].record(stream)
-            for b in range(nb):
-                sl = slice(b * B, (b + 1) * B)
-                h.quat_to_rot(quat[sl], rot)
-                h.loss_grad(geom, st.v, images[sl], rot, dfs(sl), lam, scale, grad=g_buf,
-                            loss=l_buf)
+            for start, size in bl:
+                sl = slice(start, start + size)
+                h.quat_to_rot(quat[sl], rot[:size])
+                h.loss_grad(geom, st.v, images[sl], rot[:size], dfs(sl), lam,
+                            W["n_img"] / size, grad=g_buf, loss=l_buf)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         per_pass = sorted(a.elapsed_time(b_) for a, b_ in ev)
         med = per_pass[len(per_pass) // 2]
-        ips = nb * B / (med / 1e3)
+        ips = W["n_img"] / (med / 1e3)
         npx = n_disc_pixels(M, M // 2 - 1)
         # byte rates the images/s stand for: per image, its disc pixels and
         # pose from HBM; in L2 the trilinear gathers (8 corners x 8 bytes)
@@ -464,10 +480,11 @@ def run_gpu(args, cfg, rank, world):
         lg = {"metric": "cs_loss_grad images/s (loss + gradient only)",
               "value": round(ips, 1), "unit": "images/s",
               "ms_per_pass_median": round(med, 4), "passes": 20,
-              "pass": f"{nb} batches of {B} (every image once), poses converted per batch",
+              "pass": f"{W['n_img']} images in {nb} batches of up to {B} (every image once), "
+                      "poses converted per batch",
               "hbm_GB_per_s_equivalent": round(ips * (8 * npx + 20) / 1e9, 1),
               "l2_GB_per_s_equivalent": round(ips * (64 + 64) * npx / 1e9, 1)}
-    return dict(ms=ms, launches=launches, phases={k: round(v, 4) for k, v in per.items()},
+    return dict(ms=ms, timed_images=timed_images, launches=launches, phases={k: round(v, 4) for k, v in per.items()},
                 roofline=roof, red_roofline=red_roof, e2e=e2e, clocks=clk, scalars=sc, n_img=W["n_img"],
                 loss_grad_only=lg, graph=graph)
 
@@ -477,13 +494,13 @@ TTE_CONFIGS = {
     # Fourier volume, images, batch, epochs as in the refinement workloads
     "m32_nearest": dict(M=32, n_img=1000, B=100, epochs=5, interp="nearest", K=16, df=None,
                         snr=0.1, blobs=20, seed=1000),
-    "m64_trilinear_ctf": dict(M=64, n_img=20480, B=256, epochs=10, interp="trilinear", K=32,
+    "m64_trilinear_ctf": dict(M=64, n_img=20000, B=256, epochs=10, interp="trilinear", K=32,
                               df=(1.0, 3.0), snr=0.05, blobs=200, seed=2000),
     # the same problems with little image noise (SNR 10): the mini-batch
     # noise floor drops and the conditioning of H decides the speed
     "m32_nearest_snr10": dict(M=32, n_img=1000, B=100, epochs=5, interp="nearest", K=16,
                               df=None, snr=10.0, blobs=20, seed=1000),
-    "m64_trilinear_ctf_snr10_b1024": dict(M=64, n_img=20480, B=1024, epochs=20,
+    "m64_trilinear_ctf_snr10_b1024": dict(M=64, n_img=20000, B=1024, epochs=20,
                                           interp="trilinear", K=32, df=(1.0, 3.0), snr=10.0,
                                           blobs=200, seed=2000),
 }
@@ -533,7 +550,6 @@ def sgd_arms(h, torch, ops, synth, W, cfg, vstar, lam, arms, epochs):
     geom, images, quat, df, n_img = W["geom"], W["images"], W["quat"], W["df"], W["n_img"]
     alpha = h.threshold_alpha(geom, df if W["ctf"] else None, n_img, lam)
     v0 = torch.from_numpy(synth.initial_volume(M, r, 1.0, cfg["seed"] + 7)).cuda()
-    scale = n_img / B
     out = {}
     for name, (mode, D) in arms.items():
         st = ops.SGDState(v0, mode=mode, alpha=alpha, eta0=1.0, beta=0.9, armijo_c=0.5,
@@ -550,12 +566,12 @@ def sgd_arms(h, torch, ops, synth, W, cfg, vstar, lam, arms, epochs):
             im_p, q_p = images[perm].contiguous(), quat[perm].contiguous()
             df_p = df[perm].contiguous() if W["ctf"] else None
             torch.cuda.synchronize()
-            for bi in range(n_img // B):
-                sl = slice(bi * B, (bi + 1) * B)
+            for start, size in batches(n_img, B):
+                sl = slice(start, start + size)
                 e0.record()
-                h.quat_to_rot(q_p[sl], rot)
-                h.precond_sgd_step(geom, st, im_p[sl], rot, df_p[sl] if df_p is not None else None,
-                                   lam, scale)
+                h.quat_to_rot(q_p[sl], rot[:size])
+                h.precond_sgd_step(geom, st, im_p[sl], rot[:size],
+                                   df_p[sl] if df_p is not None else None, lam, n_img / size)
                 e1.record()
                 h.rel_err(geom, st.v, vstar, out=err)
                 torch.cuda.synchronize()
@@ -991,6 +1007,8 @@ def cpu_baseline(cfg, n):
                       f"Hutchinson, literal Armijo loop) per host core, {max(1, n // 8)} images "
                       f"each of the {cfg['M']}^3 workload, {cores} single-threaded replicas "
                       f"started together, {wall:.1f} s wall",
+            "sample_short": f"one literal Algorithm-1 step of the FP64 oracle per core, "
+                            f"{max(1, n // 8)} images each, {cores} replicas, {wall:.1f} s",
             "single_core": single, "host_cores": cores,
             "operators_single_core": oracle_operators(cfg),
             "config1_alg1_run": oracle_config1_run()}
@@ -1071,16 +1089,75 @@ def run_reference(args, cfg, rank, world):
 
 
 def config_json(args, cfg):
-    return {"workload": f"Algorithm-1 step, {cfg['M']}^3 complex64 volume, "
-                        f"{cfg['n_img'] // cfg['B'] * cfg['B']} images {cfg['M']}x{cfg['M']} "
-                        f"in HBM, {cfg['interp']}, "
+    n_img, B = cfg["n_img"], cfg["B"]
+    nf, tail = divmod(n_img, B)
+    split = f"{nf} x {B}" + (f" + {tail}" if tail else "")
+    return {"workload": f"Algorithm-1 step, {cfg['M']}^3 complex64 volume, {n_img} images "
+                        f"{cfg['M']}x{cfg['M']} in HBM (batches {split}), {cfg['interp']}, "
                         f"{'CTF' if cfg['df'] else 'no CTF'}, {cfg['K']} probes",
-            "M": cfg["M"], "global_batch": cfg["B"] * args.gpus, "batch_per_gpu": cfg["B"],
-            "interp": cfg["interp"], "n_probes": cfg["K"],
-            "images_in_hbm_per_gpu": cfg["n_img"] // cfg["B"] * cfg["B"],
-            "parallelism": f"replicas{args.gpus}", "scatter": args.algo,
-            "l2": "inputs larger than L2: consecutive steps read distinct 134 MB batches "
-                  "from a 6.4 GB image set; the volume stays L2-resident by design"}
+            "global_batch": B * args.gpus, "batch_per_gpu": B,
+            "images_in_hbm_per_gpu": n_img, "parallelism": f"replicas{args.gpus}",
+            "l2": "inputs > L2: each step reads a distinct batch of the image set"}
+
+
+ARM_KEYS = {"plain": "plain", "hutchinson": "alg1", "precomputed": "pre", "learned": "learned",
+            "exact_diagonal_control": "exact"}
+
+
+def metric2_summary(tte, learned):
+    """Time-to-relative-error races in a few hundred bytes: per workload and
+    arm, [final relative error, device ms of the steps to 1e-2 or null]."""
+    sel = [("m32_snr0.1", (tte or {}).get("m32_nearest")),
+           ("m64_snr0.05", (tte or {}).get("m64_trilinear_ctf")),
+           ("m64_snr10_b4096", (learned or {}).get("time_to_rel_err_64_snr10_b4096"))]
+    out = {}
+    for key, res in sel:
+        if not res:
+            continue
+        out[key] = {short: [round(res[a]["final_rel_err"], 4), res[a]["ms_to_rel_err"]["0.01"]]
+                    for a, short in ARM_KEYS.items() if a in res}
+    return out or None
+
+
+def contract_line(args, cfg, world, r, cpu=None, metric2=None):
+    """The benchmark's record: the last line bench.py prints, a few KB at
+    most.  ``r`` is run_gpu's result; ``cpu`` the oracle baseline; ``metric2``
+    metric2_summary's result."""
+    ms_step = r["ms"] / args.steps
+    value = world * r["timed_images"] / (r["ms"] / 1e3)
+    e2e = None
+    if r.get("e2e"):
+        e = r["e2e"]
+        e2e = {k: e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step",
+                                 "direct_value") if k in e}
+        e2e["api"] = "cs_precond_sgd_step_host"
+        if "h2d_copy_only" in e:
+            e2e["h2d_copy_only_GB_per_s"] = e["h2d_copy_only"]["GB_per_s"]
+    cpu_line = None
+    if cpu:
+        cpu_line = {k: cpu[k] for k in ("value", "unit", "cores", "kind")}
+        cpu_line["sample"] = cpu.get("sample_short", cpu["sample"])
+        if "single_core" in cpu:
+            cpu_line["single_core_value"] = cpu["single_core"]["value"]
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "images/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_json(args, cfg),
+            "roofline": r["roofline"], "roofline_l2_reductions": r.get("red_roofline"),
+            "e2e": e2e, "gpu_launches": r["launches"],
+            "clocks": ({k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+                       if r.get("clocks") else None),
+            "cpu_baseline": cpu_line, "phases_ms_per_step": r.get("phases"),
+            "metric2": metric2}
+    if r.get("loss_grad_only"):
+        line["loss_grad_only_images_per_s"] = r["loss_grad_only"]["value"]
+    return line
+
+
+def emit_aux(name, payload):
+    """An auxiliary leg's full result, on its own line before the record."""
+    print(json.dumps({"aux": name, "result": payload}), flush=True)
 
 
 def main():
@@ -1104,37 +1181,29 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     r = run_gpu(args, cfg, rank, world)
     if rank == 0:
-        ms_step = r["ms"] / args.steps
-        value = job_value(world, cfg["B"], args.steps, r["ms"])
-        line = {"metric": METRIC, "value": round(value, 1), "unit": "images/s",
-                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": round(ms_step, 4), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic", "config": config_json(args, cfg),
-                "roofline": r["roofline"], "roofline_l2_reductions": r["red_roofline"],
-                "e2e": r["e2e"], "clocks": r["clocks"],
-                "gpu_launches": r["launches"], "phases_ms_per_step": r["phases"],
-                "loss_grad_only": r["loss_grad_only"],
-                "graph_replay": r["graph"],
-                "final_scalars": {"eta": r["scalars"][0], "k": r["scalars"][1],
-                                  "loss": r["scalars"][3]}}
+        emit_aux("step_details", {k: r[k] for k in ("phases", "e2e", "graph", "loss_grad_only",
+                                                    "red_roofline", "scalars")})
+        tte = learned = cpu = None
         if world == 1 and not args.no_metric2:
             from paper_2311_16100_gb300 import ops, synth
             h2 = ops.Handle(torch.cuda.current_device())
-            line["time_to_rel_err"] = {k: time_to_error(c, torch, ops, synth, h2)
-                                       for k, c in TTE_CONFIGS.items()}
+            tte = {k: time_to_error(c, torch, ops, synth, h2) for k, c in TTE_CONFIGS.items()}
             h2.close()
+            emit_aux("time_to_rel_err", tte)
         if world == 1 and not args.no_learned:
             from paper_2311_16100_gb300 import ops, synth
-            line["learned_preconditioner"] = learned_leg(args, torch, ops, synth)
+            learned = learned_leg(args, torch, ops, synth)
+            emit_aux("learned_preconditioner", learned)
         if world == 1 and not args.no_metric2:
             from paper_2311_16100_gb300 import ops, synth
-            line["conditioning"] = conditioning(args, torch, ops, synth)
+            emit_aux("conditioning", conditioning(args, torch, ops, synth))
         if world == 1 and not args.no_multi:
             from paper_2311_16100_gb300 import ops, synth
-            line["multi_volume"] = multi_volume(args, torch, ops, synth)
+            emit_aux("multi_volume", multi_volume(args, torch, ops, synth))
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_sample)
+            cpu = cpu_baseline(cfg, args.cpu_sample)
+            emit_aux("cpu_baseline", cpu)
+        line = contract_line(args, cfg, world, r, cpu, metric2_summary(tte, learned))
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -211,9 +211,13 @@ int cs_precompute_preconditioner(cs_handle* h, const cs_geom* g, const float* ro
  * errors return CS_ERR_ARG / CS_ERR_SHAPE as in cs_hutchinson_diag (no
  * message is recorded: there is no handle).  No cudaMalloc or cudaFree is
  * made.  The first call on a device looks up the array's device address
- * (make it before any stream capture).  All calls share the array, so calls
- * that overlap on the GPU (different streams, or devices sharing nothing but
- * the process) race on it: serialise them on one stream per device. */
+ * (make it before any stream capture); that address is kept for the life of
+ * the process, so do not call this entry point on a device after a
+ * cudaDeviceReset of it.  Each device holds its own copy of the array; all
+ * calls on one device share that copy and find the last call's probe words
+ * in it (every call rewrites the words it reads), so calls that overlap on
+ * the same GPU (different streams) race on it: serialise them on one stream
+ * per device. */
 int cs_hutchinson_diag_noalloc(const cs_geom* g, const float* rot,
                                const float* defocus, int B, float lambda,
                                float scale, int n_probes, uint64_t seed,

@@ -32,7 +32,10 @@ int g_num_sms[kMaxDevices] = {};
 
 // Device address of the scratch array and the SM count, fetched once per
 // device with that device current.  In host code the array's name is only a
-// host-side stand-in, never a device address.
+// host-side stand-in, never a device address.  The cached address belongs
+// to the device's context as it was at the first call: after a
+// cudaDeviceReset of that device the array is reloaded elsewhere, so this
+// entry point must not be called on a device that was reset.
 cudaError_t setup_device(int dev, uint32_t** scratch, int* num_sms) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_scratch_ptr[dev]) {
@@ -71,10 +74,13 @@ extern "C" int cs_hutchinson_diag_noalloc(const cs_geom* g, const float* rot,
   if ((long)B * nch > 0x7fffffffL) return CS_ERR_SHAPE;
   if (B > 0 && !rot) return CS_ERR_ARG;
   if (B > 0 && g->ctf.enabled && !defocus) return CS_ERR_ARG;
-  if (g->ctf.enabled &&
-      !(g->ctf.kv > 0 && g->ctf.pixel_A > 0 && g->ctf.cs_mm >= 0 && g->ctf.amp >= 0 &&
-        g->ctf.amp < 1))
-    return CS_ERR_ARG;
+  if (g->ctf.enabled) {
+    const cs_ctf& c = g->ctf;
+    if (!(std::isfinite(c.kv) && c.kv > 0) || !(std::isfinite(c.pixel_A) && c.pixel_A > 0) ||
+        !(std::isfinite(c.cs_mm) && c.cs_mm >= 0) ||
+        !(std::isfinite(c.amp) && c.amp >= 0 && c.amp < 1))
+      return CS_ERR_ARG;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();

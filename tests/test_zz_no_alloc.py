@@ -4,10 +4,13 @@ Some callers of this library cannot allocate device memory when they need
 the preconditioner estimate: they run inside another application's stream
 capture, or their device memory belongs to a caching allocator, or they
 allocate only at start-up.  cs_hutchinson_diag_noalloc serves them with a
-fixed scratch array inside the library.  This test checks that two calls in
-a row agree with cs_hutchinson_diag (same tolerance as the other parity
-tests), that the scratch size limit is enforced, and that no device memory
-is taken from the caller's allocator.  It is collected last on purpose.
+fixed scratch array inside the library.  This test checks that calls in a
+row agree with cs_hutchinson_diag (same tolerance as the other parity
+tests) under trilinear and nearest interpolation, up to the largest grid the
+scratch holds (128^3) and for an empty batch, that the size limit and the
+argument checks are enforced, and that the calls take no device memory,
+neither from the caller's allocator nor from the device (cudaMemGetInfo).
+It is collected last on purpose.
 """
 import ctypes
 
@@ -37,36 +40,71 @@ def call_noalloc(lib, geom, rot, df, B, lam, scale, K, seed, block, out):
         block, ctypes.c_void_p(out.data_ptr()), stream)
 
 
-def test_noalloc_matches_hutchinson_diag_twice(lib):
+# (M, B, probes, probe block, interpolation, CTF)
+CASES = ((32, 24, 16, 3, "trilinear", True),
+         (64, 10, 32, 7, "trilinear", True),
+         (128, 4, 32, 2, "trilinear", True),      # the largest grid the scratch holds
+         (32, 20, 8, 5, "nearest", False),
+         (40, 16, 1, 9, "nearest", True),
+         (16, 0, 32, 1, "trilinear", True))       # empty batch: diag = lambda
+
+
+def test_noalloc_matches_hutchinson_diag_in_a_row(lib):
     from paper_2311_16100_gb300 import native as N
     from paper_2311_16100_gb300.ops import Handle
     torch.cuda.set_device(0)
     h = Handle(0)
-    for call, (M, B, K, block, interp) in enumerate(((32, 24, 16, 3, "trilinear"),
-                                                     (64, 10, 32, 7, "trilinear"))):
-        c = Case(M, B, interp=interp, ctf=True, seed=900 + call)
+    lam, scale = 0.01, 8.0
+    for call, (M, B, K, block, interp, ctf) in enumerate(CASES):
+        c = Case(M, max(B, 1), interp=interp, ctf=ctf, seed=900 + call)
         g = c.to_gpu()
         geom = c.gpu_geometry()
-        want = h.hutchinson_diag(geom, g["rot"], g["df"], 0.01, 8.0, n_probes=K, seed=11,
-                                 probe_block=block)
-        out = torch.full((M, M, M), float("nan"), device="cuda")
-        torch.cuda.synchronize()
-        before = torch.cuda.memory_allocated()
-        rc = call_noalloc(lib, geom, g["rot"], g["df"], B, 0.01, 8.0, K, 11, block, out)
-        torch.cuda.synchronize()
-        assert rc == N.CS_OK
-        assert torch.cuda.memory_allocated() == before
-        assert rel_l2(out.cpu().numpy(), want.cpu().numpy()) <= TOL
+        # with B = 0 the pointers stay valid, and the call must not read them
+        rot = g["rot"]
+        df = g["df"] if ctf else None
+        want = h.hutchinson_diag(geom, rot[:B].contiguous(),
+                                 df[:B].contiguous() if ctf else None, lam, scale,
+                                 n_probes=K, seed=11, probe_block=block)
+        outs = []
+        for rep in range(2):                     # two calls in a row on the shared scratch
+            out = torch.full((M, M, M), float("nan"), device="cuda")
+            torch.cuda.synchronize()
+            before = torch.cuda.memory_allocated()
+            free_before = torch.cuda.mem_get_info()[0]
+            rc = call_noalloc(lib, geom, rot, df, B, lam, scale, K, 11, block, out)
+            torch.cuda.synchronize()
+            free_after = torch.cuda.mem_get_info()[0]
+            assert rc == N.CS_OK, (M, B, interp, rep)
+            assert torch.cuda.memory_allocated() == before
+            if call > 0 or rep > 0:
+                # after the first call (which may load the library's kernels)
+                # no device memory changes hands
+                assert free_after == free_before, (M, B, interp, rep)
+            outs.append(out)
+        for out in outs:
+            if B == 0:
+                assert bool(torch.all(out == lam)) and bool(torch.all(want == lam))
+            else:
+                assert rel_l2(out.cpu().numpy(), want.cpu().numpy()) <= TOL, (M, B, interp)
     h.close()
 
 
-def test_noalloc_rejects_grids_beyond_its_scratch(lib):
+def test_noalloc_rejects_bad_arguments(lib):
     from paper_2311_16100_gb300 import native as N
     from paper_2311_16100_gb300.ops import CTF, Geometry
-    geom = Geometry(130, interp="trilinear", ctf=CTF())
     rot = torch.eye(3, device="cuda").reshape(1, 3, 3).contiguous()
     df = torch.full((1,), 2e4, device="cuda")
     out = torch.zeros((1,), device="cuda")
+    geom = Geometry(130, interp="trilinear", ctf=CTF())       # beyond the fixed scratch
     assert call_noalloc(lib, geom, rot, df, 1, 0.0, 1.0, 8, 1, 0, out) == N.CS_ERR_SHAPE
+    small = torch.zeros((32, 32, 32), device="cuda")
     assert call_noalloc(lib, Geometry(32), rot, df, 1, 0.0, 1.0, 33, 1, 0,
-                        torch.zeros((32, 32, 32), device="cuda")) == N.CS_ERR_SHAPE
+                        small) == N.CS_ERR_SHAPE
+    for bad in (CTF(kv=float("inf")), CTF(pixel_A=float("inf")), CTF(cs_mm=float("inf")),
+                CTF(kv=float("nan")), CTF(amp=1.0)):
+        assert call_noalloc(lib, Geometry(32, ctf=bad), rot, df, 1, 0.0, 1.0, 8, 1, 0,
+                            small) == N.CS_ERR_ARG
+    assert call_noalloc(lib, Geometry(32), rot, df, 1, float("inf"), 1.0, 8, 1, 0,
+                        small) == N.CS_ERR_ARG
+    torch.cuda.synchronize()
+    assert bool(torch.all(small == 0))           # nothing was enqueued
