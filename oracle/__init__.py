@@ -31,8 +31,16 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
                        (every probe exact, equal batches average to the
                        full diagonal), dense-Hessian z-scores under trilinear
   alpha_threshold      pinned: shell-ratio asymptotics, shell mean of diag(H)
-  alg1_step            pinned: EM M-step equivalence (nearest, exact D, eta=1),
-                       monotone decrease under the Armijo rule
+  alg1_step            pinned: EM M-step equivalence (nearest, exact D, eta=1);
+                       accepted eta against the closed-form Armijo bound;
+                       preconditioner update in closed form under nearest
+                       interpolation (every estimate exact, Remark 3.3):
+                       D_avg^(k) = mean of the batch diagonals,
+                       D^(k) = beta^k + (1 - beta^k) diag for equal batches;
+                       the step v - eta g / max(|D|, alpha)
+  coverage_features    pinned: nearest = brute-force pixel counts; the
+                       weights of a pixel sum to 1 (sum = B n_px) and the
+                       CTF^2 sum equals sum_i sum_p C_ip^2
   cg_solve             pinned: closed form under nearest interpolation
   diagnostics.fsc      pinned: Eq. fsc identities (1, -1, cos theta, shell
                        locality, energy partition), independent noise ~ 0
@@ -46,7 +54,8 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   mlp (learned preconditioner network; not in the paper)
                        pinned: BF16 rounding and GELU against torch's
                        library routines, backpropagation against central
-                       finite differences of the FP64 network
+                       finite differences of the FP64 network; features:
+                       the |k| column voxel by voxel from its index
 """
 from .geometry import (ball_mask, ctf_of_s2, ctf_pixels, default_r_max, disc_mask,
                        electron_wavelength_A, freq_axis, nearest_coords_fp32,

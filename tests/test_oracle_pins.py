@@ -534,3 +534,144 @@ def test_cg_matches_nearest_closed_form():
     vs, _ = O.cg_solve(b, R, df, M, r, "nearest", CTF, lam)
     D = O.exact_diag(R, df, M, r, "nearest", CTF, lam, 1.0)
     np.testing.assert_allclose(vs, b / D, atol=1e-10 * np.max(np.abs(b / D)))
+
+
+# --------------------------------------- Algorithm 1's preconditioner update
+def _alg1_run(batches, M, r, lam, scale, alpha, beta, steps, mode="hutchinson"):
+    """Run alg1_step k = 1..steps on the given (x, R, df) batches in turn,
+    collecting D_avg^(k), D^(k), the accepted eta and the step v - v+."""
+    v = cplx((M, M, M), 50)
+    D, Da, eta = np.ones((M, M, M)), np.zeros((M, M, M)), 1.0
+    hist = []
+    for k in range(1, steps + 1):
+        x, R, df = batches[(k - 1) % len(batches)]
+        out = O.alg1_step(v, D, Da, eta, k, x, R, df, M, r, "nearest", None, lam, scale,
+                          alpha, beta, 0.5, mode, n_probes=3, seed=17)
+        hist.append(dict(D_avg=out["D_avg"], D=out["D"], eta=out["eta"], v=v,
+                         step=v - out["v"]))
+        v, D, Da, eta = out["v"], out["D"], out["D_avg"], out["eta"]
+    return hist
+
+
+def test_alg1_preconditioner_update_closed_form_equal_batches():
+    """Algorithm 1 (Eqs. hutch update and exp avg update) under nearest
+    interpolation without CTF, the same batch at every iteration: H_I is
+    diagonal, so every Rademacher estimate is exactly diag(H_I) (Remark 3.3),
+    the running mean stays diag(H_I) and the exponential average from D^0 = I
+    is D^(k) = beta^k + (1 - beta^k) diag(H_I).  A swapped beta / (1 - beta)
+    or a running mean indexed from 0 fails this."""
+    M, B = 10, 6
+    r = M // 2 - 1
+    R = rots(B, 51)
+    x = cplx((B, M, M), 52)
+    lam, scale, beta = 0.02, 3.0, 0.9
+    diag = O.exact_diag(R, np.zeros(B), M, r, "nearest", None, lam, scale)
+    hist = _alg1_run([(x, R, np.zeros(B))], M, r, lam, scale, 1e-9, beta, 5)
+    for k, h in enumerate(hist, start=1):
+        np.testing.assert_allclose(h["D_avg"], diag, rtol=1e-13)
+        np.testing.assert_allclose(h["D"], beta ** k + (1 - beta ** k) * diag, rtol=1e-12)
+
+
+def test_alg1_running_mean_over_different_batches():
+    """Different batches I_1, I_2, I_3 (nearest, no CTF, so each estimate is
+    the batch's exact diagonal): D_avg^(k) is the plain mean of the first k
+    batch diagonals, and D^(k) = beta D^(k-1) + (1 - beta) D_avg^(k) from I."""
+    M, B = 10, 5
+    r = M // 2 - 1
+    lam, scale, beta = 0.01, 4.0, 0.75
+    batches = [(cplx((B, M, M), 60 + i), rots(B, 70 + i), np.zeros(B)) for i in range(3)]
+    diags = [O.exact_diag(R, df, M, r, "nearest", None, lam, scale) for _, R, df in batches]
+    hist = _alg1_run(batches, M, r, lam, scale, 1e-9, beta, 3)
+    D = np.ones((M, M, M))
+    for k, h in enumerate(hist, start=1):
+        mean_k = sum(diags[:k]) / k
+        np.testing.assert_allclose(h["D_avg"], mean_k, rtol=1e-13)
+        D = beta * D + (1 - beta) * mean_k
+        np.testing.assert_allclose(h["D"], D, rtol=1e-12)
+    # the batch diagonals really differ, so the mean is not trivially one of them
+    assert np.max(np.abs(diags[0] - diags[1])) > 1.0
+
+
+def test_alg1_step_divides_by_thresholded_d():
+    """Eq. thresh and the step of Algorithm 1: v+ = v - eta g / max(|D|, alpha),
+    with g the mini-batch gradient (pinned by finite differences) and D the
+    closed form above; alpha is set between the smallest and largest D so
+    that both branches of the maximum occur."""
+    M, B = 10, 6
+    r = M // 2 - 1
+    R = rots(B, 53)
+    x = cplx((B, M, M), 54)
+    lam, scale, beta = 0.02, 3.0, 0.9
+    diag = O.exact_diag(R, np.zeros(B), M, r, "nearest", None, lam, scale)
+    D1 = beta + (1 - beta) * diag
+    alpha = float(0.5 * (D1.min() + D1.max()))
+    hist = _alg1_run([(x, R, np.zeros(B))], M, r, lam, scale, alpha, beta, 1)
+    h = hist[0]
+    _, g = O.loss_grad(h["v"], x, R, np.zeros(B), M, r, "nearest", None, lam, scale)
+    Dhat = np.where(D1 < alpha, alpha, D1)
+    assert 0 < np.count_nonzero(D1 < alpha) < D1.size
+    np.testing.assert_allclose(h["step"], h["eta"] * g / Dhat,
+                               atol=1e-12 * np.max(np.abs(h["step"])))
+    # plain mode: D-hat = I
+    hp = _alg1_run([(x, R, np.zeros(B))], M, r, lam, scale, alpha, beta, 1, mode="plain")[0]
+    np.testing.assert_allclose(hp["step"], hp["eta"] * g,
+                               atol=1e-12 * np.max(np.abs(hp["step"])))
+
+
+# ------------------------------------------------ per-voxel network features
+def test_coverage_features_nearest_are_pixel_counts():
+    """Nearest without CTF every weight is 1: the coverage count is the
+    brute-force-pinned diagonal count |Omega_j| (exact_diag with lam = 0,
+    scale 1) and the CTF^2 sum equals it (C = 1)."""
+    M, B = 10, 7
+    r = M // 2 - 1
+    R = rots(B, 55)
+    cov, c2 = O.coverage_features(R, np.zeros(B), M, r, "nearest", None)
+    counts = O.exact_diag(R, np.zeros(B), M, r, "nearest", None, 0.0, 1.0)
+    np.testing.assert_array_equal(cov, counts)
+    np.testing.assert_array_equal(c2, counts)
+    assert cov.sum() == B * int(np.count_nonzero(O.disc_mask(M, r)))
+
+
+@pytest.mark.parametrize("interp", ["nearest", "trilinear"])
+def test_coverage_features_conserve_pixel_mass(interp):
+    """The weights of a pixel sum to one (Definition 2.1's interpolation
+    reproduces constants), so sum_j coverage_j = B n_px and
+    sum_j ctf2w_j = sum_i sum_p C_ip^2 with C from the pinned CTF formula."""
+    M, B = 12, 5
+    r = M // 2 - 1
+    R = rots(B, 56)
+    df = synth.defocus_angstrom(B, 57)
+    cov, c2 = O.coverage_features(R, df, M, r, interp, CTF)
+    m = O.disc_mask(M, r)
+    kx, ky = O.pixel_coords(M)
+    q = (kx * kx + ky * ky)[m]
+    c2_total = sum(float(np.sum(O.ctf_pixels(q, df[i], M, CTF) ** 2)) for i in range(B))
+    assert abs(cov.sum() - B * int(np.count_nonzero(m))) < 1e-9 * B * m.sum()
+    assert abs(c2.sum() - c2_total) < 1e-9 * c2_total
+    assert np.all(cov >= 0) and np.all(c2 >= 0) and np.all(c2 <= cov + 1e-12)
+
+
+def test_network_features_radius_column_closed_form():
+    """The first feature of voxel j = (iz M + iy) M + ix is
+    |k| / (M/2) with k = (ix, iy, iz) - M/2, written out voxel by voxel; the
+    other two are log1p of the given per-voxel sums in the same order."""
+    import math
+    M = 12
+    h = M // 2
+    g = np.random.default_rng(5)
+    cov = g.uniform(0, 50, size=(M, M, M))
+    c2 = g.uniform(0, 9, size=(M, M, M))
+    F = O.mlp.features(M, cov, c2)
+    assert F.shape == (M ** 3, 3)
+    for j in list(g.integers(0, M ** 3, size=40)) + [0, (h * M + h) * M + h,
+                                                     (h * M + h) * M, (h * M + h) * M + h + 3]:
+        iz, rem = divmod(int(j), M * M)
+        iy, ix = divmod(rem, M)
+        want = math.sqrt((ix - h) ** 2 + (iy - h) ** 2 + (iz - h) ** 2) / h
+        assert abs(F[j, 0] - want) < 1e-15
+        assert abs(F[j, 1] - math.log(1 + cov[iz, iy, ix])) < 1e-13
+        assert abs(F[j, 2] - math.log(1 + c2[iz, iy, ix])) < 1e-13
+    assert F[(h * M + h) * M + h, 0] == 0.0          # the centre, k = 0
+    assert F[(h * M + h) * M, 0] == 1.0               # k = (-M/2, 0, 0)
+    assert abs(F[0, 0] - math.sqrt(3)) < 1e-15        # the corner (-M/2, -M/2, -M/2)
