@@ -13,6 +13,7 @@ neither from the caller's allocator nor from the device (cudaMemGetInfo).
 It is collected last on purpose.
 """
 import ctypes
+import gc
 
 import pytest
 
@@ -69,13 +70,21 @@ def test_noalloc_matches_hutchinson_diag_in_a_row(lib):
         for rep in range(2):                     # two calls in a row on the shared scratch
             out = torch.full((M, M, M), float("nan"), device="cuda")
             torch.cuda.synchronize()
-            before = torch.cuda.memory_allocated()
-            free_before = torch.cuda.mem_get_info()[0]
-            rc = call_noalloc(lib, geom, rot, df, B, lam, scale, K, 11, block, out)
-            torch.cuda.synchronize()
-            free_after = torch.cuda.mem_get_info()[0]
+            # no garbage collection inside the measured window: freeing an
+            # earlier test's tensors there would change the counters
+            gc.collect()
+            gc.disable()
+            try:
+                before = torch.cuda.memory_allocated()
+                free_before = torch.cuda.mem_get_info()[0]
+                rc = call_noalloc(lib, geom, rot, df, B, lam, scale, K, 11, block, out)
+                torch.cuda.synchronize()
+                free_after = torch.cuda.mem_get_info()[0]
+                after = torch.cuda.memory_allocated()
+            finally:
+                gc.enable()
             assert rc == N.CS_OK, (M, B, interp, rep)
-            assert torch.cuda.memory_allocated() == before
+            assert after == before
             if call > 0 or rep > 0:
                 # after the first call (which may load the library's kernels)
                 # no device memory changes hands
