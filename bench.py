@@ -494,17 +494,20 @@ TTE_CONFIGS = {
     # Fourier volume, images, batch, epochs as in the refinement workloads
     "m32_nearest": dict(M=32, n_img=1000, B=100, epochs=5, interp="nearest", K=16, df=None,
                         snr=0.1, blobs=20, seed=1000),
-    "m64_trilinear_ctf": dict(M=64, n_img=20000, B=256, epochs=10, interp="trilinear", K=32,
+    "m64_trilinear_ctf": dict(M=64, n_img=20480, B=256, epochs=10, interp="trilinear", K=32,
                               df=(1.0, 3.0), snr=0.05, blobs=200, seed=2000),
     # the same problems with little image noise (SNR 10): the mini-batch
     # noise floor drops and the conditioning of H decides the speed
     "m32_nearest_snr10": dict(M=32, n_img=1000, B=100, epochs=5, interp="nearest", K=16,
                               df=None, snr=10.0, blobs=20, seed=1000),
-    "m64_trilinear_ctf_snr10_b1024": dict(M=64, n_img=20000, B=1024, epochs=20,
+    "m64_trilinear_ctf_snr10_b1024": dict(M=64, n_img=20480, B=1024, epochs=20,
                                           interp="trilinear", K=32, df=(1.0, 3.0), snr=10.0,
                                           blobs=200, seed=2000),
 }
 THRESHOLDS = [0.5, 0.3, 0.2, 0.15, 0.1, 0.05, 0.02, 0.01]
+# the learned preconditioner's features come from the first 1/8 of a
+# dataset's poses (scaled to the whole dataset), in training and in use
+FEATURE_SUBSAMPLE = 8
 
 
 def ground_truth(h, torch, synth, W, cfg, lam):
@@ -721,7 +724,7 @@ def learned_leg(args, torch, ops, synth):
         rot = h.quat_to_rot(q)
         df = torch.from_numpy(synth.defocus_angstrom(50000, 8001 + 10 * s_, 0.5, 3.5)
                               .astype("float32")).to(dev)
-        cov, c2w = dataset_features(h, geom, rot, df)
+        cov, c2w = dataset_features(h, geom, rot, df, subsample=FEATURE_SUBSAMPLE)
         samples.append(Sample(M, r, cov, c2w, hutchinson_target(h, geom, rot, df)))
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
@@ -750,7 +753,7 @@ def learned_leg(args, torch, ops, synth):
     W = build_workload(cfg, 0, h, torch, ops, synth)
     lam = W["sigma2"]
     vstar, rot_all = ground_truth(h, torch, synth, W, cfg, lam)
-    cov, c2w = dataset_features(h, W["geom"], rot_all, W["df"])
+    cov, c2w = dataset_features(h, W["geom"], rot_all, W["df"], subsample=FEATURE_SUBSAMPLE)
     D_learned = net.predict(64, cov, c2w, lam)
     exact, _, _ = h.exact_diag(W["geom"], rot_all, W["df"], lam, 1.0)
     D_pre, _ = precomputed(h, torch, W, rot_all, cfg, lam)
@@ -778,7 +781,7 @@ def learned_race(h, torch, ops, synth, net, geom, samples, hist, t_data, t_train
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
-    cov, c2w = dataset_features(h, geom, rot_all, W["df"])
+    cov, c2w = dataset_features(h, geom, rot_all, W["df"], subsample=FEATURE_SUBSAMPLE)
     D_learned = net.predict(M, cov, c2w, lam)
     e1.record()
     torch.cuda.synchronize()
@@ -794,6 +797,7 @@ def learned_race(h, torch, ops, synth, net, geom, samples, hist, t_data, t_train
     per = len(samples) * samples[0].n_ball
     out = {"training": {"datasets": "8 x 50000 poses, 128^3, defocus U[0.5,3.5] um",
                         "targets": "log of Hutchinson estimates, 4 x 32 probes",
+                        "features": f"from 1/{FEATURE_SUBSAMPLE} of each dataset's poses",
                         "adam_steps": len(hist), "mse_first": hist[0] / per,
                         "mse_last": hist[-1] / per,
                         "data_s": round(t_data, 3), "train_s": round(t_train, 3)},

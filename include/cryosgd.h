@@ -227,10 +227,11 @@ int cs_hutchinson_diag_noalloc(const cs_geom* g, const float* rot,
 /* Exact diagonal of the mini-batch Hessian (Eq. hessian; under nearest
  * interpolation without CTF it is |Omega_j| + lambda, Eq. H diag):
  *   diag_out_j = lambda + scale sum_i sum_p C_ip^2 w_pj^2,
- * and the per-voxel features coverage_j = sum_i sum_p w_pj (the pose
+ * and the per-voxel features coverage_j = scale sum_i sum_p w_pj (the pose
  * coverage count |Omega_j| of Section 3.1 under nearest interpolation) and
- * ctf2w_j = sum_i sum_p C_ip^2 w_pj.  All float[M^3], overwritten; each of
- * the three outputs may be NULL. */
+ * ctf2w_j = scale sum_i sum_p C_ip^2 w_pj; with scale = N/B the batch's
+ * sums estimate the dataset's.  All float[M^3], overwritten; each of the
+ * three outputs may be NULL. */
 int cs_exact_diag(cs_handle* h, const cs_geom* g, const float* rot,
                   const float* defocus, int B, float lambda, float scale,
                   float* diag_out, float* coverage_out, float* ctf2w_out,
@@ -443,12 +444,14 @@ int cs_autotune(cs_handle* h, const cs_problem* probs, int n, int* block_threads
  * ------------------------------------------------------------------------ */
 #define CS_MLP_NPARAMS 4481
 
-/* out_j = network(features_j) for all M^3 voxels (exp_out: exp of it, the
- * preconditioner D itself).  use_tensor_cores = 0 runs the FP32 reference
- * kernel (same rounding points). */
+/* out_j = network(features_j) + offset for all M^3 voxels (exp_out:
+ * exp(network(features_j)) + offset, the preconditioner D = exp(log D) +
+ * lambda when offset = lambda).  use_tensor_cores = 0 runs the FP32
+ * reference kernel (same rounding points).  CS_ERR_ARG for a non-finite
+ * offset. */
 int cs_mlp_forward(cs_handle* h, int M, const float* params, const float* coverage,
-                   const float* ctf2w, float* out, int exp_out, int use_tensor_cores,
-                   void* stream);
+                   const float* ctf2w, float* out, int exp_out, float offset,
+                   int use_tensor_cores, void* stream);
 /* grad += gradient of L = mean over voxels with |k| <= r_ball of
  * (network_j - target_j)^2; *sse += sum of squared residuals (device
  * double).  The caller zeroes grad and sse. */
@@ -456,9 +459,23 @@ int cs_mlp_grad(cs_handle* h, int M, int r_ball, const float* params, const floa
                 const float* ctf2w, const float* target, float* grad, double* sse,
                 int use_tensor_cores, void* stream);
 /* One Adam step (Kingma & Ba 2015) on params with moments m, v (caller
- * zeroes them before step 1); grad is read and zeroed.  step >= 1. */
-int cs_mlp_adam_step(cs_handle* h, float* params, float* m, float* v, float* grad, int step,
-                     float lr, float beta1, float beta2, float eps, void* stream);
+ * zeroes them before step 1), on the gradient grad_scale * grad (e.g.
+ * 1 / number of accumulated samples: the mean of per-sample gradients);
+ * grad is read and zeroed.  step >= 1; CS_ERR_ARG for a non-finite or
+ * non-positive grad_scale or hyper-parameters out of range. */
+int cs_mlp_adam_step(cs_handle* h, float* params, float* m, float* v, float* grad,
+                     float grad_scale, int step, float lr, float beta1, float beta2, float eps,
+                     void* stream);
+/* Training target of the network from n_est >= 1 Hutchinson estimates of
+ * the diagonal (Eq. hutch), estimates float[n_est][M^3] (e.g. independent
+ * probe blocks of cs_hutchinson_diag with lambda = 0):
+ *   m_j = (1/n_est) sum_e estimates[e][j],
+ *   target_j = log(max(m_j, floor_rel * mean of the positive m_j))
+ * (floor_rel alone when no m_j is positive).  target float[M^3],
+ * overwritten.  CS_ERR_ARG for NULL pointers or floor_rel not in (0, 1];
+ * CS_ERR_SHAPE for M or n_est out of range. */
+int cs_mlp_target(cs_handle* h, int M, int n_est, const float* estimates, float floor_rel,
+                  float* target, void* stream);
 /* Failure-handling self-test (no counterpart in the paper): launches one
  * block whose mbarrier wait can never complete; the wait gives up after
  * `spins` polls (1 .. 2^24) and records the expiry in the handle's device

@@ -1453,15 +1453,32 @@ long ball_count(int M, int r) {
 extern "C" {
 
 int cs_mlp_forward(cs_handle* h, int M, const float* params, const float* cov, const float* c2w,
-                   float* out, int exp_out, int tc, void* stream) {
+                   float* out, int exp_out, float offset, int tc, void* stream) {
   if (!h) return CS_ERR_ARG;
   if (M < 4 || M > CS_MAX_M || (M & 1)) return fail(h, CS_ERR_SHAPE, "M=%d invalid", M);
   if (!params || !cov || !c2w || !out) return fail(h, CS_ERR_ARG, "NULL pointer argument");
+  if (!is_finite(offset)) return fail(h, CS_ERR_ARG, "offset is not finite");
   CS_SCOPE(h);
   CS_TRY(ensure_status(h));
-  CS_CUDA(launch_mlp_forward(M, params, cov, c2w, out, exp_out, tc != 0, h->status, h->num_sms,
-                             S(stream)),
+  CS_CUDA(launch_mlp_forward(M, params, cov, c2w, out, exp_out, offset, tc != 0, h->status,
+                             h->num_sms, S(stream)),
           "mlp_forward launch");
+  return CS_OK;
+}
+
+int cs_mlp_target(cs_handle* h, int M, int n_est, const float* est, float floor_rel,
+                  float* target, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  if (M < 4 || M > CS_MAX_M || (M & 1)) return fail(h, CS_ERR_SHAPE, "M=%d invalid", M);
+  if (n_est < 1 || n_est > 4096) return fail(h, CS_ERR_SHAPE, "n_est=%d invalid", n_est);
+  if (!est || !target) return fail(h, CS_ERR_ARG, "NULL pointer argument");
+  if (!(floor_rel > 0.f && floor_rel <= 1.f))
+    return fail(h, CS_ERR_ARG, "floor_rel must be in (0, 1]");
+  CS_SCOPE(h);
+  Workspace w;
+  CS_TRY(ensure_ws(h, M, 1, &w));
+  CS_CUDA(launch_mlp_target(M, n_est, est, floor_rel, target, w.part, h->num_sms, S(stream)),
+          "mlp_target launch");
   return CS_OK;
 }
 
@@ -1482,14 +1499,18 @@ int cs_mlp_grad(cs_handle* h, int M, int r_ball, const float* params, const floa
   return CS_OK;
 }
 
-int cs_mlp_adam_step(cs_handle* h, float* params, float* m, float* v, float* grad, int step,
-                     float lr, float b1, float b2, float eps, void* stream) {
+int cs_mlp_adam_step(cs_handle* h, float* params, float* m, float* v, float* grad,
+                     float grad_scale, int step, float lr, float b1, float b2, float eps,
+                     void* stream) {
   if (!h) return CS_ERR_ARG;
   if (!params || !m || !v || !grad) return fail(h, CS_ERR_ARG, "NULL pointer argument");
   if (step < 1 || !(lr > 0) || !(b1 >= 0 && b1 < 1) || !(b2 >= 0 && b2 < 1) || !(eps > 0))
     return fail(h, CS_ERR_ARG, "Adam hyper-parameters out of range");
+  if (!(is_finite(grad_scale) && grad_scale > 0))
+    return fail(h, CS_ERR_ARG, "grad_scale must be finite and positive");
   CS_SCOPE(h);
-  CS_CUDA(launch_adam(params, m, v, grad, step, lr, b1, b2, eps, S(stream)), "adam launch");
+  CS_CUDA(launch_adam(params, m, v, grad, grad_scale, step, lr, b1, b2, eps, S(stream)),
+          "adam launch");
   return CS_OK;
 }
 

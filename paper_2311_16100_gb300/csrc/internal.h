@@ -179,15 +179,19 @@ cudaError_t launch_update(int n, float2* v, const float2* d, const double* scala
 // learned preconditioner network (mlp.cu)
 constexpr int kMlpParams = 4481;
 cudaError_t launch_mlp_forward(int M, const float* params, const float* cov, const float* c2w,
-                               float* out, int exp_out, bool tc, int* err, int num_sms,
-                               cudaStream_t s);
+                               float* out, int exp_out, float offset, bool tc, int* err,
+                               int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_grad(int M, int r2, float inv_n, const float* params, const float* cov,
                             const float* c2w, const float* target, float* grad, double* sse,
                             bool tc, int* err, int num_sms, cudaStream_t s);
 // Failure-handling self-test: a bounded mbarrier wait that runs out.
 cudaError_t launch_wait_selftest(long long limit, int* err, cudaStream_t s);
-cudaError_t launch_adam(float* p, float* m, float* v, float* g, int step, float lr, float b1,
-                        float b2, float eps, cudaStream_t s);
+cudaError_t launch_adam(float* p, float* m, float* v, float* g, float gscale, int step,
+                        float lr, float b1, float b2, float eps, cudaStream_t s);
+// network target: log(max(mean of n_est estimates, floor_rel x mean of the
+// positive means)); part: 2 x (grid) doubles of scratch
+cudaError_t launch_mlp_target(int M, int n_est, const float* est, float floor_rel,
+                              float* target, double* part, int num_sms, cudaStream_t s);
 
 // Rate of 16-byte global reductions (G ops/s) measured on a scratch buffer.
 cudaError_t measure_red_rate(void* scratch, size_t bytes, int num_sms, cudaStream_t s,

@@ -230,11 +230,11 @@ __device__ __forceinline__ void load_params(const float* __restrict__ p, float* 
 }
 
 // ------------------------------------------------------ tensor-core kernels
-// logd[j] = MLP(features(j)) (exp_out: D = exp(logd) instead)
+// logd[j] = MLP(features(j)) + offset (exp_out: exp(logd) + offset instead)
 __global__ void __launch_bounds__(kRows)
 k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restrict__ cov,
                  const float* __restrict__ c2w, float* __restrict__ out, int exp_out,
-                 int* __restrict__ err) {
+                 float offset, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   FwdSmem& S = *reinterpret_cast<FwdSmem*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
@@ -310,7 +310,7 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
         y = fmaf(q.y, gelu_f(a2[u] + q.x), y);
       }
     }
-    if (j < n) out[j] = exp_out ? expf(y) : y;
+    if (j < n) out[j] = (exp_out ? expf(y) : y) + offset;
     fence_before();
     __syncthreads();
   }
@@ -531,7 +531,8 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
 // ------------------------------------------------------ FP32 reference kernels
 __global__ void __launch_bounds__(128)
 k_mlp_forward_ref(int M, const float* __restrict__ params, const float* __restrict__ cov,
-                  const float* __restrict__ c2w, float* __restrict__ out, int exp_out) {
+                  const float* __restrict__ c2w, float* __restrict__ out, int exp_out,
+                  float offset) {
   __shared__ float W1[192], b1[64], W2[kHid * kHid], b2[64], w3[64], b3;
   load_params(params, W1, b1, b2, w3, &b3);
   for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) W2[e] = bf16r(params[oW2 + e]);
@@ -553,7 +554,7 @@ k_mlp_forward_ref(int M, const float* __restrict__ params, const float* __restri
       for (int i = 0; i < kHid; ++i) a = fmaf(W2[o * kHid + i], h1[i], a);
       y = fmaf(w3[o], gelu_f(a + b2[o]), y);
     }
-    out[j] = exp_out ? expf(y) : y;
+    out[j] = (exp_out ? expf(y) : y) + offset;
   }
 }
 
@@ -651,12 +652,13 @@ k_mlp_grad_ref(int M, int r2, float inv_n, const float* __restrict__ params,
   if (t == 0) atomicAdd(sse, s);
 }
 
-// Adam (Kingma & Ba 2015) on the FP32 master parameters; grad is zeroed.
+// Adam (Kingma & Ba 2015) on the FP32 master parameters, gradient gs * g;
+// g is zeroed.
 __global__ void k_adam(int np, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                       float* __restrict__ g, float lr, float b1, float b2, float eps,
+                       float* __restrict__ g, float gs, float lr, float b1, float b2, float eps,
                        float c1, float c2) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
-    const float gi = g[i];
+    const float gi = gs * g[i];
     const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
     const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
     m[i] = mi;
@@ -664,6 +666,57 @@ __global__ void k_adam(int np, float* __restrict__ p, float* __restrict__ m, flo
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     g[i] = 0.f;
   }
+}
+
+// Network target, pass 1: m_j = mean of the n_est estimates of voxel j into
+// out; per block, the sum and the count of the positive m_j (part[b],
+// part[gridDim.x + b]).
+__global__ void __launch_bounds__(256)
+k_target_mean(int n, int n_est, const float* __restrict__ est, float* __restrict__ out,
+              double* __restrict__ part) {
+  const float inv = 1.f / (float)n_est;
+  float s = 0.f, c = 0.f;
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
+    float a = 0.f;
+    for (int e = 0; e < n_est; ++e) a += __ldg(est + (size_t)e * n + j);
+    a *= inv;
+    out[j] = a;
+    if (a > 0.f) {
+      s += a;
+      c += 1.f;
+    }
+  }
+  const double ts = block_sum_f(s);
+  const double tc = block_sum_f(c);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = ts;
+    part[gridDim.x + blockIdx.x] = tc;
+  }
+}
+
+// pass 2: every block sums pass 1's nb partials (warp 0), then
+// out_j = log(max(m_j, floor_rel * mean of the positive m))
+__global__ void __launch_bounds__(256)
+k_target_log(int n, int nb, const double* __restrict__ part, float floor_rel,
+             float* __restrict__ out) {
+  __shared__ float fl;
+  if (threadIdx.x < 32) {
+    double s = 0.0, c = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) {
+      s += part[b];
+      c += part[nb + b];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (threadIdx.x == 0) fl = c > 0.0 ? (float)(floor_rel * (s / c)) : floor_rel;
+  }
+  __syncthreads();
+  const float f = fl;
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256)
+    out[j] = logf(fmaxf(out[j], f));
 }
 
 }  // namespace
@@ -693,13 +746,13 @@ cudaError_t launch_wait_selftest(long long limit, int* err, cudaStream_t s) {
 }
 
 cudaError_t launch_mlp_forward(int M, const float* params, const float* cov, const float* c2w,
-                               float* out, int exp_out, bool tc, int* err, int num_sms,
-                               cudaStream_t s) {
+                               float* out, int exp_out, float offset, bool tc, int* err,
+                               int num_sms, cudaStream_t s) {
   const int n = M * M * M;
   if (!tc) {
     const int g = (n + 127) / 128;
     k_mlp_forward_ref<<<g < num_sms * 16 ? g : num_sms * 16, 128, 0, s>>>(M, params, cov, c2w,
-                                                                         out, exp_out);
+                                                                         out, exp_out, offset);
     count_launches(1);
     return cudaGetLastError();
   }
@@ -714,7 +767,8 @@ cudaError_t launch_mlp_forward(int M, const float* params, const float* cov, con
   // eight CTAs per SM: 8 x 64 TMEM columns, the whole tensor memory
   const int tiles = (n + kRows - 1) / kRows;
   const int g = tiles < num_sms * 8 ? tiles : num_sms * 8;
-  k_mlp_forward_tc<<<g, kRows, sizeof(FwdSmem), s>>>(M, params, cov, c2w, out, exp_out, err);
+  k_mlp_forward_tc<<<g, kRows, sizeof(FwdSmem), s>>>(M, params, cov, c2w, out, exp_out, offset,
+                                                     err);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -753,11 +807,22 @@ cudaError_t launch_mlp_grad(int M, int r2, float inv_n, const float* params, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_adam(float* p, float* m, float* v, float* g, int step, float lr, float b1,
-                        float b2, float eps, cudaStream_t s) {
+cudaError_t launch_adam(float* p, float* m, float* v, float* g, float gscale, int step,
+                        float lr, float b1, float b2, float eps, cudaStream_t s) {
   const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
-  k_adam<<<(kNP + 255) / 256, 256, 0, s>>>(kNP, p, m, v, g, lr, b1, b2, eps, c1, c2);
+  k_adam<<<(kNP + 255) / 256, 256, 0, s>>>(kNP, p, m, v, g, gscale, lr, b1, b2, eps, c1, c2);
   count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_target(int M, int n_est, const float* est, float floor_rel,
+                              float* target, double* part, int num_sms, cudaStream_t s) {
+  const int n = M * M * M;
+  int g = (n + 255) / 256;
+  if (g > num_sms * 4) g = num_sms * 4;
+  k_target_mean<<<g, 256, 0, s>>>(n, n_est, est, target, part);
+  k_target_log<<<g, 256, 0, s>>>(n, g, part, floor_rel, target);
+  count_launches(2);
   return cudaGetLastError();
 }
 

@@ -279,8 +279,8 @@ k_exact_diag(Geo G, const float* __restrict__ rot, const float* __restrict__ df,
       const float wc = S.w[c];
       if (wc == 0.0f) continue;
       if (diag) atomicAdd(diag + S.idx[c], scale * c2 * wc * wc);
-      if (cov) atomicAdd(cov + S.idx[c], wc);
-      if (c2w) atomicAdd(c2w + S.idx[c], c2 * wc);
+      if (cov) atomicAdd(cov + S.idx[c], scale * wc);
+      if (c2w) atomicAdd(c2w + S.idx[c], scale * c2 * wc);
     }
   }
 }

@@ -16,7 +16,6 @@ import math
 import numpy as np
 import torch
 
-from . import native as N
 from .ops import Geometry, Handle
 
 # parameter layout of the library: W1[64][3] b1[64] W2[64][64] b2[64] w3[64] b3
@@ -39,10 +38,14 @@ class Sample:
         self.coverage, self.ctf2w, self.target = coverage, ctf2w, target
 
 
-def dataset_features(h: Handle, geom: Geometry, rot, defocus):
-    """(coverage, sum C^2 w) per voxel over the whole dataset (one pass)."""
-    _, cov, c2w = h.exact_diag(geom, rot, defocus, 0.0, 1.0, diag=False, coverage=True,
-                               ctf2w=True)
+def dataset_features(h: Handle, geom: Geometry, rot, defocus, subsample: int = 1):
+    """(coverage, sum C^2 w) per voxel, estimated for the whole dataset of N
+    poses from its first ceil(N / subsample) poses (one pose-only pass over
+    them, scaled by N / their number; subsample = 1: the exact sums)."""
+    N = rot.shape[0]
+    n = -(-N // subsample)
+    _, cov, c2w = h.exact_diag(geom, rot[:n], defocus[:n] if defocus is not None else None,
+                               0.0, N / n, diag=False, coverage=True, ctf2w=True)
     return cov, c2w
 
 
@@ -50,15 +53,13 @@ def hutchinson_target(h: Handle, geom: Geometry, rot, defocus, n_probes=32, n_bl
                       seed=12345, floor=1e-3):
     """log(max(D_hutch, floor * mean)) with D_hutch the Hutchinson estimate of
     diag(sum_i P_i^* C_i^2 P_i) over the dataset (lambda = 0), averaged over
-    n_blocks independent probe blocks of n_probes probes."""
-    acc = None
+    n_blocks independent probe blocks of n_probes probes (cs_mlp_target)."""
+    M = geom.M
+    est = torch.empty((n_blocks, M, M, M), dtype=torch.float32, device=rot.device)
     for blk in range(n_blocks):
-        d = h.hutchinson_diag(geom, rot, defocus, 0.0, 1.0, n_probes=n_probes, seed=seed,
-                              probe_block=blk + 1)
-        acc = d if acc is None else acc + d
-    acc = acc / n_blocks
-    fl = floor * float(acc[acc > 0].mean()) if bool((acc > 0).any()) else floor
-    return torch.log(torch.clamp(acc, min=fl))
+        h.hutchinson_diag(geom, rot, defocus, 0.0, 1.0, n_probes=n_probes, seed=seed,
+                          probe_block=blk + 1, out=est[blk])
+    return h.mlp_target(M, est, floor)
 
 
 class LearnedPreconditioner:
@@ -95,18 +96,17 @@ class LearnedPreconditioner:
                 # each sample's mean squared error, averaged over samples
                 self.h.mlp_grad(s.M, s.r_ball, self.params, s.coverage, s.ctf2w, s.target,
                                 self.grad, self.sse, self.tc)
-            self.grad /= len(samples)
             self.step += 1
-            self.h.mlp_adam_step(self.params, self.m, self.v, self.grad, self.step, lr)
+            self.h.mlp_adam_step(self.params, self.m, self.v, self.grad, self.step, lr,
+                                 grad_scale=1.0 / len(samples))
             hist.append(float(self.sse))
         self.h.check_device_status()
         return hist
 
     def predict(self, M, coverage, ctf2w, lam=0.0):
         """Predicted preconditioner D = exp(network) + lambda, float32 [M][M][M]."""
-        d = self.h.mlp_forward(M, self.params, coverage, ctf2w, exp=True,
-                               tensor_cores=self.tc)
-        return d + lam
+        return self.h.mlp_forward(M, self.params, coverage, ctf2w, exp=True, offset=lam,
+                                  tensor_cores=self.tc)
 
 
 def _ball(M, r, device):

@@ -96,9 +96,11 @@ SIGNATURES = {
     "cs_graph_destroy": (c_int, [P]),
     "cs_set_launch_shape": (c_int, [P, c_int, c_int]),
     "cs_autotune": (c_int, [P, POINTER(CsProblem), c_int, POINTER(c_int), POINTER(c_int)]),
-    "cs_mlp_forward": (c_int, [P, c_int, P, P, P, P, c_int, c_int, P]),
+    "cs_mlp_forward": (c_int, [P, c_int, P, P, P, P, c_int, c_float, c_int, P]),
     "cs_mlp_grad": (c_int, [P, c_int, c_int, P, P, P, P, P, P, c_int, P]),
-    "cs_mlp_adam_step": (c_int, [P, P, P, P, P, c_int, c_float, c_float, c_float, c_float, P]),
+    "cs_mlp_adam_step": (c_int, [P, P, P, P, P, c_float, c_int, c_float, c_float, c_float,
+                                 c_float, P]),
+    "cs_mlp_target": (c_int, [P, c_int, c_int, P, c_float, P, P]),
     "cs_check_device_status": (c_int, [P]),
 }
 

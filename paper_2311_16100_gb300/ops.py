@@ -334,14 +334,25 @@ class Handle:
         return bt.value, bps.value
 
     # ------------------------------------------- learned preconditioner
-    def mlp_forward(self, M, params, coverage, ctf2w, out=None, exp=False, tensor_cores=True,
-                    stream=None):
+    def mlp_forward(self, M, params, coverage, ctf2w, out=None, exp=False, offset=0.0,
+                    tensor_cores=True, stream=None):
         if out is None:
             out = torch.empty((M, M, M), dtype=torch.float32, device=params.device)
         self._check("cs_mlp_forward", self.lib.cs_mlp_forward(
             self.h, M, _ptr(params, torch.float32, "params"),
             _ptr(coverage, torch.float32, "coverage"), _ptr(ctf2w, torch.float32, "ctf2w"),
-            _ptr(out, torch.float32, "out"), int(exp), int(tensor_cores), _stream(stream)))
+            _ptr(out, torch.float32, "out"), int(exp), float(offset), int(tensor_cores),
+            _stream(stream)))
+        return out
+
+    def mlp_target(self, M, estimates, floor_rel=1e-3, out=None, stream=None):
+        """log of the mean of Hutchinson estimates [n_est][M][M][M], floored
+        at floor_rel x the mean of the positive means (cs_mlp_target)."""
+        if out is None:
+            out = torch.empty((M, M, M), dtype=torch.float32, device=estimates.device)
+        self._check("cs_mlp_target", self.lib.cs_mlp_target(
+            self.h, M, int(estimates.shape[0]), _ptr(estimates, torch.float32, "estimates"),
+            float(floor_rel), _ptr(out, torch.float32, "target"), _stream(stream)))
         return out
 
     def mlp_grad(self, M, r_ball, params, coverage, ctf2w, target, grad, sse,
@@ -353,11 +364,11 @@ class Handle:
             _ptr(sse, torch.float64, "sse"), int(tensor_cores), _stream(stream)))
 
     def mlp_adam_step(self, params, m, v, grad, step, lr=1e-2, beta1=0.9, beta2=0.999,
-                      eps=1e-8, stream=None):
+                      eps=1e-8, grad_scale=1.0, stream=None):
         self._check("cs_mlp_adam_step", self.lib.cs_mlp_adam_step(
             self.h, _ptr(params, torch.float32, "params"), _ptr(m, torch.float32, "m"),
-            _ptr(v, torch.float32, "v"), _ptr(grad, torch.float32, "grad"), int(step),
-            float(lr), float(beta1), float(beta2), float(eps), _stream(stream)))
+            _ptr(v, torch.float32, "v"), _ptr(grad, torch.float32, "grad"), float(grad_scale),
+            int(step), float(lr), float(beta1), float(beta2), float(eps), _stream(stream)))
 
     def check_device_status(self):
         self._check("cs_check_device_status", self.lib.cs_check_device_status(self.h))

@@ -97,3 +97,45 @@ def test_adam_step_matches_numpy(h):
     want = p - 0.01 * mh / (np.sqrt(vh) + 1e-8)
     np.testing.assert_allclose(tp.cpu().numpy(), want, rtol=1e-5, atol=1e-6)
     assert float(tg.abs().max()) == 0.0
+
+
+def test_adam_gradient_scale_and_forward_offset(h):
+    """The Adam step on grad_scale * grad equals the step on the scaled
+    gradient; the forward's offset is added after exp (D = exp(net) + lambda)."""
+    d = torch.device("cuda")
+    g = np.random.default_rng(4)
+    p = g.normal(size=4481).astype(np.float32)
+    grad = g.normal(size=4481).astype(np.float32)
+    a, b = torch.from_numpy(p).to(d), torch.from_numpy(p).to(d)
+    ma, va, mb, vb = (torch.zeros_like(a) for _ in range(4))
+    h.mlp_adam_step(a, ma, va, torch.from_numpy(grad).to(d), 1, lr=0.01, grad_scale=0.25)
+    h.mlp_adam_step(b, mb, vb, torch.from_numpy(0.25 * grad).to(d), 1, lr=0.01)
+    np.testing.assert_allclose(a.cpu().numpy(), b.cpu().numpy(), rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(ma.cpu().numpy(), mb.cpu().numpy(), rtol=1e-6, atol=1e-9)
+    M = 16
+    cov, c2w, _, P = inputs(M, 5)
+    args = [torch.from_numpy(x).to(d) for x in (P, cov, c2w)]
+    for tc in (True, False):
+        y = h.mlp_forward(M, *args, tensor_cores=tc)
+        D = h.mlp_forward(M, *args, exp=True, offset=2.5, tensor_cores=tc)
+        np.testing.assert_allclose(D.cpu().numpy(), np.exp(y.cpu().numpy()) + 2.5, rtol=2e-6)
+    from paper_2311_16100_gb300.ops import CryoSGDError
+    with pytest.raises(CryoSGDError):
+        h.mlp_forward(M, *args, offset=float("inf"))
+    with pytest.raises(CryoSGDError):
+        h.mlp_adam_step(a, ma, va, torch.zeros_like(a), 2, grad_scale=0.0)
+
+
+def test_target_is_the_floored_log_mean_of_the_estimates(h):
+    """cs_mlp_target: log(max(mean over estimates, floor x mean of the positive
+    means)), written out in numpy."""
+    d = torch.device("cuda")
+    g = np.random.default_rng(6)
+    M, n_est, floor = 20, 3, 0.05
+    est = g.normal(5.0, 3.0, size=(n_est, M, M, M)).astype(np.float32)
+    est[:, :2] = 0.0                      # some voxels unseen (mean 0)
+    t = h.mlp_target(M, torch.from_numpy(est).to(d), floor).cpu().numpy()
+    m = est.astype(np.float64).mean(axis=0)
+    fl = floor * m[m > 0].mean()
+    np.testing.assert_allclose(t, np.log(np.maximum(m, fl)), rtol=2e-6, atol=2e-6)
+    assert float(t.min()) == pytest.approx(np.log(fl), rel=1e-5)

@@ -178,6 +178,7 @@ def test_exact_diag_and_features(h, interp):
     d, cov, cw = h.exact_diag(c.gpu_geometry(), g["rot"], g["df"], 0.02, 3.0, True, True, True)
     want = O.exact_diag(c.R, c.df, lam=0.02, scale=3.0, **c.geo())
     cov_w, c2_w = O.coverage_features(c.R, c.df, **c.geo())
+    cov_w, c2_w = 3.0 * cov_w, 3.0 * c2_w          # the batch's sums at scale 3
     assert rel_l2(cpu(d), want) <= TOL_GRAD
     assert rel_l2(cpu(cw), c2_w) <= TOL_GRAD
     if interp == "nearest":
