@@ -486,8 +486,17 @@ int cs_mlp_target(cs_handle* h, int M, int n_est, const float* estimates, float 
 int cs_selftest_wait_timeout(cs_handle* h, long long spins, void* stream);
 /* Synchronises the handle's device and reports whether a bounded
  * device-side wait ran out since the last check (CS_ERR_TIMEOUT, and the
- * word is cleared) or not (CS_OK). */
+ * word is cleared) or not (CS_OK).  In the debug variant of the library
+ * (cs_build_flags() & CS_BUILD_DEBUG_BOUNDS) every gather and scatter index
+ * of the traversal kernels is range-checked on the device; an index out of
+ * range skips its access and the next call returns CS_ERR_INTERNAL (the
+ * flags are cleared).  No counterpart in the paper. */
 int cs_check_device_status(cs_handle* h);
+
+/* Build options of the loaded library: CS_BUILD_DEBUG_BOUNDS when it is the
+ * debug variant with device-side index range checks. */
+#define CS_BUILD_DEBUG_BOUNDS 1
+int cs_build_flags(void);
 
 /* In-plane shift operator T_i of Definition 2.1 (a diagonal phase):
  *   images[i][y][x] *= T_i(k)      (sign = +1)

@@ -2,8 +2,10 @@
 
 Each translation unit under csrc/ is compiled in parallel, then linked into
 paper_2311_16100_gb300/libcryosgd.so against the shared CUDA runtime.
-Objects go to paper_2311_16100_gb300/_build/.  Usage:
-    python -m paper_2311_16100_gb300.build [--force]
+Objects go to paper_2311_16100_gb300/_build/; --debug builds the variant
+with device-side index range checks (libcryosgd_debug.so, objects in
+_build_debug/).  Usage:
+    python -m paper_2311_16100_gb300.build [--force] [--debug]
 """
 from __future__ import annotations
 
@@ -17,6 +19,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcryosgd.so")
+# the debug variant: device-side index range checks (-DCS_DEBUG_BOUNDS)
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libcryosgd_debug.so")
 ROOT = os.path.dirname(PKG)
 INCLUDE = os.path.join(ROOT, "include")
 
@@ -49,17 +54,19 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    bdir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    flags = NVCC_FLAGS + (["-DCS_DEBUG_BOUNDS"] if debug else [])
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     hdr = headers()
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdr):
-            jobs.append([cc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj])
+            jobs.append([cc, *ARCH, *flags, "-c", src, "-o", obj])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             for cmd, res in zip(jobs, ex.map(
@@ -68,14 +75,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     sys.stderr.write(res.stdout + res.stderr)
                 if res.returncode != 0:
                     raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    if force or jobs or _stale(LIB, objs):
-        cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs]
+    if force or jobs or _stale(lib, objs):
+        cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", lib, *objs]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             sys.stderr.write(res.stdout + res.stderr)
             raise RuntimeError("link failed: " + " ".join(cmd))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                debug="--debug" in sys.argv))

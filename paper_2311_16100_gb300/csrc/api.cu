@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 #include "tiles.h"
 #include "fused.h"
@@ -91,6 +93,17 @@ int pixel_grid(int num_sms, int B, int M) {
 }
 
 }  // namespace cs
+
+#ifdef CS_DEBUG_BOUNDS
+namespace cs {
+// readers of every translation unit's range-check flag (debug build)
+std::vector<unsigned (*)()>& dbg_readers() {
+  static std::vector<unsigned (*)()> v;
+  return v;
+}
+void dbg_register(unsigned (*reader)()) { dbg_readers().push_back(reader); }
+}  // namespace cs
+#endif
 
 using namespace cs;
 
@@ -258,8 +271,28 @@ inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
   DeviceScope _scope((h)->device);                                    \
   if (_scope.err != cudaSuccess) return cuda_fail((h), _scope.err, "cudaSetDevice")
 
-// Records boundary event `b` (0..CS_NPHASES) of the current timed step.
+// NVTX range of the step phase being enqueued by this thread (a tool such
+// as Nsight Systems shows it; without one attached the calls do nothing)
+thread_local bool t_phase_open = false;
+
+void phase_range(int b) {
+  static const char* const kNames[CS_NPHASES] = {"cs step: precond", "cs step: loss_grad",
+                                                  "cs step: direction", "cs step: curvature",
+                                                  "cs step: update"};
+  if (t_phase_open) {       // the previous phase ends (or a step that returned early)
+    nvtxRangePop();
+    t_phase_open = false;
+  }
+  if (b < CS_NPHASES) {
+    nvtxRangePushA(kNames[b]);
+    t_phase_open = true;
+  }
+}
+
+// Records boundary event `b` (0..CS_NPHASES) of the current step: the NVTX
+// phase range, and the timing event when the profiler is on.
 void prof_mark(cs_handle* h, int b, cudaStream_t s) {
+  phase_range(b);
   if (!h->prof || h->prof_steps >= h->prof_max_steps) return;
   const size_t i = (size_t)h->prof_steps * (CS_NPHASES + 1) + b;
   if (i < h->prof_events.size()) cudaEventRecord(h->prof_events[i], s);
@@ -1526,6 +1559,15 @@ int cs_selftest_wait_timeout(cs_handle* h, long long spins, void* stream) {
 
 int cs_check_device_status(cs_handle* h) {
   if (!h) return CS_ERR_ARG;
+#ifdef CS_DEBUG_BOUNDS
+  {
+    CS_SCOPE(h);
+    CS_CUDA(cudaDeviceSynchronize(), "synchronise");
+    unsigned bad = 0;
+    for (unsigned (*rd)() : dbg_readers()) bad |= rd();
+    if (bad) return fail(h, CS_ERR_INTERNAL, "a device-side index range check failed");
+  }
+#endif
   if (!h->status) return CS_OK;
   CS_SCOPE(h);
   CS_CUDA(cudaDeviceSynchronize(), "synchronise");
@@ -1536,6 +1578,14 @@ int cs_check_device_status(cs_handle* h) {
     return fail(h, CS_ERR_TIMEOUT, "a bounded device-side wait ran out (tensor-core kernel)");
   }
   return CS_OK;
+}
+
+int cs_build_flags(void) {
+#ifdef CS_DEBUG_BOUNDS
+  return CS_BUILD_DEBUG_BOUNDS;
+#else
+  return 0;
+#endif
 }
 
 }  // extern "C"

@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "debug_bounds.cuh"
+
 namespace cs {
 
 // Kernel-side copy of the geometry.  The CTF phase (in units of pi) is

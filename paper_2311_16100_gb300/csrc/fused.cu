@@ -125,7 +125,9 @@ __device__ __forceinline__ float2 gather_cell_pairs_slow(const Geo& G, const Cel
   for (int k = 0; k < 8; ++k) {
     if (!corner_in(G, c, k)) continue;
     const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-    const float4 a = __ldg(vp + ((size_t)(c.z0 + dz) * G.M + (c.y0 + dy)) * G.M + (c.x0 + dx));
+    const size_t j = ((size_t)(c.z0 + dz) * G.M + (c.y0 + dy)) * G.M + (c.x0 + dx);
+    if (!CS_IN(j, (size_t)G.M * G.M * G.M)) continue;
+    const float4 a = __ldg(vp + j);
     const float w = corner_w(c, k);
     re = fmaf(w, a.x, re);
     im = fmaf(w, a.y, im);
@@ -175,7 +177,9 @@ __device__ __forceinline__ float2 gather_pairs_w(const Geo& G, const Cell& c,
   for (int r = 0; r < 4; ++r) {
     const int y = c.y0 + (r & 1), z = c.z0 + (r >> 1);
     if (z >= M || y >= M) continue;
-    const float4 a = __ldg(vp + ((size_t)z * M + y) * M + c.x0);
+    const size_t j = ((size_t)z * M + y) * M + c.x0;
+    if (!CS_IN(j, (size_t)M * M * M)) continue;
+    const float4 a = __ldg(vp + j);
     re = fmaf(w8[2 * r], a.x, fmaf(w8[2 * r + 1], a.z, re));
     im = fmaf(w8[2 * r], a.y, fmaf(w8[2 * r + 1], a.w, im));
   }
@@ -195,7 +199,9 @@ __device__ __forceinline__ void scatter_c2_w(const Geo& G, const Cell& c, float2
     const int y = c.y0 + (r & 1), z = c.z0 + (r >> 1);
     if (z >= M || y >= M) continue;
     const float a0 = w8[2 * r], a1 = w8[2 * r + 1];
-    float4* p = reinterpret_cast<float4*>(base + ((size_t)z * M + y) * M + xb);
+    const size_t j = ((size_t)z * M + y) * M + xb;
+    if (!CS_IN(j + 1, (size_t)M * M * M)) continue;     // the pair (j, j + 1)
+    float4* p = reinterpret_cast<float4*>(base + j);
     atomicAdd(p, make_float4(a0 * val.x, a0 * val.y, a1 * val.x, a1 * val.y));
   }
 }
@@ -211,8 +217,9 @@ __device__ __forceinline__ void scatter_cell_c2(const Geo& G, const Cell& c, flo
       if (!corner_in(G, c, k)) continue;
       const float w = corner_w(c, k);
       const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-      atomicAdd(E + ((size_t)(c.z0 + dz) * M + (c.y0 + dy)) * M + (c.x0 + dx),
-                make_float2(w * val.x, w * val.y));
+      const size_t j = ((size_t)(c.z0 + dz) * M + (c.y0 + dy)) * M + (c.x0 + dx);
+      if (!CS_IN(j, (size_t)M * M * M)) continue;
+      atomicAdd(E + j, make_float2(w * val.x, w * val.y));
     }
     return;
   }
@@ -230,7 +237,9 @@ __device__ __forceinline__ void scatter_cell_c2(const Geo& G, const Cell& c, flo
       if (z >= M || y >= M) continue;
       const float wzy = wz * (dy ? c.ty : 1.f - c.ty);
       const float a0 = wzy * w0x, a1 = wzy * w1x;
-      float4* p = reinterpret_cast<float4*>(base + ((size_t)z * M + y) * M + xb);
+      const size_t j = ((size_t)z * M + y) * M + xb;
+      if (!CS_IN(j + 1, (size_t)M * M * M)) continue;   // the pair (j, j + 1)
+      float4* p = reinterpret_cast<float4*>(base + j);
       atomicAdd(p, make_float4(a0 * val.x, a0 * val.y, a1 * val.x, a1 * val.y));
     }
   }
@@ -248,7 +257,9 @@ __device__ __forceinline__ void scatter_cell_r4(const Geo& G, const Cell& c, con
       if (!corner_in(G, c, k)) continue;
       const int x = c.x0 + (k & 1), y = c.y0 + ((k >> 1) & 1), z = c.z0 + (k >> 2);
       float* buf = P + (size_t)((y & 1) * 2 + (x & 1)) * nb;
-      atomicAdd(buf + 4 * (((size_t)z * Mh + (y >> 1)) * Mh + (x >> 1)), vals[k]);
+      const size_t j = 4 * (((size_t)z * Mh + (y >> 1)) * Mh + (x >> 1));
+      if (!CS_IN(j, nb)) continue;
+      atomicAdd(buf + j, vals[k]);
     }
     return;
   }
@@ -259,7 +270,9 @@ __device__ __forceinline__ void scatter_cell_r4(const Geo& G, const Cell& c, con
   for (int dz = 0; dz < 2; ++dz) {
     const int z = c.z0 + dz;
     if (z >= M) continue;
-    float4* p = reinterpret_cast<float4*>(buf + 4 * (((size_t)z * Mh + Y) * Mh + X));
+    const size_t j = 4 * (((size_t)z * Mh + Y) * Mh + X);
+    if (!CS_IN(j + 3, nb)) continue;                    // the patch j .. j + 3
+    float4* p = reinterpret_cast<float4*>(buf + j);
     atomicAdd(p, make_float4(vals[4 * dz + 0], vals[4 * dz + 1], vals[4 * dz + 2],
                              vals[4 * dz + 3]));
   }
@@ -274,8 +287,9 @@ __device__ __forceinline__ float gather_cell_r(const Geo& G, const Cell& c,
   for (int k = 0; k < 8; ++k) {
     if (!corner_in(G, c, k)) continue;
     const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-    a = fmaf(corner_w(c, k),
-             __ldg(z + ((size_t)(c.z0 + dz) * G.M + (c.y0 + dy)) * G.M + (c.x0 + dx)), a);
+    const size_t j = ((size_t)(c.z0 + dz) * G.M + (c.y0 + dy)) * G.M + (c.x0 + dx);
+    if (!CS_IN(j, (size_t)G.M * G.M * G.M)) continue;
+    a = fmaf(corner_w(c, k), __ldg(z + j), a);
   }
   return a;
 }
@@ -480,6 +494,7 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
       const int it = __ldg(A.slab_items + first + w);
       b = it / nch;
       chc = it - b * nch;
+      if (!CS_IN(b, A.B)) continue;
     } else {
       b = b_next;
       chc = ch;
@@ -496,6 +511,7 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
     if ((FL & (F_SLAB | F_HOLES)) && e < 0) continue;   // holes of the tile-ordered table
     const int ix = e & 0xffff, iy = e >> 16;
     const int kx = ix - G.half, ky = iy - G.half;
+    if (!CS_IN(b, A.B) || !CS_IN(ix, G.M) || !CS_IN(iy, G.M)) continue;
     const Rot R = load_rot(A.rot, b);
     const Cell c = cell_of(G, R, kx, ky);
     float C = 1.f;

@@ -48,10 +48,12 @@ __device__ __forceinline__ float image_ctf(const Geo& G, const float* __restrict
 }
 
 template <int I>
-__device__ __forceinline__ float2 gather(const Stencil& S, const float2* __restrict__ v) {
+__device__ __forceinline__ float2 gather(const Stencil& S, const float2* __restrict__ v,
+                                         int n = 0x7fffffff) {
   float re = 0.f, im = 0.f;
 #pragma unroll
   for (int c = 0; c < (I ? 8 : 1); ++c) {
+    if (!CS_IN(S.idx[c], n)) continue;
     float2 x = __ldg(v + S.idx[c]);
     re = fmaf(S.w[c], x.x, re);
     im = fmaf(S.w[c], x.y, im);
@@ -60,27 +62,31 @@ __device__ __forceinline__ float2 gather(const Stencil& S, const float2* __restr
 }
 
 template <int I>
-__device__ __forceinline__ float gather_real(const Stencil& S, const float* __restrict__ v) {
+__device__ __forceinline__ float gather_real(const Stencil& S, const float* __restrict__ v,
+                                             int n = 0x7fffffff) {
   float a = 0.f;
 #pragma unroll
-  for (int c = 0; c < (I ? 8 : 1); ++c) a = fmaf(S.w[c], __ldg(v + S.idx[c]), a);
+  for (int c = 0; c < (I ? 8 : 1); ++c)
+    if (CS_IN(S.idx[c], n)) a = fmaf(S.w[c], __ldg(v + S.idx[c]), a);
   return a;
 }
 
 template <int I>
-__device__ __forceinline__ void scatter(const Stencil& S, float2 val, float2* v) {
+__device__ __forceinline__ void scatter(const Stencil& S, float2 val, float2* v,
+                                        int n = 0x7fffffff) {
 #pragma unroll
   for (int c = 0; c < (I ? 8 : 1); ++c) {
-    if (S.w[c] != 0.0f)
+    if (S.w[c] != 0.0f && CS_IN(S.idx[c], n))
       atomicAdd(v + S.idx[c], make_float2(S.w[c] * val.x, S.w[c] * val.y));
   }
 }
 
 template <int I>
-__device__ __forceinline__ void scatter_real(const Stencil& S, float val, float* v) {
+__device__ __forceinline__ void scatter_real(const Stencil& S, float val, float* v,
+                                             int n = 0x7fffffff) {
 #pragma unroll
   for (int c = 0; c < (I ? 8 : 1); ++c)
-    if (S.w[c] != 0.0f) atomicAdd(v + S.idx[c], S.w[c] * val);
+    if (S.w[c] != 0.0f && CS_IN(S.idx[c], n)) atomicAdd(v + S.idx[c], S.w[c] * val);
 }
 
 // ------------------------------------------------------------- kernels
@@ -97,7 +103,7 @@ k_slice_project(Geo G, const float2* __restrict__ vol, const float* __restrict__
       Rot R = load_rot(rot, it.b);
       Stencil S;
       make_stencil<I>(G, R, it.kx, it.ky, S);
-      float2 a = gather<I>(S, vol);
+      float2 a = gather<I>(S, vol, G.M * G.M * G.M);
       float C = image_ctf(G, df, it.b, it.q);
       y = make_float2(C * a.x, C * a.y);
     }
@@ -118,7 +124,7 @@ k_backproject(Geo G, const float2* __restrict__ img, const float* __restrict__ r
     Stencil S;
     make_stencil<I>(G, R, it.kx, it.ky, S);
     float sc = scale * image_ctf(G, df, it.b, it.q);
-    scatter<I>(S, make_float2(sc * y.x, sc * y.y), vol);
+    scatter<I>(S, make_float2(sc * y.x, sc * y.y), vol, G.M * G.M * G.M);
   }
 }
 
@@ -150,13 +156,13 @@ k_loss_grad(Geo G, const float2* __restrict__ vol, const float2* __restrict__ im
     Rot R = load_rot(rot, it.b);
     Stencil S;
     make_stencil<I>(G, R, it.kx, it.ky, S);
-    float2 a = gather<I>(S, vol);
+    float2 a = gather<I>(S, vol, G.M * G.M * G.M);
     float2 x = __ldg(img + (size_t)it.b * MM + it.p);
     float C = image_ctf(G, df, it.b, it.q);
     float rr = fmaf(C, a.x, -x.x), ri = fmaf(C, a.y, -x.y);
     acc = fmaf(rr, rr, fmaf(ri, ri, acc));
     float sc = scale * C;
-    scatter<I>(S, make_float2(sc * rr, sc * ri), grad);
+    scatter<I>(S, make_float2(sc * rr, sc * ri), grad, G.M * G.M * G.M);
   }
   double t = block_sum_f(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
@@ -200,9 +206,9 @@ k_hvp(Geo G, const float* __restrict__ z, const float* __restrict__ rot,
     Rot R = load_rot(rot, it.b);
     Stencil S;
     make_stencil<I>(G, R, it.kx, it.ky, S);
-    float a = gather_real<I>(S, z);
+    float a = gather_real<I>(S, z, G.M * G.M * G.M);
     float C = image_ctf(G, df, it.b, it.q);
-    scatter_real<I>(S, scale * C * C * a, Hz);
+    scatter_real<I>(S, scale * C * C * a, Hz, G.M * G.M * G.M);
   }
 }
 
@@ -237,15 +243,16 @@ k_hutchinson(Geo G, const uint32_t* __restrict__ bits, const float* __restrict__
     make_stencil<I>(G, R, it.kx, it.ky, S);
     float C = image_ctf(G, df, it.b, it.q);
     const float sc = scale * C * C;
+    const int nv = G.M * G.M * G.M;
     if (I == 0) {
-      if (S.w[0] != 0.0f) atomicAdd(diag + S.idx[0], sc);
+      if (S.w[0] != 0.0f && CS_IN(S.idx[0], nv)) atomicAdd(diag + S.idx[0], sc);
       continue;
     }
     uint32_t bw[8];
     float wsum = 0.f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      bw[c] = __ldg(bits + S.idx[c]);
+      bw[c] = CS_IN(S.idx[c], nv) ? __ldg(bits + S.idx[c]) : 0u;
       wsum += S.w[c];
     }
 #pragma unroll
@@ -256,7 +263,7 @@ k_hutchinson(Geo G, const uint32_t* __restrict__ bits, const float* __restrict__
       for (int l = 0; l < 8; ++l)
         if (l != j) pc = fmaf(S.w[l], (float)__popc((bw[j] ^ bw[l]) & mask), pc);
       float sj = fmaf(-2.0f * invK, pc, wsum);
-      if (S.w[j] != 0.0f) atomicAdd(diag + S.idx[j], sc * S.w[j] * sj);
+      if (S.w[j] != 0.0f && CS_IN(S.idx[j], nv)) atomicAdd(diag + S.idx[j], sc * S.w[j] * sj);
     }
   }
 }
@@ -277,7 +284,7 @@ k_exact_diag(Geo G, const float* __restrict__ rot, const float* __restrict__ df,
 #pragma unroll
     for (int c = 0; c < (I ? 8 : 1); ++c) {
       const float wc = S.w[c];
-      if (wc == 0.0f) continue;
+      if (wc == 0.0f || !CS_IN(S.idx[c], G.M * G.M * G.M)) continue;
       if (diag) atomicAdd(diag + S.idx[c], scale * c2 * wc * wc);
       if (cov) atomicAdd(cov + S.idx[c], scale * wc);
       if (c2w) atomicAdd(c2w + S.idx[c], scale * c2 * wc);
@@ -297,7 +304,7 @@ k_curvature(Geo G, const float2* __restrict__ d, const float* __restrict__ rot,
     Rot R = load_rot(rot, it.b);
     Stencil S;
     make_stencil<I>(G, R, it.kx, it.ky, S);
-    float2 a = gather<I>(S, d);
+    float2 a = gather<I>(S, d, G.M * G.M * G.M);
     float C = image_ctf(G, df, it.b, it.q);
     acc = fmaf(C * C, fmaf(a.x, a.x, a.y * a.y), acc);
   }

@@ -436,8 +436,9 @@ k_tile(TileArgs A) {
         const int lx = i % kT, ly = (i / kT) % kT, lz = i / (kT * kT);
         const int gx = ax + lx, gy = ay + ly, gz = az + lz;
         const AccT v = acc[i];
-        if (gx < M && gy < M && gz < M && nonzero(v))
-          global_add(dst + ((size_t)gz * M + gy) * M + gx, v);
+        const size_t j = ((size_t)gz * M + gy) * M + gx;
+        if (gx < M && gy < M && gz < M && nonzero(v) && CS_IN(j, (size_t)M * M * M))
+          global_add(dst + j, v);
       }
     }
     if (Tr::kSum) {

@@ -10,7 +10,11 @@ import os
 from ctypes import c_longlong, POINTER, c_char_p, c_double, c_float, c_int, c_size_t, c_uint64, c_void_p
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libcryosgd.so")
+# CS_LIBRARY=debug selects the debug variant (device-side index range
+# checks, reported by cs_check_device_status)
+LIB_PATH = os.path.join(PKG, "libcryosgd_debug.so" if os.environ.get("CS_LIBRARY") == "debug"
+                        else "libcryosgd.so")
+CS_BUILD_DEBUG_BOUNDS = 1
 
 CS_OK, CS_ERR_ARG, CS_ERR_SHAPE, CS_ERR_CUDA, CS_ERR_TIMEOUT, CS_ERR_INTERNAL, CS_ERR_ALLOC = range(7)
 CS_NEAREST, CS_TRILINEAR = 0, 1
@@ -102,6 +106,7 @@ SIGNATURES = {
                                  c_float, P]),
     "cs_mlp_target": (c_int, [P, c_int, c_int, P, c_float, P, P]),
     "cs_check_device_status": (c_int, [P]),
+    "cs_build_flags": (c_int, []),
 }
 
 _lib = None
@@ -114,7 +119,7 @@ def load() -> ctypes.CDLL:
         return _lib
     if not os.path.exists(LIB_PATH):
         raise ImportError(
-            f"libcryosgd.so is not built ({LIB_PATH}); run "
+            f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); run "
             "`python -m paper_2311_16100_gb300.build` (needs nvcc)")
     lib = ctypes.CDLL(LIB_PATH)
     for name, (res, args) in SIGNATURES.items():

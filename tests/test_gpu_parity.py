@@ -32,6 +32,9 @@ def h(request):
         hd.set_algo(request.param)
     hd.algo_name = request.param
     yield hd
+    # reports a bounded wait that ran out and, in the debug variant of the
+    # library, any device-side index range check that failed
+    hd.check_device_status()
     hd.close()
 
 
