@@ -786,6 +786,7 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
                              st->beta, st->scalars, w.fw, st->D, st->D_avg, pD, pV, &nd,
                              h->num_sms, s),
             "step_post launch");
+    CS_CUDA(launch_patches(g->M, w.fw, h->num_sms, s), "patch layout launch");
     nvv = nd;
     prof_mark(h, CS_PH_CURVATURE, s);
     CS_CUDA(launch_fused(F_CURV, G, w.fw, rot, defocus, B, scale, w.d, w.fw.pairs, nullptr,
@@ -1097,6 +1098,7 @@ FusedArgs problem_args(const cs_problem& q, const ProblemWs& w, const Geo& G) {
   A.P = w.fw.P;
   A.K = q.state.n_probes;
   A.vp = w.fw.pairs;
+  A.dq = w.fw.dq;
   A.seed = q.state.seed;
   A.k_dev = q.state.scalars + CS_S_K;
   A.cursor = q.state.scalars + CS_S_K;
@@ -1161,6 +1163,7 @@ int multi_step_enqueue(cs_handle* h, const cs_problem* P, int n, const ProblemWs
                              q.state.D_avg, W[p].part + 2 * kPartRegion, W[p].part + kPartRegion,
                              &nd[p], h->num_sms, s),
             "step_post launch");
+    CS_CUDA(launch_patches(q.geom.M, W[p].fw, h->num_sms, s), "patch layout launch");
     BA[p].img = nullptr;
     BA[p].part = W[p].part + 3 * kPartRegion;   // curvature partials
   }

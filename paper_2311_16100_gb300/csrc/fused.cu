@@ -186,6 +186,57 @@ __device__ __forceinline__ float2 gather_pairs_w(const Geo& G, const Cell& c,
   return make_float2(re, im);
 }
 
+// 32-byte load of one 2 x 2 (x, y) patch of complex values:
+// (re, im) of (x, y), (x+1, y), (x, y+1), (x+1, y+1)
+__device__ __forceinline__ void ld_patch(const float4* __restrict__ p, float (&a)[8]) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=f"(a[0]), "=f"(a[1]), "=f"(a[2]), "=f"(a[3]), "=f"(a[4]), "=f"(a[5]), "=f"(a[6]),
+        "=f"(a[7])
+      : "l"(p));
+}
+
+// gather from the 2 x 2 patch layout with precomputed corner weights
+// (base_in cells): one 32-byte load per z-plane of the cell; weight
+// w8[4 dz + 2 dy + dx] goes with patch element dx + 2 dy
+__device__ __forceinline__ float2 gather_patch_w(const Geo& G, const Cell& c,
+                                                 const float4* __restrict__ dq,
+                                                 const float w8[8]) {
+  const int M = G.M;
+  float re = 0.f, im = 0.f;
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz) {
+    const int z = c.z0 + dz;
+    if (z >= M) continue;
+    const size_t j = ((size_t)z * M + c.y0) * M + c.x0;
+    if (!CS_IN(j, (size_t)M * M * M)) continue;
+    float a[8];
+    ld_patch(dq + 2 * j, a);
+    const float* w = w8 + 4 * dz;
+    re = fmaf(w[0], a[0], fmaf(w[1], a[2], fmaf(w[2], a[4], fmaf(w[3], a[6], re))));
+    im = fmaf(w[0], a[1], fmaf(w[1], a[3], fmaf(w[2], a[5], fmaf(w[3], a[7], im))));
+  }
+  return make_float2(re, im);
+}
+
+// per-corner gather from the patch layout (element 0 of patch j is d[j]);
+// cells whose base corner is outside the grid
+__device__ __forceinline__ float2 gather_cell_patch_slow(const Geo& G, const Cell& c,
+                                                         const float4* __restrict__ dq) {
+  float re = 0.f, im = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (!corner_in(G, c, k)) continue;
+    const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+    const size_t j = ((size_t)(c.z0 + dz) * G.M + (c.y0 + dy)) * G.M + (c.x0 + dx);
+    if (!CS_IN(j, (size_t)G.M * G.M * G.M)) continue;
+    const float4 a = __ldg(dq + 2 * j);
+    const float w = corner_w(c, k);
+    re = fmaf(w, a.x, re);
+    im = fmaf(w, a.y, im);
+  }
+  return make_float2(re, im);
+}
+
 // scatter of val * w8 into E / O (base_in cells), one v4 reduction per row
 __device__ __forceinline__ void scatter_c2_w(const Geo& G, const Cell& c, float2 val,
                                              float2* __restrict__ E, float2* __restrict__ O,
@@ -537,7 +588,7 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
         scatter_cell_c2(G, c, make_float2(sc * r.x, sc * r.y), A.E, A.O);
     }
     if (FL & F_CURV) {
-      const float2 a = inb ? gather_pairs_w(G, c, A.vp, w8) : gather_cell_pairs_slow(G, c, A.vp);
+      const float2 a = inb ? gather_patch_w(G, c, A.dq, w8) : gather_cell_patch_slow(G, c, A.dq);
       acc = fmaf(C * C, fmaf(a.x, a.x, a.y * a.y), acc);
     }
     if (FL & F_HVP) {
@@ -765,7 +816,7 @@ __global__ void __launch_bounds__(256)
 k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float beta,
             const double* __restrict__ sc, float2* __restrict__ E, float2* __restrict__ O,
             float* __restrict__ P, float* __restrict__ D, float* __restrict__ Davg,
-            float4* __restrict__ dp, double* __restrict__ partG, double* __restrict__ partV,
+            float2* __restrict__ dn, double* __restrict__ partG, double* __restrict__ partV,
             int nb) {
   grid_dep_wait();
   const int n = M * M * M, Mh = M / 2;
@@ -813,10 +864,7 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
     g.y = fmaf(lambda, vv.y, g.y);
     const float inv = 1.0f / dh;
     const float2 d = make_float2(g.x * inv, g.y * inv);
-    float2* dp2 = reinterpret_cast<float2*>(dp);
-    dp2[2 * (size_t)j] = d;
-    if (x >= 1) dp2[2 * (size_t)j - 1] = d;
-    if (x == M - 1) dp2[2 * (size_t)j + 1] = make_float2(0.f, 0.f);
+    dn[j] = d;
     aG += fmaf(g.x, g.x, g.y * g.y) * inv;
     aD += fmaf(d.x, d.x, d.y * d.y);
     aV += fmaf(vv.x, vv.x, vv.y * vv.y);
@@ -831,20 +879,43 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
   }
 }
 
-// v -= eta d, with d read from its pair layout; thread q handles voxels
-// q + k n/4, k = 0..3, all loads issued before the stores
+// 2 x 2 (x, y) patch layout of d for the curvature pass: patch j =
+// (d[j], d[j+1], d[j+M], d[j+M+1]), 0 past the grid's edge in x or y; one
+// thread per patch, written as two consecutive 16-byte stores (a warp's
+// stores cover 1 KB contiguously).  Written by k_step_post directly instead
+// (d[j] stored into four patches, 8 bytes each): slower (curvature 0.107 ->
+// 0.115 ms and step 0.616 -> 0.620 ms at 128^3).
 __global__ void __launch_bounds__(256)
-k_update_pairs(int n, float2* __restrict__ v, const float4* __restrict__ dp,
+k_patches(int M, const float2* __restrict__ dn, float4* __restrict__ dq) {
+  grid_dep_wait();
+  const int n = M * M * M;
+  const float2 z2 = make_float2(0.f, 0.f);
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
+    const int x = j % M, y = (j / M) % M;
+    const bool xin = x + 1 < M, yin = y + 1 < M;
+    const float2 a = dn[j];
+    const float2 b = xin ? dn[j + 1] : z2;
+    const float2 c = yin ? dn[j + M] : z2;
+    const float2 d = xin && yin ? dn[j + M + 1] : z2;
+    dq[2 * (size_t)j] = make_float4(a.x, a.y, b.x, b.y);
+    dq[2 * (size_t)j + 1] = make_float4(c.x, c.y, d.x, d.y);
+  }
+}
+
+// v -= eta d; thread q handles voxels q + k n/4, k = 0..3, all loads issued
+// before the stores
+__global__ void __launch_bounds__(256)
+k_update_pairs(int n, float2* __restrict__ v, const float2* __restrict__ dn,
                const double* __restrict__ sc) {
   grid_dep_wait();
   const float eta = (float)sc[CS_S_ETA];
   const int n4 = n / 4;
   for (int q = blockIdx.x * 256 + threadIdx.x; q < n4; q += gridDim.x * 256) {
-    float4 d[4];
+    float2 d[4];
     float2 a[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      d[k] = dp[q + k * n4];
+      d[k] = dn[q + k * n4];
       a[k] = v[q + k * n4];
     }
 #pragma unroll
@@ -890,9 +961,11 @@ void slab_carve(void* region, int M, int B, FusedWs& w) {
 
 size_t fused_ws_bytes(int M) {
   const size_t n = (size_t)M * M * M;
-  // E, O (complex), P (4 real buffers), pair layout, disc table, count
+  // E, O (complex), P (4 real buffers), pair layout, d, d's patches, disc
+  // table, count
   return 2 * n * sizeof(float2) + 4 * n * sizeof(float) + n * sizeof(float4) +
-         table_entries(M) * sizeof(int) + tile_slots(M) * sizeof(int) + 256;
+         n * sizeof(float2) + 2 * n * sizeof(float4) + table_entries(M) * sizeof(int) +
+         tile_slots(M) * sizeof(int) + 256;
 }
 
 FusedWs fused_carve(void* base, int M) {
@@ -903,6 +976,8 @@ FusedWs fused_carve(void* base, int M) {
   w.O = reinterpret_cast<float2*>(p);   p += n * sizeof(float2);
   w.P = reinterpret_cast<float*>(p);    p += 4 * n * sizeof(float);
   w.pairs = reinterpret_cast<float4*>(p); p += n * sizeof(float4);
+  w.dq = reinterpret_cast<float4*>(p);  p += 2 * n * sizeof(float4);
+  w.dn = reinterpret_cast<float2*>(p);  p += n * sizeof(float2);
   w.table = reinterpret_cast<int*>(p);  p += table_entries(M) * sizeof(int);
   w.tile_org = reinterpret_cast<int*>(p); p += tile_slots(M) * sizeof(int);
   w.n_px = reinterpret_cast<int*>(p);
@@ -1003,6 +1078,7 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
   A.P = w.P;
   A.K = K;
   A.vp = vp;
+  A.dq = w.dq;
   A.seed = seed;
   A.block_host = block_host;
   A.k_dev = k_dev;
@@ -1074,7 +1150,8 @@ cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid
 }
 
 // The passes with reductions touch 48 bytes per voxel at random (pair layout
-// of v, E/O, the four patch buffers), the curvature pass 16 (pair layout).
+// of v, E/O, the four patch buffers), the curvature pass 32 (the 2 x 2
+// patch layout of d).
 // About one launch per ~134 MB (128 MB for the curvature) of that footprint.
 // Measured at 256^3, batch 1024 (tiles owned by the slab of their centre):
 // the loss-gradient pass takes 1.98 / 1.96 / 1.96 / 1.98 / 2.01 / 2.06 ms
@@ -1083,7 +1160,7 @@ cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid
 // takes 0.87 / 0.77 / 0.78 ms with 1 / 2 / 3 slabs; at 128^3 one is best.
 int slab_count(int M, int flags) {
   const double vox = (double)M * M * M;
-  const double ratio = flags == F_CURV ? 16.0 * vox / 128e6 : 48.0 * vox / 134e6;
+  const double ratio = flags == F_CURV ? 32.0 * vox / 128e6 : 48.0 * vox / 134e6;
   // passes with reductions: 2 slabs from 1.25 x the footprint on (measured
   // at 160^3: loss-gradient pass 0.87 -> 0.77 ms)
   long S = flags == F_CURV ? lround(ratio) : (ratio >= 1.25 ? lround(ratio + 0.25) : 1);
@@ -1120,7 +1197,14 @@ cudaError_t launch_step_post(int M, int mode, const float2* v, float lambda, flo
   const int g = elem_grid(M * M * M, num_sms);
   *nb = g;
   const cudaError_t e = launch_pdl(k_step_post, g, 256, s, M, mode, v, lambda, beta, scalars,
-                                   w.E, w.O, w.P, D, Davg, w.pairs, partG, partV, g);
+                                   w.E, w.O, w.P, D, Davg, w.dn, partG, partV, g);
+  count_launches(1);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_patches(int M, const FusedWs& w, int num_sms, cudaStream_t s) {
+  const cudaError_t e =
+      launch_pdl(k_patches, elem_grid(M * M * M, num_sms), 256, s, M, w.dn, w.dq);
   count_launches(1);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -1129,10 +1213,11 @@ cudaError_t launch_update_pairs(int M, float2* v, const FusedWs& w, const double
                                 int num_sms, cudaStream_t s) {
   const int n = M * M * M;
   const cudaError_t e =
-      launch_pdl(k_update_pairs, elem_grid(n / 4, num_sms), 256, s, n, v, w.pairs, scalars);
+      launch_pdl(k_update_pairs, elem_grid(n / 4, num_sms), 256, s, n, v, w.dn, scalars);
   count_launches(1);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
+
 
 cudaError_t launch_step_prep(int M, const float2* v, const FusedWs& w, bool zero_p, int num_sms,
                              cudaStream_t s) {

@@ -10,6 +10,9 @@ struct FusedWs {
   float2* O;      // complex accumulator shifted by one voxel along x [M^3]
   float* P;       // four real 2x2-patch accumulators [4][M^3]
   float4* pairs;  // pair layout (v[j], v[j+1]) of the gathered volume [M^3]
+  float2* dn;     // search direction d of a step, natural layout [M^3]
+  float4* dq;     // d as 2 x 2 (x, y) patches, 32 bytes per voxel [2 M^3]:
+                  // (d[j], d[j+1], d[j+M], d[j+M+1]), 0 past the grid's edge
   int* table;     // disc pixel table (row order, or tile order: see fused.cu)
   int* tile_org;  // tile order: origin of each table chunk
   int* n_px;      // number of table entries
