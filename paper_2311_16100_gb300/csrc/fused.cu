@@ -237,10 +237,26 @@ __device__ __forceinline__ float2 gather_cell_patch_slow(const Geo& G, const Cel
   return make_float2(re, im);
 }
 
+// L2 policy that keeps lines (the accumulators) in L2 ahead of others, and
+// a 16-byte reduction / store under it
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void red_add_keep(float4* p, float4 v, uint64_t pol) {
+  asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+               :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep(float4* p, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+               :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
+}
+
 // scatter of val * w8 into E / O (base_in cells), one v4 reduction per row
 __device__ __forceinline__ void scatter_c2_w(const Geo& G, const Cell& c, float2 val,
                                              float2* __restrict__ E, float2* __restrict__ O,
-                                             const float w8[8]) {
+                                             const float w8[8], uint64_t pol) {
   const int M = G.M;
   const bool odd = c.x0 & 1;
   float2* base = odd ? O : E;
@@ -253,7 +269,7 @@ __device__ __forceinline__ void scatter_c2_w(const Geo& G, const Cell& c, float2
     const size_t j = ((size_t)z * M + y) * M + xb;
     if (!CS_IN(j + 1, (size_t)M * M * M)) continue;     // the pair (j, j + 1)
     float4* p = reinterpret_cast<float4*>(base + j);
-    atomicAdd(p, make_float4(a0 * val.x, a0 * val.y, a1 * val.x, a1 * val.y));
+    red_add_keep(p, make_float4(a0 * val.x, a0 * val.y, a1 * val.x, a1 * val.y), pol);
   }
 }
 
@@ -299,7 +315,7 @@ __device__ __forceinline__ void scatter_cell_c2(const Geo& G, const Cell& c, flo
 // adds per-corner real values to the 2x2 (x, y) patch buffers, one v4
 // reduction per z-plane.  vals[k] for corner k = dx + 2 dy + 4 dz.
 __device__ __forceinline__ void scatter_cell_r4(const Geo& G, const Cell& c, const float* vals,
-                                                float* __restrict__ P) {
+                                                float* __restrict__ P, uint64_t pol) {
   const int M = G.M, Mh = G.M / 2;
   const size_t nb = (size_t)M * M * M;
   if (!base_in(G, c)) {
@@ -324,8 +340,8 @@ __device__ __forceinline__ void scatter_cell_r4(const Geo& G, const Cell& c, con
     const size_t j = 4 * (((size_t)z * Mh + Y) * Mh + X);
     if (!CS_IN(j + 3, nb)) continue;                    // the patch j .. j + 3
     float4* p = reinterpret_cast<float4*>(buf + j);
-    atomicAdd(p, make_float4(vals[4 * dz + 0], vals[4 * dz + 1], vals[4 * dz + 2],
-                             vals[4 * dz + 3]));
+    red_add_keep(p, make_float4(vals[4 * dz + 0], vals[4 * dz + 1], vals[4 * dz + 2],
+                                vals[4 * dz + 3]), pol);
   }
 }
 
@@ -532,6 +548,8 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
     step_z = (uint64_t)G.M * G.M / 2 * kSplitMixGamma;       // next plane: M^2/2
   }
   float acc = 0.f;
+  // the accumulators stay in L2 ahead of the streamed images
+  const uint64_t pol = l2_keep_policy();
   // item w = (image b, chunk ch) = (w / nch, w % nch), advanced by nblk
   // items per iteration without a division
   // F_SLAB: this slab's items from its list; otherwise every item in order
@@ -583,7 +601,7 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
       }
       const float sc = A.scale * C;
       if (inb)
-        scatter_c2_w(G, c, make_float2(sc * r.x, sc * r.y), A.E, A.O, w8);
+        scatter_c2_w(G, c, make_float2(sc * r.x, sc * r.y), A.E, A.O, w8, pol);
       else
         scatter_cell_c2(G, c, make_float2(sc * r.x, sc * r.y), A.E, A.O);
     }
@@ -596,7 +614,7 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
       float vals[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) vals[k] = corner_in(G, c, k) ? corner_w(c, k) * y : 0.f;
-      scatter_cell_r4(G, c, vals, A.P);
+      scatter_cell_r4(G, c, vals, A.P, pol);
     }
     if (FL & F_HUTCH) {
       uint32_t bw[8];
@@ -661,7 +679,7 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
       float vals[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) vals[j] = sc * w8[j] * fmaf(-2.0f * invK, S[j], wsum);
-      scatter_cell_r4(G, c, vals, A.P);
+      scatter_cell_r4(G, c, vals, A.P, pol);
     }
   }
   return acc;
@@ -734,14 +752,15 @@ k_step_prep(int M, const float2* __restrict__ v, float2* __restrict__ E, float2*
   float4* E4 = reinterpret_cast<float4*>(E);
   float4* O4 = reinterpret_cast<float4*>(O);
   float4* P4 = reinterpret_cast<float4*>(P);
+  const uint64_t pol = l2_keep_policy();     // the accumulators stay in L2
   for (int q = blockIdx.x * 256 + threadIdx.x; q < n4; q += gridDim.x * 256) {
-    E4[q] = z4;
-    E4[q + n4] = z4;
-    O4[q] = z4;
-    O4[q + n4] = z4;
+    st_keep(E4 + q, z4, pol);
+    st_keep(E4 + q + n4, z4, pol);
+    st_keep(O4 + q, z4, pol);
+    st_keep(O4 + q + n4, z4, pol);
     if (zero_p) {
 #pragma unroll
-      for (int b = 0; b < 4; ++b) P4[q + b * n4] = z4;
+      for (int b = 0; b < 4; ++b) st_keep(P4 + q + b * n4, z4, pol);
     }
     float2 a[4], c[4];
 #pragma unroll

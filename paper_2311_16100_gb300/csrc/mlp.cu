@@ -8,13 +8,16 @@
 //    (thread t owns voxel row t = TMEM lane t).  The 64 x 64 layer
 //    H1 W2^T and the input gradient dA2 W2 are tcgen05.mma kind::f16
 //    (BF16 operands in shared memory, FP32 accumulators in tensor memory,
-//    M = 128, N = 64, K = 64); the weight gradient dA2^T H1 is read from the
-//    Gram matrix X X^T of X = [dA2 | H1]^T (M = N = 128, K = 128 voxels),
-//    accumulated in tensor memory over all tiles of the CTA.  The 3 -> 64
-//    and 64 -> 1 layers and the bias / small-layer gradients run on the FP32
-//    pipes.  Operands use the K-major, no-swizzle canonical layout: 8-row x
-//    16-byte core matrices, LBO = next core matrix along K, SBO = next
-//    8-row group.
+//    M = 128, N = 64, K = 64).  In the gradient kernel each voxel's row
+//    [bf(dA2) | bf(H1)] (128 features) is one row of a shared buffer; the
+//    weight gradient dA2^T H1 comes from the same buffer read as
+//    MN-major operands (M = 128 features, N = the 64 H1 features, K = 128
+//    voxels: rows 0..63 of the product), accumulated in tensor memory over
+//    all tiles of the CTA.  The 3 -> 64 and 64 -> 1 layers and the bias /
+//    small-layer gradients run on the FP32 pipes.  Operands use the
+//    no-swizzle canonical layouts: 8-row x 16-byte core matrices; K-major:
+//    LBO = next core matrix along K, SBO = next 8-row group; MN-major:
+//    LBO = next 8 rows along K, SBO = next core matrix along M (or N).
 //  * FP32 reference (any GPU): the same arithmetic (same BF16 rounding
 //    points) with plain FMAs, used to cross-check the tensor-core kernels.
 #include <cuda_bf16.h>
@@ -96,9 +99,10 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
 }
 
 // kind::f16 instruction descriptor: BF16 A and B, FP32 D, K-major A and B
-__host__ __device__ constexpr uint32_t umma_idesc(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(m >> 4) << 24);
+// (mn_major: both MN-major instead)
+__host__ __device__ constexpr uint32_t umma_idesc(int m, int n, bool mn_major = false) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (mn_major ? (3u << 15) : 0u) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
@@ -156,6 +160,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 8 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // byte offset of element (row, k) in a K-major canonical tile with K extent
 // kext (LBO = 128 bytes, SBO = kext/8 * 128 bytes)
 __device__ __forceinline__ uint32_t core_off(int row, int k, int kext) {
@@ -204,19 +221,24 @@ struct FwdSmem {
   uint32_t tmem;
 };
 
+constexpr int kFeat = 2 * kHid;        // a voxel's row of the gradient kernel: dA2 | H1
 struct GradSmem {
+  // [voxel][feature], K-major with K extent 128: features 0..63 = bf(dA2)
+  // (A of the backward MMA), 64..127 = bf(H1) (A of the forward MMA); read
+  // as MN-major operands by the weight-gradient MMA
+  unsigned short XV[kRows * kFeat];
   unsigned short W2[kHid * kHid];       // forward B: rows o, K = i
   unsigned short W2T[kHid * kHid];      // backward B: rows i, K = o
-  unsigned short H1[kRows * kHid];      // forward A: rows = voxels, K = i
-  unsigned short DA[kRows * kHid];      // backward A: rows = voxels, K = o
-  unsigned short XT[128 * kRows];       // Gram operand: rows = features (dA2 | H1), K = voxels
   float4 L1[kHid];                      // (W1[i][0..2], b1[i])
   float2 L2[kHid];                      // (b2[o], w3[o])
-  float W1[192], b1[64], b2[64], w3[64], b3;
+  float b3;
   float small[kSmall];                  // dW1, db1, db2, dw3, db3 of this CTA
   unsigned long long bar;
   uint32_t tmem;
 };
+
+// Dynamic shared memory of the gradient kernel (four CTAs fit on an SM).
+constexpr size_t kGradSmemBytes = sizeof(GradSmem);
 
 __device__ __forceinline__ void load_params(const float* __restrict__ p, float* W1, float* b1,
                                             float* b2, float* w3, float* b3) {
@@ -325,7 +347,12 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
 
 // Gradient of L = (1/n_ball) sum_{|k| <= r} (y_j - target_j)^2 (accumulated
 // into grad with atomics), and the sum of squared residuals into *sse.
-__global__ void __launch_bounds__(kRows)
+// 128 TMEM columns per CTA (the layer-2 accumulator, reused for the
+// backward product, and the weight gradient) and at most 128 registers per
+// thread: four CTAs per SM (gradient 0.72 -> 0.63 ms at 128^3 against the
+// earlier build with a separate transposed Gram operand, 256 columns and
+// two CTAs per SM).
+__global__ void __launch_bounds__(kRows, 4)
 k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
               const float* __restrict__ cov, const float* __restrict__ c2w,
               const float* __restrict__ target, float* __restrict__ grad, double* __restrict__ sse,
@@ -335,12 +362,12 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int n = M * M * M;
   const int n_tiles = (n + kRows - 1) / kRows;
-  load_params(params, S.W1, S.b1, S.b2, S.w3, &S.b3);
   for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
     S.L1[i] = make_float4(params[oW1 + 3 * i], params[oW1 + 3 * i + 1], params[oW1 + 3 * i + 2],
                           params[ob1 + i]);
     S.L2[i] = make_float2(params[ob2 + i], params[ow3 + i]);
   }
+  if (t == 0) S.b3 = params[ob3];
   for (int e = t; e < kHid * kHid; e += kRows) {
     const int o = e / kHid, i = e % kHid;
     const unsigned short w = bf16bits(params[oW2 + e]);
@@ -352,7 +379,7 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
   for (int i = t; i < kSmall; i += kRows) S.small[i] = 0.f;
   if (t == 0) bar_init(smem_u32(&S.bar));
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;"
                  :: "r"(smem_u32(&S.tmem)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
@@ -361,43 +388,41 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
   fence_after();
   const uint32_t tmem = S.tmem;
   const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-  const uint32_t d1 = tmem, d2 = tmem + 64, d3 = tmem + 128;   // TMEM columns
+  // columns 0..63: layer-2 pre-activation, then the backward product dA2 W2;
+  // columns 64..127: the weight gradient (rows 0..63 of its product)
+  const uint32_t d1 = tmem, d3 = tmem + 64;
   const uint32_t bar = smem_u32(&S.bar);
-  const uint32_t idesc64 = umma_idesc(128, 64), idesc128 = umma_idesc(128, 128);
+  const uint32_t idesc64 = umma_idesc(128, 64), idesc_w = umma_idesc(128, 64, true);
   uint32_t phase = 0;
   bool ok = true;
   int tiles_done = 0;
   double my_sse = 0.0;
-  unsigned char* H1b = reinterpret_cast<unsigned char*>(S.H1);
-  unsigned char* DAb = reinterpret_cast<unsigned char*>(S.DA);
-  unsigned char* XTb = reinterpret_cast<unsigned char*>(S.XT);
+  unsigned char* XVb = reinterpret_cast<unsigned char*>(S.XV);
   for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
     const int j = tile * kRows + t;
     float x[3] = {0.f, 0.f, 0.f};
     bool inb = false;
     if (j < n) features(j, M, cov, c2w, x, r2, inb);
-    // ---- forward, layer 1 -> smem (A of the forward MMA, rows 64.. of X^T)
+    // ---- forward, layer 1 -> features 64..127 of this voxel's row
 #pragma unroll 2
     for (int i0 = 0; i0 < kHid; i0 += 8) {
       float h[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int i = i0 + u;
-        const float4 q = S.L1[i];
+        const float4 q = S.L1[i0 + u];
         h[u] = gelu_f(fmaf(q.z, x[2], fmaf(q.y, x[1], fmaf(q.x, x[0], q.w))));
-        *reinterpret_cast<unsigned short*>(XTb + core_off(64 + i, t, kRows)) = bf16bits(h[u]);
       }
-      st_bf16x8(H1b, core_off(t, i0, kHid), h);
+      st_bf16x8(XVb, core_off(t, kHid + i0, kFeat), h);
     }
     fence_async_smem();
     fence_before();
     __syncthreads();
     if (t == 0) {
       fence_after();
-      const uint32_t aB = smem_u32(S.H1), bB = smem_u32(S.W2);
+      const uint32_t aB = smem_u32(S.XV) + core_off(0, kHid, kFeat), bB = smem_u32(S.W2);
 #pragma unroll
       for (int kc = 0; kc < kHid / 16; ++kc)
-        mma_bf16(d1, umma_desc(aB + 256 * kc, 128, 1024), umma_desc(bB + 256 * kc, 128, 1024),
+        mma_bf16(d1, umma_desc(aB + 256 * kc, 128, 2048), umma_desc(bB + 256 * kc, 128, 1024),
                  idesc64, kc > 0);
       mma_commit(bar);
     }
@@ -405,34 +430,38 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
     phase ^= 1u;
     fence_after();
     if (!ok) break;
-    // ---- forward, layers 2-3, loss, backward through layer 3
+    // ---- forward, layers 2-3, loss, backward through layer 3 (the
+    // pre-activation is read from tensor memory twice instead of being held
+    // in 64 registers: 86 registers, no spills, gradient 0.631 -> 0.620 ms)
     float y = S.b3;
-    float a2[kHid];
 #pragma unroll
-    for (int c = 0; c < kHid; c += 16) tmem_ld16(d1 + lane_off + c, a2 + c);
+    for (int c = 0; c < kHid; c += 16) {
+      float a2[16];
+      tmem_ld16(d1 + lane_off + c, a2);
 #pragma unroll
-    for (int o = 0; o < kHid; ++o) {
-      const float2 q = S.L2[o];
-      a2[o] += q.x;
-      y = fmaf(q.y, gelu_f(a2[o]), y);
+      for (int u = 0; u < 16; ++u) {
+        const float2 q = S.L2[c + u];
+        y = fmaf(q.y, gelu_f(a2[u] + q.x), y);
+      }
     }
     const float r = inb ? y - __ldg(target + j) : 0.f;
     my_sse += (double)r * r;
     const float dy = 2.f * r * inv_n;
     float acc_db3 = dy;
-    // dA2 -> smem (A of the backward MMA, rows 0..63 of X^T); dw3, db2
+    // dA2 -> features 0..63 of this voxel's row; dw3, db2
 #pragma unroll
     for (int c = 0; c < kHid; c += 16) {
-      float v[32], dab[8];
+      float v[32], dab[8], a2[16];
+      tmem_ld16(d1 + lane_off + c, a2);
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const int o = c + u;
-        const float sg = gelu_sig(a2[o]);        // one tanh for GELU and GELU'
-        const float h2 = a2[o] * sg;
-        const float da = dy * S.L2[o].y * gelu_grad_s(a2[o], sg);
+        const float a = a2[u] + S.L2[o].x;
+        const float sg = gelu_sig(a);             // one tanh for GELU and GELU'
+        const float h2 = a * sg;
+        const float da = dy * S.L2[o].y * gelu_grad_s(a, sg);
         dab[u & 7] = da;
-        *reinterpret_cast<unsigned short*>(XTb + core_off(o, t, kRows)) = bf16bits(da);
-        if ((u & 7) == 7) st_bf16x8(DAb, core_off(t, o - 7, kHid), dab);
+        if ((u & 7) == 7) st_bf16x8(XVb, core_off(t, o - 7, kFeat), dab);
         v[u] = dy * h2;          // dw3[o]
         v[16 + u] = da;          // db2[o]
       }
@@ -448,15 +477,22 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
     __syncthreads();
     if (t == 0) {
       fence_after();
-      const uint32_t aB = smem_u32(S.DA), bB = smem_u32(S.W2T), xB = smem_u32(S.XT);
+      const uint32_t xB = smem_u32(S.XV), bB = smem_u32(S.W2T);
+      // dH1 = bf(dA2) W2 into columns 0..63 (layer 2's pre-activation has
+      // been read by every thread)
 #pragma unroll
       for (int kc = 0; kc < kHid / 16; ++kc)
-        mma_bf16(d2, umma_desc(aB + 256 * kc, 128, 1024), umma_desc(bB + 256 * kc, 128, 1024),
+        mma_bf16(d1, umma_desc(xB + 256 * kc, 128, 2048), umma_desc(bB + 256 * kc, 128, 1024),
                  idesc64, kc > 0);
+      // weight gradient: rows = the 128 features of the tile's rows, columns =
+      // the H1 features 64..127, K = voxels; MN-major without swizzling: 8
+      // features per 16-byte core row, next 8 voxels (LBO) 2048 bytes on,
+      // next 8 features (SBO) 128 bytes on
 #pragma unroll
       for (int kc = 0; kc < kRows / 16; ++kc)
-        mma_bf16(d3, umma_desc(xB + 256 * kc, 128, 2048), umma_desc(xB + 256 * kc, 128, 2048),
-                 idesc128, (tiles_done > 0 || kc > 0) ? 1u : 0u);
+        mma_bf16(d3, umma_desc(xB + 4096 * kc, 2048, 128),
+                 umma_desc(xB + core_off(0, kHid, kFeat) + 4096 * kc, 2048, 128), idesc_w,
+                 (tiles_done > 0 || kc > 0) ? 1u : 0u);
       mma_commit(bar);
     }
     ok = __syncthreads_and(bar_wait(bar, phase)) != 0;
@@ -466,15 +502,14 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
     ++tiles_done;
     // ---- backward through layer 1: dA1 = dH1 * gelu'(A1); dW1, db1
 #pragma unroll
-    for (int c = 0; c < kHid; c += 16) {
-      float dh[16];
-      tmem_ld16(d2 + lane_off + c, dh);
+    for (int c = 0; c < kHid; c += 8) {
+      float dh[8];
+      tmem_ld8(d1 + lane_off + c, dh);
       // v[4u + f] = dA1 x_f (f < 3) and dA1 (f = 3) of unit c + u
-      float v[64];
+      float v[32];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int i = c + u;
-        const float4 q = S.L1[i];
+      for (int u = 0; u < 8; ++u) {
+        const float4 q = S.L1[c + u];
         const float a = fmaf(q.z, x[2], fmaf(q.y, x[1], fmaf(q.x, x[0], q.w)));
         const float da1 = dh[u] * gelu_grad_f(a);
         v[4 * u] = da1 * x[0];
@@ -483,11 +518,10 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
         v[4 * u + 3] = da1;
       }
       warp_reduce_scatter(v, lane);
-      // lane l holds elements 2l and 2l+1: unit c + l/2, quantities f = 2(l%2), 2(l%2)+1
+      // lane l holds element l: unit c + l/4, quantity l%4 (x0, x1, x2, bias)
       {
-        const int i = c + (lane >> 1), f = 2 * (lane & 1);
-        atomicAdd(&S.small[3 * i + f], v[0]);
-        atomicAdd(f == 0 ? &S.small[3 * i + 1] : &S.small[192 + i], v[1]);
+        const int i = c + (lane >> 2), f = lane & 3;
+        atomicAdd(f < 3 ? &S.small[3 * i + f] : &S.small[192 + i], v[0]);
       }
     }
     fence_before();
@@ -497,12 +531,13 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
   fence_before();
   __syncthreads();
   fence_after();
-  // dW2 = rows 0..63 (dA2 features), columns 64..127 (H1 features) of the Gram
+  // dW2[o][i] = row o (lanes 0..63: warps 0 and 1), column i of the weight
+  // gradient's accumulator
   if (ok && tiles_done > 0 && t < 64) {
 #pragma unroll
     for (int c = 0; c < kHid; c += 16) {
       float gv[16];
-      tmem_ld16(d3 + lane_off + 64 + c, gv);
+      tmem_ld16(d3 + lane_off + c, gv);
 #pragma unroll
       for (int u = 0; u < 16; ++u) atomicAdd(grad + oW2 + t * kHid + c + u, gv[u]);
     }
@@ -524,7 +559,7 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
   __syncthreads();
   if (warp == 0) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" :: "r"(tmem));
   }
 }
 
@@ -722,7 +757,7 @@ k_target_log(int n, int nb, const double* __restrict__ part, float floor_rel,
 }  // namespace
 
 size_t mlp_fwd_smem() { return sizeof(FwdSmem); }
-size_t mlp_grad_smem() { return sizeof(GradSmem); }
+size_t mlp_grad_smem() { return kGradSmemBytes; }
 
 namespace {
 
@@ -795,14 +830,14 @@ cudaError_t launch_mlp_grad(int M, int r2, float inv_n, const float* params, con
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(GradSmem));
+                                         (int)kGradSmemBytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  // two CTAs per SM: 2 x 256 TMEM columns, the whole tensor memory
-  const int g = tiles < num_sms * 2 ? tiles : num_sms * 2;
-  k_mlp_grad_tc<<<g, kRows, sizeof(GradSmem), s>>>(M, r2, inv_n, params, cov, c2w, target, grad,
-                                                   sse, err);
+  // four CTAs per SM: 4 x 128 TMEM columns, the whole tensor memory
+  const int g = tiles < num_sms * 4 ? tiles : num_sms * 4;
+  k_mlp_grad_tc<<<g, kRows, kGradSmemBytes, s>>>(M, r2, inv_n, params, cov, c2w, target, grad,
+                                                 sse, err);
   count_launches(1);
   return cudaGetLastError();
 }
