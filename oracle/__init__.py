@@ -42,6 +42,9 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
                        weights of a pixel sum to 1 (sum = B n_px) and the
                        CTF^2 sum equals sum_i sum_p C_ip^2
   cg_solve             pinned: closed form under nearest interpolation
+  lbfgs_solve          pinned: closed form under nearest interpolation, the
+                       CG solution under trilinear interpolation with CTF, and
+                       the quadratic's first-order condition H v = b
   diagnostics.fsc      pinned: Eq. fsc identities (1, -1, cos theta, shell
                        locality, energy partition), independent noise ~ 0
   diagnostics.shell_minmax / shell_index
@@ -64,8 +67,8 @@ from .geometry import (ball_mask, ctf_of_s2, ctf_pixels, default_r_max, disc_mas
 from .operators import (backproject_adjoint, coverage_features, dense_hessian,
                         exact_diag, hvp, loss, loss_grad, slice_project)
 from .hutchinson import hutchinson_diag, probe_words, rademacher_probes, splitmix64
-from .sgd import (alg1_step, alpha_threshold, cg_solve, full_rhs, precomputed_preconditioner,
-                  rel_err, shell_counts)
+from .sgd import (alg1_step, alpha_threshold, cg_solve, full_rhs, lbfgs_solve,
+                  precomputed_preconditioner, rel_err, shell_counts)
 from . import diagnostics, mlp
 
 __all__ = [n for n in dir() if not n.startswith("_")]

@@ -144,6 +144,61 @@ def cg_solve(b, R, defocus, M, r_max, interp, ctf, lam, tol=1e-12, max_iter=2000
     return x, it
 
 
+def lbfgs_solve(b, R, defocus, M, r_max, interp, ctf, lam, memory=10, max_iter=1000,
+                tol=1e-12):
+    """v* minimising Eq. (optim cp), f(v) = 1/2 <v, H v> - <b, v> + const, by
+    L-BFGS (Liu & Nocedal 1989), the paper's ground-truth solver (Section 4,
+    1000 iterations there).
+
+    The search direction comes from the two-loop recursion over the last
+    ``memory`` pairs s = v_{k+1} - v_k, y = g_{k+1} - g_k, with the initial
+    scaling gamma = <s, y> / <y, y>; since f is quadratic the step length is
+    the exact minimiser along the direction, t = -<g, p> / <p, H p>.  Complex
+    volumes are real vectors of twice the length (H acts alike on the real
+    and imaginary parts).  Stops when |g| <= tol |b| or after max_iter
+    iterations.  Returns (v, iterations)."""
+    def Hmul(x):
+        return (hvp(x.real, R, defocus, M, r_max, interp, ctf, lam, 1.0)
+                + 1j * hvp(x.imag, R, defocus, M, r_max, interp, ctf, lam, 1.0))
+
+    def dot(a, c):
+        return float(np.vdot(a, c).real)
+
+    b = np.asarray(b, dtype=np.complex128)
+    v = np.zeros_like(b)
+    g = -b                                  # gradient H v - b at v = 0
+    bn = np.sqrt(dot(b, b))
+    S, Y = [], []
+    it = 0
+    for it in range(max_iter):
+        if np.sqrt(dot(g, g)) <= tol * bn:
+            break
+        q = g.copy()
+        alphas = []
+        for s_i, y_i in zip(reversed(S), reversed(Y)):
+            a_i = dot(s_i, q) / dot(y_i, s_i)
+            alphas.append(a_i)
+            q = q - a_i * y_i
+        if S:
+            q = q * (dot(S[-1], Y[-1]) / dot(Y[-1], Y[-1]))
+        for (s_i, y_i), a_i in zip(zip(S, Y), reversed(alphas)):
+            beta = dot(y_i, q) / dot(y_i, s_i)
+            q = q + (a_i - beta) * s_i
+        p = -q
+        Hp = Hmul(p)
+        t = -dot(g, p) / dot(p, Hp)
+        s_new = t * p
+        y_new = t * Hp                       # g_{k+1} - g_k = H s
+        v = v + s_new
+        g = g + y_new
+        S.append(s_new)
+        Y.append(y_new)
+        if len(S) > memory:
+            S.pop(0)
+            Y.pop(0)
+    return v, it
+
+
 def rel_err(v, v_star, M, r_max):
     """|v - v*| / |v*| over the ball |k| <= r_max (voxels outside are unseen)."""
     m = ball_mask(M, r_max)

@@ -675,3 +675,27 @@ def test_network_features_radius_column_closed_form():
     assert F[(h * M + h) * M + h, 0] == 0.0          # the centre, k = 0
     assert F[(h * M + h) * M, 0] == 1.0               # k = (-M/2, 0, 0)
     assert abs(F[0, 0] - math.sqrt(3)) < 1e-15        # the corner (-M/2, -M/2, -M/2)
+
+
+def test_lbfgs_ground_truth():
+    """Section 4's ground-truth solver: L-BFGS on Eq. optim cp reaches the
+    minimiser, i.e. the nearest-interpolation closed form b / diag(H), the
+    CG solution under trilinear interpolation with CTF, and H v = b."""
+    M, B = 10, 8
+    r = M // 2 - 1
+    R = rots(B, 80)
+    df = synth.defocus_angstrom(B, 81)
+    x = cplx((B, M, M), 82)
+    lam = 0.2
+    b = O.full_rhs(x, R, df, M, r, "nearest", CTF)
+    v, _ = O.lbfgs_solve(b, R, df, M, r, "nearest", CTF, lam)
+    D = O.exact_diag(R, df, M, r, "nearest", CTF, lam, 1.0)
+    np.testing.assert_allclose(v, b / D, atol=1e-10 * np.max(np.abs(b / D)))
+    b = O.full_rhs(x, R, df, M, r, "trilinear", CTF)
+    v, it = O.lbfgs_solve(b, R, df, M, r, "trilinear", CTF, lam, max_iter=400)
+    vc, _ = O.cg_solve(b, R, df, M, r, "trilinear", CTF, lam)
+    np.testing.assert_allclose(v, vc, atol=1e-9 * np.max(np.abs(vc)))
+    Hv = (O.hvp(v.real, R, df, M, r, "trilinear", CTF, lam, 1.0)
+          + 1j * O.hvp(v.imag, R, df, M, r, "trilinear", CTF, lam, 1.0))
+    assert np.linalg.norm(Hv - b) <= 1e-10 * np.linalg.norm(b)
+    assert it < 400
