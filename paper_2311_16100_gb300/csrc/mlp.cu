@@ -56,6 +56,14 @@ __device__ __forceinline__ float gelu_f(float x) {
   const float hx = 0.5f * x;
   return fmaf(hx, t, hx);
 }
+// 2 GELU(x) = x + x tanh(u): five operations.  Exactly twice gelu_f (a power
+// of two scales every rounding alike); the forward kernel takes the factor
+// 1/2 into the next layer's weights instead.
+__device__ __forceinline__ float gelu2_f(float x) {
+  const float c = 0.7978845608028654f, c3 = 0.7978845608028654f * 0.044715f;
+  const float t = tanh_hw(x * fmaf(c3, x * x, c));
+  return fmaf(x, t, x);
+}
 // d/dx GELU = s + x s (1 - s) 2c (1 + 3 * 0.044715 x^2), s = 0.5 (1 + tanh(u))
 __device__ __forceinline__ float gelu_grad_s(float x, float s) {
   const float c = 0.7978845608028654f;
@@ -212,11 +220,12 @@ __device__ __forceinline__ void warp_reduce_scatter(float (&v)[N], int lane) {
 
 // ------------------------------------------------------ shared layouts
 struct FwdSmem {
-  unsigned short W2[kHid * kHid];       // B operand: rows o (N), K = i
-  unsigned short H1[kRows * kHid];      // A operand: rows = voxels, K = i
+  unsigned short W2[kHid * kHid];       // B operand: rows o (N), K = i; bf(W2 / 2)
+  unsigned short H1[kRows * kHid];      // A operand: rows = voxels, K = i; bf(2 H1)
   float4 L1[kHid];                      // (W1[i][0..2], b1[i]): one load per unit
-  float2 L2[kHid];                      // (b2[o], w3[o])
-  float W1[192], b1[64], b2[64], w3[64], b3;
+  float4 b2[kHid / 4];                  // b2, four units per load
+  float4 w3[kHid / 4];                  // w3 / 2, four units per load
+  float b3;
   unsigned long long bar;
   uint32_t tmem;
 };
@@ -262,16 +271,24 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
   const int t = threadIdx.x, warp = t >> 5;
   const int n = M * M * M;
   const int n_tiles = (n + kRows - 1) / kRows;
-  load_params(params, S.W1, S.b1, S.b2, S.w3, &S.b3);
-  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+  // Both activations are evaluated as 2 GELU (gelu2_f, one multiplication
+  // fewer each); the factor 1/2 goes into W2 (halving commutes with the BF16
+  // rounding) and into w3, so every product and sum equals the plain
+  // network's.
+  for (int i = threadIdx.x; i < kHid; i += blockDim.x)
     S.L1[i] = make_float4(params[oW1 + 3 * i], params[oW1 + 3 * i + 1], params[oW1 + 3 * i + 2],
                           params[ob1 + i]);
-    S.L2[i] = make_float2(params[ob2 + i], params[ow3 + i]);
+  for (int i = threadIdx.x; i < kHid / 4; i += blockDim.x) {
+    S.b2[i] = make_float4(params[ob2 + 4 * i], params[ob2 + 4 * i + 1], params[ob2 + 4 * i + 2],
+                          params[ob2 + 4 * i + 3]);
+    S.w3[i] = make_float4(0.5f * params[ow3 + 4 * i], 0.5f * params[ow3 + 4 * i + 1],
+                          0.5f * params[ow3 + 4 * i + 2], 0.5f * params[ow3 + 4 * i + 3]);
   }
+  if (t == 0) S.b3 = params[ob3];
   for (int e = t; e < kHid * kHid; e += kRows) {
     const int o = e / kHid, i = e % kHid;
     *reinterpret_cast<unsigned short*>(reinterpret_cast<unsigned char*>(S.W2) +
-                                       core_off(o, i, kHid)) = bf16bits(params[oW2 + e]);
+                                       core_off(o, i, kHid)) = bf16bits(0.5f * params[oW2 + e]);
   }
   if (t == 0) bar_init(smem_u32(&S.bar));
   if (warp == 0) {
@@ -301,7 +318,7 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
       for (int u = 0; u < 8; ++u) {
         const int i = i0 + u;
         const float4 q = S.L1[i];
-        h[u] = gelu_f(fmaf(q.z, x[2], fmaf(q.y, x[1], fmaf(q.x, x[0], q.w))));
+        h[u] = gelu2_f(fmaf(q.z, x[2], fmaf(q.y, x[1], fmaf(q.x, x[0], q.w))));
       }
       st_bf16x8(H1b, core_off(t, i0, kHid), h);
     }
@@ -327,9 +344,12 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
       float a2[16];
       tmem_ld16(lane_addr + c, a2);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const float2 q = S.L2[c + u];
-        y = fmaf(q.y, gelu_f(a2[u] + q.x), y);
+      for (int u = 0; u < 16; u += 4) {
+        const float4 bb = S.b2[(c + u) / 4], ww = S.w3[(c + u) / 4];
+        y = fmaf(ww.x, gelu2_f(a2[u] + bb.x), y);
+        y = fmaf(ww.y, gelu2_f(a2[u + 1] + bb.y), y);
+        y = fmaf(ww.z, gelu2_f(a2[u + 2] + bb.z), y);
+        y = fmaf(ww.w, gelu2_f(a2[u + 3] + bb.w), y);
       }
     }
     if (j < n) out[j] = (exp_out ? expf(y) : y) + offset;
