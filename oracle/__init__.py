@@ -26,6 +26,8 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   splitmix64           pinned: published test vector
   hutchinson_diag      pinned: exact under nearest (Remark 3.3), unbiased
                        under trilinear (z-score against the dense Hessian)
+  hutchinson_diag_at   pinned: equals hutchinson_diag at every voxel (the
+                       same literal sum restricted to chosen rows)
   precomputed_preconditioner
                        pinned: brute-force pixel counts under nearest
                        (every probe exact, equal batches average to the
@@ -66,7 +68,8 @@ from .geometry import (ball_mask, ctf_of_s2, ctf_pixels, default_r_max, disc_mas
                        stencil)
 from .operators import (backproject_adjoint, coverage_features, dense_hessian,
                         exact_diag, hvp, loss, loss_grad, slice_project)
-from .hutchinson import hutchinson_diag, probe_words, rademacher_probes, splitmix64
+from .hutchinson import (hutchinson_diag, hutchinson_diag_at, probe_words, rademacher_probes,
+                         splitmix64)
 from .sgd import (alg1_step, alpha_threshold, cg_solve, full_rhs, lbfgs_solve,
                   precomputed_preconditioner, rel_err, shell_counts)
 from . import diagnostics, mlp

@@ -6,7 +6,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .operators import hvp
+from .operators import _image_terms, hvp
 
 GOLDEN_GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _MASK32 = np.uint64(0xFFFFFFFF)
@@ -69,3 +69,37 @@ def hutchinson_diag(R, defocus, M, r_max, interp, ctf, lam, scale,
     for k in range(n_probes):
         acc += Z[k] * hvp(Z[k], R, defocus, M, r_max, interp, ctf, lam, scale).ravel()
     return (acc / n_probes).reshape(M, M, M)
+
+
+def hutchinson_diag_at(voxels, R, defocus, M, r_max, interp, ctf, lam, scale,
+                       n_probes, seed, block):
+    """Entries ``voxels`` of hutchinson_diag (Eq. hutch, same probes),
+    computed literally for those rows only, for checking a full-size
+    estimate at sampled voxels:
+
+        D_j = (1/K) sum_k z_kj (H_I z_k)_j,
+        (H_I z)_j = lam z_j + scale sum_i sum_p C_ip^2 w_pj (P_i z)_p,
+
+    the inner sum running over the pixels p whose interpolation stencil
+    holds voxel j.  Since z_kj^2 = 1 the lam term is lam.  Returns float64
+    [len(voxels)]."""
+    vox_sel = np.asarray(voxels, dtype=np.int64)
+    if len(np.unique(vox_sel)) != len(vox_sel):
+        raise ValueError("voxels must be distinct")
+    n = M ** 3
+    words = probe_words(seed, block, n).astype(np.int64)
+    ks = np.arange(n_probes)
+    acc = np.zeros(len(vox_sel))
+    order = np.argsort(vox_sel)
+    sorted_sel = vox_sel[order]
+    for i in range(len(R)):
+        pix, vox, w, C = _image_terms(R[i], defocus[i], M, r_max, interp, ctf)
+        hit = np.isin(vox, sorted_sel) & (w != 0)
+        rows = np.nonzero(hit.any(axis=1))[0]
+        for p in rows:
+            z = 1.0 - 2.0 * ((words[vox[p]][None, :] >> ks[:, None]) & 1)   # [K][c]
+            pz = z @ w[p]                                                  # (P_i z_k)_p
+            for c in np.nonzero(hit[p])[0]:
+                j = order[np.searchsorted(sorted_sel, vox[p, c])]
+                acc[j] += C[p] ** 2 * w[p, c] * float(np.dot(z[:, c], pz)) / n_probes
+    return lam + scale * acc

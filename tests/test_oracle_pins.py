@@ -699,3 +699,21 @@ def test_lbfgs_ground_truth():
           + 1j * O.hvp(v.imag, R, df, M, r, "trilinear", CTF, lam, 1.0))
     assert np.linalg.norm(Hv - b) <= 1e-10 * np.linalg.norm(b)
     assert it < 400
+
+
+@pytest.mark.parametrize("interp", ["nearest", "trilinear"])
+def test_hutchinson_rows_equal_the_full_estimate(interp):
+    """hutchinson_diag_at (rows of Eq. hutch computed one by one, for checks
+    at sampled voxels of full-size runs) equals the literal full estimate
+    hutchinson_diag, K Hessian-vector products, at every voxel."""
+    M, B = 10, 6
+    r = M // 2 - 1
+    R = rots(B, 90)
+    df = synth.defocus_angstrom(B, 91)
+    lam, scale, K = 0.05, 3.0, 8
+    full = O.hutchinson_diag(R, df, M, r, interp, CTF, lam, scale, K, 21, 4).ravel()
+    g = np.random.default_rng(7)
+    sel = np.concatenate([g.choice(M ** 3, size=40, replace=False),
+                          [((M // 2) * M + M // 2) * M + M // 2]])
+    rows = O.hutchinson_diag_at(sel, R, df, M, r, interp, CTF, lam, scale, K, 21, 4)
+    np.testing.assert_allclose(rows, full[sel], rtol=1e-12, atol=1e-12)
