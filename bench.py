@@ -327,20 +327,30 @@ def run_gpu(args, cfg, rank, world):
     if not args.no_e2e:
         nh = min(4, nb)
         pin_img = [images[i * B:(i + 1) * B].cpu().pin_memory() for i in range(nh)]
+        # the same batches as their disc pixels only (the layout of
+        # cs_precond_sgd_step_host_disc)
+        pin_disc = [ops.pack_disc(images[i * B:(i + 1) * B], M // 2 - 1).cpu().pin_memory()
+                    for i in range(nh)]
         pin_q = [quat[i * B:(i + 1) * B].cpu().pin_memory() for i in range(nh)]
         pin_df = [df[i * B:(i + 1) * B].cpu().pin_memory() for i in range(nh)]
         out_loss = torch.zeros(max(args.steps, args.warmup), dtype=torch.float64).pin_memory()
 
-        def e2e_step(s, i):
+        def e2e_step(s, i, disc=False):
             j = s % nh
-            h.precond_sgd_step_host(geom, st, pin_img[j], pin_q[j],
-                                    pin_df[j] if W["ctf"] else None, lam, scale,
-                                    loss_host=out_loss[i])
+            if disc:
+                h.precond_sgd_step_host_disc(geom, st, pin_disc[j], pin_q[j],
+                                             pin_df[j] if W["ctf"] else None, lam, scale,
+                                             loss_host=out_loss[i])
+            else:
+                h.precond_sgd_step_host(geom, st, pin_img[j], pin_q[j],
+                                        pin_df[j] if W["ctf"] else None, lam, scale,
+                                        loss_host=out_loss[i])
 
         def e2e_run(mode):
-            h.set_host_mode(mode)
+            disc = mode == "disc"
+            h.set_host_mode("staged" if disc else mode)
             for s in range(args.warmup):
-                e2e_step(s, s)
+                e2e_step(s, s, disc)
             torch.cuda.synchronize()
             if world > 1:
                 dist.barrier()
@@ -348,7 +358,7 @@ def run_gpu(args, cfg, rank, world):
             w0 = time.perf_counter()
             a0.record(stream)
             for i in range(args.steps):
-                e2e_step(i, i)
+                e2e_step(i, i, disc)
             a1.record(stream)
             torch.cuda.synchronize()
             wall_ = (time.perf_counter() - w0) * 1e3
@@ -357,9 +367,11 @@ def run_gpu(args, cfg, rank, world):
             assert bool(torch.isfinite(out_loss[: args.steps]).all()) and float(out_loss[0]) != 0.0
             return ems_, wall_
 
-        # the default (staged copies), then the direct reads of the images
-        # from the pinned buffers over the host link
-        ems, wall = e2e_run("staged")
+        # the images as their disc pixels (staged), the full images (staged
+        # copies), then the direct reads of the full images from the pinned
+        # buffers over the host link
+        ems, wall = e2e_run("disc")
+        ems_full, _ = e2e_run("staged")
         ems_dir, _ = e2e_run("direct")
         h.set_host_mode("staged")
         # the host-to-device rate alone: the same batches copied back to back
@@ -376,16 +388,20 @@ def run_gpu(args, cfg, rank, world):
         torch.cuda.synchronize()
         cms = c0.elapsed_time(c1) / args.steps
         del dev_img
+        n_px_disc = ops.disc_pixels(M, M // 2 - 1)
         e2e = {"value": job_value(world, B, args.steps, ems), "unit": "images/s",
-               "h2d_bytes_per_step": B * M * M * 8 + B * 16 + B * 4,
+               "h2d_bytes_per_step": B * n_px_disc * 8 + B * 16 + B * 4,
                "d2h_bytes_per_step": 8,
                "host_wall_value": round(job_value(world, B, args.steps, wall), 1),
+               "full_images_value": job_value(world, B, args.steps, ems_full),
+               "full_images_h2d_bytes_per_step": B * M * M * 8 + B * 16 + B * 4,
                "h2d_copy_only": {"GB_per_s": round(B * M * M * 8 / (cms / 1e3) / 1e9, 1),
                                  "images_per_s_at_that_rate": round(world * B / (cms / 1e3), 1)},
                "direct_value": job_value(world, B, args.steps, ems_dir),
-               "api": "cs_precond_sgd_step_host (double-buffered staging copies on a copy "
-                      "stream; direct_value: the traversal reading the disc pixels from the "
-                      "pinned host buffer instead)"}
+               "api": "cs_precond_sgd_step_host_disc (images as their disc pixels, "
+                      "double-buffered staging copies on a copy stream); full_images_value: "
+                      "cs_precond_sgd_step_host with whole images; direct_value: the "
+                      "traversal reading the disc pixels from the pinned full images instead"}
 
     # --- roofline of the dominant phase
     n_px = n_disc_pixels(M, M // 2 - 1)
@@ -1132,9 +1148,10 @@ def contract_line(args, cfg, world, r, cpu=None, metric2=None):
     e2e = None
     if r.get("e2e"):
         e = r["e2e"]
-        e2e = {k: e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step",
-                                 "direct_value") if k in e}
-        e2e["api"] = "cs_precond_sgd_step_host"
+        e2e = {k: (round(e[k], 1) if isinstance(e[k], float) else e[k])
+               for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step",
+                         "full_images_value", "direct_value") if k in e}
+        e2e["api"] = "cs_precond_sgd_step_host_disc"
         if "h2d_copy_only" in e:
             e2e["h2d_copy_only_GB_per_s"] = e["h2d_copy_only"]["GB_per_s"]
     cpu_line = None
@@ -1148,7 +1165,10 @@ def contract_line(args, cfg, world, r, cpu=None, metric2=None):
             "ms_per_step": round(ms_step, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_json(args, cfg),
-            "roofline": r["roofline"], "roofline_l2_reductions": r.get("red_roofline"),
+            "roofline": r["roofline"],
+            "roofline_l2_reductions": ({k: v for k, v in r["red_roofline"].items()
+                                        if k != "peak_source"}
+                                       if r.get("red_roofline") else None),
             "e2e": e2e, "gpu_launches": r["launches"],
             "clocks": ({k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
                        if r.get("clocks") else None),

@@ -319,6 +319,31 @@ int cs_precond_sgd_step_host(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
                              const float* defocus_host, int B, float lambda, float scale,
                              double* loss_host, void* stream);
 
+/* Pixels of an M x M image inside the disc of radius r_max (kx^2 + ky^2 <=
+ * r_max^2): the only pixels the model of Eq. fwd model uses (Section 2.1's
+ * images restricted to the band the volume is refined to).  A pure host
+ * function; returns -1 for M or r_max out of range. */
+int cs_disc_pixels(int M, int r_max);
+
+/* cs_precond_sgd_step_host with the images given as their disc pixels only:
+ * images_disc_host complex64[B][n_px], n_px = cs_disc_pixels(M, r_max),
+ * each image's pixels with kx^2 + ky^2 <= r_max^2 in row-major order (ky
+ * ascending, then kx ascending within a row).  Pixels outside the disc take
+ * no part in the loss, gradient or Hessian, so the step is the same as with
+ * the full images; the host-to-device copy carries n_px instead of M^2
+ * pixels per image (76% of them for r_max = M/2 - 1).  The batch is
+ * always staged: copied into the handle's staging slot on its copy stream,
+ * then stepped on `stream`, double-buffered as in cs_precond_sgd_step_host
+ * (the host mode does not apply); the vector traversal reads the packed
+ * pixels where they land, the other scatter algorithms get them spread
+ * into image layout by a small kernel on the copy stream first.  Arguments, synchronisation and errors otherwise as
+ * cs_precond_sgd_step_host.  The paper has no counterpart: it is a data
+ * layout for feeding the step from host memory. */
+int cs_precond_sgd_step_host_disc(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
+                                  const float* images_disc_host, const float* quat_host,
+                                  const float* defocus_host, int B, float lambda, float scale,
+                                  double* loss_host, void* stream);
+
 /* Phases of cs_precond_sgd_step timed by the profiler. */
 enum {
   CS_PH_PRECOND = 0,   /* probe words, Hutchinson estimate, D update (vector

@@ -347,6 +347,7 @@ int cs_destroy(cs_handle* h) {
     prof_free(h);
     if (h->mws) cudaFree(h->mws);
     if (h->status) cudaFree(h->status);
+    if (h->disc_rows) cudaFree(h->disc_rows);
     if (h->stage || h->copy_stream) {
       cudaDeviceSynchronize();
       if (h->stage) cudaFree(h->stage);
@@ -729,9 +730,12 @@ int cs_threshold_alpha(cs_handle* h, const cs_geom* g, const float* defocus_all,
   return CS_OK;
 }
 
-int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
-                        const float* images, const float* rot, const float* defocus, int B,
-                        float lambda, float scale, void* stream) {
+// One Algorithm-1 step; img_rows != NULL: images disc-packed with those
+// row starts (vector traversal only)
+static int precond_step_impl(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
+                             const float* images, const float* rot, const float* defocus,
+                             int B, float lambda, float scale, void* stream,
+                             const int* img_rows) {
   if (!h) return CS_ERR_ARG;
   CS_TRY(check_geom(h, g));
   CS_TRY(check_batch(h, g, B, rot, defocus));
@@ -779,7 +783,7 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
                          reinterpret_cast<const float2*>(st->v), w.fw.pairs, nullptr,
                          reinterpret_cast<const float2*>(images), pL, st->seed, 0,
                          st->scalars + CS_S_K, st->n_probes, vgrid, s, h->block, h->slabs,
-                         tiled_table(h, g->M)),
+                         tiled_table(h, g->M), img_rows, g->r_max),
             "fused loss_grad launch");
     prof_mark(h, CS_PH_DIRECTION, s);
     CS_CUDA(launch_step_post(g->M, st->mode, reinterpret_cast<const float2*>(st->v), lambda,
@@ -803,6 +807,8 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
     prof_mark(h, CS_NPHASES, s);
     return CS_OK;
   }
+  if (img_rows && B > 0)
+    return fail(h, CS_ERR_INTERNAL, "disc-packed images need the vector traversal");
   const bool tiles = use_tiles(h) && B > 0;
   TileArgs A;
   prof_mark(h, 0, s);
@@ -874,6 +880,12 @@ int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
           "update launch");
   prof_mark(h, CS_NPHASES, s);
   return CS_OK;
+}
+
+int cs_precond_sgd_step(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
+                        const float* images, const float* rot, const float* defocus, int B,
+                        float lambda, float scale, void* stream) {
+  return precond_step_impl(h, g, st, images, rot, defocus, B, lambda, scale, stream, nullptr);
 }
 
 int cs_profile_enable(cs_handle* h, int enable, int max_steps) {
@@ -1093,6 +1105,8 @@ FusedArgs problem_args(const cs_problem& q, const ProblemWs& w, const Geo& G) {
   A.scale = q.scale;
   A.vol = reinterpret_cast<const float2*>(q.state.v);
   A.img = reinterpret_cast<const float2*>(q.images);
+  A.img_rows = nullptr;
+  A.img_r = 0;
   A.E = w.fw.E;
   A.O = w.fw.O;
   A.P = w.fw.P;
@@ -1608,13 +1622,25 @@ struct StageSlot {
   float* quat;
   float* defocus;
   float* rot;
+  float* packed;    // disc-packed images of a cs_precond_sgd_step_host_disc batch
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// disc pixels of radius r: rows ky = -r .. r of 2 floor(sqrt(r^2 - ky^2)) + 1
+long disc_count(int r) {
+  long n = 0;
+  for (int ky = -r; ky <= r; ++ky) {
+    int xr = 0;
+    while ((long)(xr + 1) * (xr + 1) <= (long)r * r - (long)ky * ky) ++xr;
+    n += 2 * xr + 1;
+  }
+  return n;
+}
+
 size_t slot_bytes(int M, int B) {
   return align256((size_t)B * M * M * 8) + align256((size_t)B * 16) + align256((size_t)B * 4) +
-         align256((size_t)B * 36);
+         align256((size_t)B * 36) + align256((size_t)B * disc_count(M / 2 - 1) * 8);
 }
 
 StageSlot stage_slot(const cs_handle* h, int slot) {
@@ -1627,6 +1653,8 @@ StageSlot stage_slot(const cs_handle* h, int slot) {
   s.defocus = reinterpret_cast<float*>(p);
   p += align256((size_t)h->stage_B * 4);
   s.rot = reinterpret_cast<float*>(p);
+  p += align256((size_t)h->stage_B * 36);
+  s.packed = reinterpret_cast<float*>(p);
   return s;
 }
 
@@ -1667,9 +1695,39 @@ int ensure_stage(cs_handle* h, int M, int B) {
     cudaGetLastError();
     return fail(h, CS_ERR_ALLOC, "staging allocation of %zu bytes failed", need);
   }
+  // pixels a disc-packed batch does not write are zero (never read)
+  CS_CUDA(cudaMemset(p, 0, need), "staging reset");
   h->stage = p;
   h->stage_M = M;
   h->stage_B = Bn;
+  return CS_OK;
+}
+
+// Row starts of the disc of radius r in packed order, on the device.
+int ensure_disc_rows(cs_handle* h, int M, int r) {
+  if (h->disc_rows && h->disc_M == M && h->disc_r == r) return CS_OK;
+  std::vector<int> rows(2 * r + 2, 0);
+  for (int k = 0; k <= 2 * r; ++k) {
+    const int ky = k - r;
+    int xr = 0;
+    while ((long)(xr + 1) * (xr + 1) <= (long)r * r - (long)ky * ky) ++xr;
+    rows[k + 1] = rows[k] + 2 * xr + 1;
+  }
+  if (h->disc_rows) {
+    CS_CUDA(cudaDeviceSynchronize(), "synchronise before disc table change");
+    cudaFree(h->disc_rows);
+    h->disc_rows = nullptr;
+  }
+  int* d = nullptr;
+  if (cudaMalloc(&d, rows.size() * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, CS_ERR_ALLOC, "disc row table allocation failed");
+  }
+  h->disc_rows = d;
+  CS_CUDA(cudaMemcpy(d, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice),
+          "disc row table");
+  h->disc_M = M;
+  h->disc_r = r;
   return CS_OK;
 }
 
@@ -1729,6 +1787,59 @@ int cs_precond_sgd_step_host(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
   CS_TRY(cs_quat_to_rot(h, d.quat, B, d.rot, stream));
   CS_TRY(cs_precond_sgd_step(h, g, st, d.images, d.rot, defocus_host ? d.defocus : nullptr, B,
                              lambda, scale, stream));
+  if (loss_host)
+    CS_CUDA(cudaMemcpyAsync(loss_host, st->scalars + CS_S_LOSS, sizeof(double),
+                            cudaMemcpyDeviceToHost, cs),
+            "loss read-back");
+  CS_CUDA(cudaEventRecord(h->compute_done[slot], cs), "compute event");
+  ++h->stage_calls;
+  return CS_OK;
+}
+
+int cs_disc_pixels(int M, int r_max) {
+  if (M < 4 || M > CS_MAX_M || (M & 1) || r_max < 1 || r_max > M / 2 - 1) return -1;
+  return (int)disc_count(r_max);
+}
+
+int cs_precond_sgd_step_host_disc(cs_handle* h, const cs_geom* g, cs_sgd_state* st,
+                                  const float* images_disc_host, const float* quat_host,
+                                  const float* defocus_host, int B, float lambda, float scale,
+                                  double* loss_host, void* stream) {
+  if (!h) return CS_ERR_ARG;
+  CS_TRY(check_geom(h, g));
+  if (!st) return fail(h, CS_ERR_ARG, "state is NULL");
+  if (B < 1) return fail(h, CS_ERR_SHAPE, "batch size B=%d must be positive", B);
+  if (!images_disc_host || !quat_host)
+    return fail(h, CS_ERR_ARG, "images_disc_host or quat_host is NULL");
+  if (g->ctf.enabled && !defocus_host)
+    return fail(h, CS_ERR_ARG, "defocus_host is NULL but the CTF is enabled");
+  CS_SCOPE(h);
+  CS_TRY(ensure_stage(h, g->M, B));
+  CS_TRY(ensure_disc_rows(h, g->M, g->r_max));
+  const int slot = (int)(h->stage_calls & 1u);
+  const StageSlot d = stage_slot(h, slot);
+  cudaStream_t cs = S(stream), cp = h->copy_stream;
+  const size_t npk = (size_t)B * disc_count(g->r_max) * 8;
+  // the vector traversal reads the packed pixels where they land; the other
+  // scatter algorithms get them spread into image layout first
+  const bool packed = use_vector(h, g);
+  CS_CUDA(cudaStreamWaitEvent(cp, h->compute_done[slot], 0), "copy stream wait");
+  CS_CUDA(cudaMemcpyAsync(d.packed, images_disc_host, npk, cudaMemcpyHostToDevice, cp),
+          "image copy");
+  if (!packed)
+    CS_CUDA(launch_expand_disc(g->M, g->r_max, B, h->disc_rows, d.packed, d.images, cp),
+            "disc expansion launch");
+  CS_CUDA(cudaMemcpyAsync(d.quat, quat_host, (size_t)B * 16, cudaMemcpyHostToDevice, cp),
+          "pose copy");
+  if (defocus_host)
+    CS_CUDA(cudaMemcpyAsync(d.defocus, defocus_host, (size_t)B * 4, cudaMemcpyHostToDevice, cp),
+            "defocus copy");
+  CS_CUDA(cudaEventRecord(h->copy_done[slot], cp), "copy event");
+  CS_CUDA(cudaStreamWaitEvent(cs, h->copy_done[slot], 0), "compute stream wait");
+  CS_TRY(cs_quat_to_rot(h, d.quat, B, d.rot, stream));
+  CS_TRY(precond_step_impl(h, g, st, packed ? d.packed : d.images, d.rot,
+                           defocus_host ? d.defocus : nullptr, B, lambda, scale, stream,
+                           packed ? h->disc_rows : nullptr));
   if (loss_host)
     CS_CUDA(cudaMemcpyAsync(loss_host, st->scalars + CS_S_LOSS, sizeof(double),
                             cudaMemcpyDeviceToHost, cs),

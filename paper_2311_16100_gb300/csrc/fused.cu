@@ -593,7 +593,14 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
     float w8[8];
     if (inb) cell_weights(G, c, w8);
     if (FL & (F_ADJ | F_GRAD)) {
-      float2 r = __ldcs(img + (size_t)b * MM + (size_t)iy * G.M + ix);
+      size_t ii = (size_t)b * MM + (size_t)iy * G.M + ix;
+      if (FL & F_PACKED) {
+        // disc-packed images: the pixel's place in its disc row
+        const int k = ky + A.img_r;
+        const int r0 = __ldg(A.img_rows + k), r1 = __ldg(A.img_rows + k + 1);
+        ii = (size_t)b * __ldg(A.img_rows + 2 * A.img_r + 1) + r0 + kx + ((r1 - r0 - 1) >> 1);
+      }
+      float2 r = __ldcs(img + ii);
       if (FL & F_GRAD) {
         const float2 a = inb ? gather_pairs_w(G, c, A.vp, w8) : gather_cell_pairs_slow(G, c, A.vp);
         r = make_float2(fmaf(C, a.x, -r.x), fmaf(C, a.y, -r.y));
@@ -1079,7 +1086,8 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
                          const float* df, int B, float scale, const float2* vol,
                          const float4* vp, const float* zr, const float2* img, double* part,
                          uint64_t seed, uint64_t block_host, const double* k_dev, int K,
-                         int grid, cudaStream_t s, int block, int slabs, bool tiled) {
+                         int grid, cudaStream_t s, int block, int slabs, bool tiled,
+                         const int* img_rows, int img_r) {
   FusedArgs A;
   A.G = G;
   A.table = w.table;
@@ -1091,6 +1099,8 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
   A.vol = vol;
   A.zr = zr;
   A.img = img;
+  A.img_rows = img_rows;
+  A.img_r = img_r;
   A.E = w.E;
   A.O = w.O;
   A.part = part;
@@ -1137,9 +1147,10 @@ cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid
   for (int sl = 0; sl < S; ++sl) {
     if (A.slab_items) A.slab_se = w.slab_se + sl;
     A.part_add = sl > 0;
-    constexpr int X = F_SLAB, Y = F_HOLES;
+    constexpr int X = F_SLAB, Y = F_HOLES, P = F_PACKED;
     cudaError_t e0 = cudaSuccess;
-    switch (flags | (A.slab_items ? X : 0) | holes) {
+    const int packed = (A.img_rows && (flags & F_GRAD)) ? P : 0;
+    switch (flags | (A.slab_items ? X : 0) | holes | packed) {
       case F_ADJ: e0 = launch_pdl(k_fused<F_ADJ>, grid, block, s, A); break;
       case F_GRAD: e0 = launch_pdl(k_fused<F_GRAD>, grid, block, s, A); break;
       case F_GRAD | F_HUTCH: e0 = launch_pdl(k_fused<F_GRAD | F_HUTCH>, grid, block, s, A); break;
@@ -1158,6 +1169,12 @@ cudaError_t launch_fused_args(int flags, FusedArgs A, const FusedWs& w, int grid
       case F_HUTCH | Y: e0 = launch_pdl(k_fused<F_HUTCH | Y>, grid, block, s, A); break;
       case F_HVP | Y: e0 = launch_pdl(k_fused<F_HVP | Y>, grid, block, s, A); break;
       case F_CURV | Y: e0 = launch_pdl(k_fused<F_CURV | Y>, grid, block, s, A); break;
+      case F_GRAD | P: e0 = launch_pdl(k_fused<F_GRAD | P>, grid, block, s, A); break;
+      case F_GRAD | F_HUTCH | P: e0 = launch_pdl(k_fused<F_GRAD | F_HUTCH | P>, grid, block, s, A); break;
+      case F_GRAD | X | P: e0 = launch_pdl(k_fused<F_GRAD | X | P>, grid, block, s, A); break;
+      case F_GRAD | F_HUTCH | X | P: e0 = launch_pdl(k_fused<F_GRAD | F_HUTCH | X | P>, grid, block, s, A); break;
+      case F_GRAD | Y | P: e0 = launch_pdl(k_fused<F_GRAD | Y | P>, grid, block, s, A); break;
+      case F_GRAD | F_HUTCH | Y | P: e0 = launch_pdl(k_fused<F_GRAD | F_HUTCH | Y | P>, grid, block, s, A); break;
       default: return cudaErrorInvalidValue;
     }
     count_launches(1);

@@ -10,7 +10,9 @@ enum FusedFlags { F_ADJ = 1, F_GRAD = 2, F_HUTCH = 4, F_HVP = 8, F_CURV = 16,
                   // (compiled out of the one-slab launches)
                   F_SLAB = 32,
                   // one-slab launch over the tile-ordered table (skips its holes)
-                  F_HOLES = 64 };
+                  F_HOLES = 64,
+                  // F_GRAD on disc-packed images (FusedArgs::img_rows)
+                  F_PACKED = 128 };
 
 constexpr int kMaxProblems = 8;   // volumes per multi-volume launch
 
@@ -27,6 +29,11 @@ struct FusedArgs {
   const float2* vol;    // F_GRAD: volume; F_CURV: direction d
   const float* zr;      // F_HVP: real vector z
   const float2* img;    // F_ADJ, F_GRAD
+  // F_GRAD: images disc-packed (rows[k] = first pixel of disc row k, k = ky +
+  // img_r, rows[2 img_r + 1] = pixels per image) instead of [B][M][M]; NULL:
+  // image layout
+  const int* img_rows;
+  int img_r;
   float2* E;
   float2* O;
   double* part;         // F_GRAD: data-term partials; F_CURV: curvature partials
@@ -90,7 +97,7 @@ cudaError_t launch_fused(int flags, const Geo& G, const FusedWs& w, const float*
                          uint64_t seed, uint64_t block_host, const double* k_dev, int K,
                          int grid, cudaStream_t s, int block = 256,
                          int slabs = 0,
-                         bool tiled = false);
+                         bool tiled = false, const int* img_rows = nullptr, int img_r = 0);
 // One launch over several problems (flags F_GRAD, F_GRAD|F_HUTCH or F_CURV).
 // Number of z-slabs a traversal of an M^3 grid is split into: one launch
 // per slab keeps the slab's accumulators and gathered volume in L2.

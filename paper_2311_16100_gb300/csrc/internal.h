@@ -48,6 +48,10 @@ struct cs_handle {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_done[2] = {nullptr, nullptr};
   cudaEvent_t compute_done[2] = {nullptr, nullptr};
+  // disc-packed host batches: row starts of the disc of radius disc_r in
+  // the packed order (device int[2 disc_r + 2])
+  int* disc_rows = nullptr;
+  int disc_M = 0, disc_r = -1;
 };
 
 namespace cs {
@@ -192,6 +196,12 @@ cudaError_t launch_adam(float* p, float* m, float* v, float* g, float gscale, in
 // positive means)); part: 2 x (grid) doubles of scratch
 cudaError_t launch_mlp_target(int M, int n_est, const float* est, float floor_rel,
                               float* target, double* part, int num_sms, cudaStream_t s);
+
+// Spreads disc-packed images (complex64[B][n_px], rows of the disc of radius
+// r in order, row starts rows[0 .. 2r+1]) into image layout [B][M][M]; the
+// pixels outside the disc are not written.
+cudaError_t launch_expand_disc(int M, int r, int B, const int* rows, const float* packed,
+                               float* images, cudaStream_t s);
 
 // Rate of 16-byte global reductions (G ops/s) measured on a scratch buffer.
 cudaError_t measure_red_rate(void* scratch, size_t bytes, int num_sms, cudaStream_t s,

@@ -305,4 +305,37 @@ cudaError_t launch_rel_err(const Geo& G, const float2* v, const float2* vref,
   return cudaGetLastError();
 }
 
+namespace {
+
+// One block per (disc row, image): row k (ky = k - r) holds the pixels
+// kx = -xr .. xr, xr = (rows[k+1] - rows[k] - 1) / 2, packed at rows[k]
+__global__ void __launch_bounds__(128)
+k_expand_disc(int M, int r, const int* __restrict__ rows, const float2* __restrict__ packed,
+              int n_px, float2* __restrict__ images) {
+  const int k = blockIdx.x, b = blockIdx.y;
+  const int start = __ldg(rows + k), len = __ldg(rows + k + 1) - start;
+  const int xr = (len - 1) / 2, half = M / 2;
+  const float2* src = packed + (size_t)b * n_px + start;
+  float2* dst = images + (size_t)b * M * M + (size_t)(half + k - r) * M + (half - xr);
+  for (int t = threadIdx.x; t < len; t += blockDim.x) dst[t] = __ldcs(src + t);
+}
+
+}  // namespace
+
+cudaError_t launch_expand_disc(int M, int r, int B, const int* rows, const float* packed,
+                               float* images, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  int n_px = 0;
+  for (int ky = -r; ky <= r; ++ky) {
+    int xr = 0;
+    while ((xr + 1) * (xr + 1) <= r * r - ky * ky) ++xr;
+    n_px += 2 * xr + 1;
+  }
+  k_expand_disc<<<dim3(2 * r + 1, B), 128, 0, s>>>(M, r, rows,
+                                                   reinterpret_cast<const float2*>(packed), n_px,
+                                                   reinterpret_cast<float2*>(images));
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace cs

@@ -89,6 +89,9 @@ SIGNATURES = {
                                     c_float, P]),
     "cs_precond_sgd_step_host": (c_int, [P, G, POINTER(CsSgdState), P, P, P, c_int, c_float,
                                          c_float, P, P]),
+    "cs_precond_sgd_step_host_disc": (c_int, [P, G, POINTER(CsSgdState), P, P, P, c_int,
+                                              c_float, c_float, P, P]),
+    "cs_disc_pixels": (c_int, [c_int, c_int]),
     "cs_rel_err": (c_int, [P, G, P, P, P, P]),
     "cs_profile_enable": (c_int, [P, c_int, c_int]),
     "cs_profile_read": (c_int, [P, POINTER(c_double), POINTER(c_int)]),

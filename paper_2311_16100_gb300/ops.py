@@ -271,6 +271,19 @@ class Handle:
             _hptr(defocus_host, torch.float32, "defocus_host"), B, float(lam), float(scale),
             _hptr(loss_host, torch.float64, "loss_host"), _stream(stream)))
 
+    def precond_sgd_step_host_disc(self, geom: Geometry, state: "SGDState", images_disc_host,
+                                   quat_host, defocus_host=None, lam=0.0, scale=1.0,
+                                   loss_host=None, stream=None):
+        """As precond_sgd_step_host with images given as their disc pixels
+        only, complex64 [B][n_px] (pack_disc); asynchronous likewise."""
+        B = quat_host.shape[0]
+        self._check("cs_precond_sgd_step_host_disc", self.lib.cs_precond_sgd_step_host_disc(
+            self.h, geom.c, ctypes.byref(state.cstruct()),
+            _hptr(images_disc_host, torch.complex64, "images_disc_host"),
+            _hptr(quat_host, torch.float32, "quat_host"),
+            _hptr(defocus_host, torch.float32, "defocus_host"), B, float(lam), float(scale),
+            _hptr(loss_host, torch.float64, "loss_host"), _stream(stream)))
+
     def profile_enable(self, enable=True, max_steps=4096):
         self._check("cs_profile_enable", self.lib.cs_profile_enable(self.h, int(enable),
                                                                     int(max_steps)))
@@ -422,6 +435,24 @@ class Handle:
             self.h, geom.c, _ptr(v, torch.complex64, "v"), _ptr(v_ref, torch.complex64, "v_ref"),
             _ptr(out, torch.float64, "out"), _stream(stream)))
         return out
+
+
+def disc_pixels(M: int, r_max: int) -> int:
+    """Pixels of an M x M image inside the disc of radius r_max."""
+    n = int(N.load().cs_disc_pixels(M, r_max))
+    if n < 0:
+        raise ValueError(f"M={M}, r_max={r_max} out of range")
+    return n
+
+
+def pack_disc(images: torch.Tensor, r_max: int) -> torch.Tensor:
+    """images [B][M][M] -> their disc pixels [B][n_px] in the packed order of
+    cs_precond_sgd_step_host_disc (row-major: ky ascending, then kx); a copy
+    (data movement only)."""
+    M = images.shape[-1]
+    k = torch.arange(M) - M // 2
+    mask = (k[:, None] ** 2 + k[None, :] ** 2) <= r_max * r_max
+    return images[:, mask.to(images.device)].contiguous()
 
 
 MODES = {"plain": N.CS_PLAIN, "hutchinson": N.CS_HUTCHINSON, "fixed": N.CS_FIXED}

@@ -63,7 +63,8 @@ def _stub_gpu_result():
     e2e = {"value": 1556000.0, "unit": "images/s", "h2d_bytes_per_step": 134238208,
            "d2h_bytes_per_step": 8, "host_wall_value": 1549000.0,
            "h2d_copy_only": {"GB_per_s": 211.3, "images_per_s_at_that_rate": 1610000.0},
-           "direct_value": 1230000.0, "api": "cs_precond_sgd_step_host (long description)"}
+           "direct_value": 1230000.0, "full_images_value": 1521000.0,
+           "api": "cs_precond_sgd_step_host_disc (long description)"}
     return {"ms": 20 * 0.63, "timed_images": 20 * 1024, "launches": 220,
             "phases": {"precond": 0.02, "loss_grad": 0.429, "direction": 0.039,
                        "curvature": 0.136, "update": 0.019},

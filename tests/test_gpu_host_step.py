@@ -78,3 +78,55 @@ def test_host_step_rejects_bad_arguments():
     with pytest.raises(CryoSGDError):
         h._check("cs_set_host_mode", h.lib.cs_set_host_mode(h.h, 7))
     h.close()
+
+
+@pytest.mark.parametrize("algo", ["auto", "vector_slabs3", "pixel"])
+def test_disc_packed_host_steps_match_device_steps(algo):
+    """cs_precond_sgd_step_host_disc: the batch given as its disc pixels only
+    (read where they land by the vector traversal, also split into z-slabs;
+    spread into image layout first for the pixel algorithm) gives the same
+    iterates as steps on the full images held on the device; r_max below
+    M/2 - 1 and a batch size change between calls included."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_16100_gb300 import ops
+    M, r = 32, 13
+    sizes = (16, 16, 10, 16)
+    c = Case(M, sum(sizes), interp="trilinear", ctf=True, seed=85, r_max=r)
+    geom = c.gpu_geometry()
+    h_dev, h_host = ops.Handle(0), ops.Handle(0)
+    if algo == "vector_slabs3":
+        h_host.set_algo("vector")
+        h_host.set_slabs(3)
+    else:
+        h_host.set_algo(algo)
+    g = c.to_gpu()
+    alpha = float(h_dev.threshold_alpha(geom, g["df"], sum(sizes), 0.01))
+    st_dev, st_host = make_state(ops, c, alpha), make_state(ops, c, alpha)
+    disc = ops.pack_disc(torch.from_numpy(c.images), r).pin_memory()
+    assert disc.shape == (sum(sizes), ops.disc_pixels(M, r))
+    q = torch.from_numpy(c.quat.astype(np.float32)).pin_memory()
+    df = torch.from_numpy(c.df).pin_memory()
+    losses = torch.zeros(len(sizes), dtype=torch.float64).pin_memory()
+    rot = torch.empty((max(sizes), 3, 3), device="cuda")
+    start = 0
+    dev_losses = []
+    for k, B in enumerate(sizes):
+        sl = slice(start, start + B)
+        start += B
+        h_host.precond_sgd_step_host_disc(geom, st_host, disc[sl], q[sl], df[sl], 0.01, 2.0,
+                                          loss_host=losses[k])
+        h_dev.quat_to_rot(g["quat"][sl].contiguous(), rot[:B])
+        h_dev.precond_sgd_step(geom, st_dev, g["images"][sl].contiguous(), rot[:B],
+                               g["df"][sl].contiguous(), 0.01, 2.0)
+        dev_losses.append(st_dev.scalars[3].clone())
+    torch.cuda.synchronize()
+    assert rel_l2(st_host.v.cpu().numpy(), st_dev.v.cpu().numpy()) <= 1e-6
+    assert float(st_host.scalars[0]) == float(st_dev.scalars[0])
+    for k in range(len(sizes)):
+        assert abs(float(losses[k]) - float(dev_losses[k])) <= 1e-6 * abs(float(dev_losses[k]))
+    assert ops.disc_pixels(M, M // 2 - 1) == 709
+    with pytest.raises(ValueError):
+        ops.disc_pixels(M, M // 2)
+    h_dev.close()
+    h_host.close()
