@@ -597,8 +597,11 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
       if (FL & F_PACKED) {
         // disc-packed images: the pixel's place in its disc row
         const int k = ky + A.img_r;
+        if (!CS_IN(k, 2 * A.img_r + 1)) continue;
         const int r0 = __ldg(A.img_rows + k), r1 = __ldg(A.img_rows + k + 1);
-        ii = (size_t)b * __ldg(A.img_rows + 2 * A.img_r + 1) + r0 + kx + ((r1 - r0 - 1) >> 1);
+        const int xi = kx + ((r1 - r0 - 1) >> 1);          // place within the row
+        if (!CS_IN(xi, r1 - r0)) continue;
+        ii = (size_t)b * __ldg(A.img_rows + 2 * A.img_r + 1) + r0 + xi;
       }
       float2 r = __ldcs(img + ii);
       if (FL & F_GRAD) {

@@ -4,9 +4,10 @@ libcryosgd_debug.so (built by build() with -DCS_DEBUG_BOUNDS) range-checks
 every gather and scatter index of the traversal kernels on the device: an
 index out of range skips its access and cs_check_device_status reports
 CS_ERR_INTERNAL.  This runs the small parity cases (every scatter algorithm,
-the three-slab traversal) in a child process that loads that variant
-(CS_LIBRARY=debug); each handle's status is checked when its tests end, so
-any failed range check fails the run.
+the three-slab traversal) and the host-fed steps (whole and disc-packed
+images) in a child process that loads that variant (CS_LIBRARY=debug); each
+handle's status is checked when its tests end, so any failed range check
+fails the run.
 """
 import os
 import subprocess
@@ -36,6 +37,7 @@ def test_parity_suite_under_range_checks():
     env = dict(os.environ, CS_LIBRARY="debug")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         "-m", "gpu", "tests/test_gpu_parity.py",
+                        "tests/test_gpu_host_step.py",
                         "tests/test_gpu_debug_bounds.py::test_loaded_library_variant",
                         "-k", "not full_size"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)

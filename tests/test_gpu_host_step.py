@@ -128,5 +128,7 @@ def test_disc_packed_host_steps_match_device_steps(algo):
     assert ops.disc_pixels(M, M // 2 - 1) == 709
     with pytest.raises(ValueError):
         ops.disc_pixels(M, M // 2)
+    # a failed device-side range check (debug variant) would be reported here
+    h_host.check_device_status()
     h_dev.close()
     h_host.close()
