@@ -70,7 +70,28 @@ def parse():
                    help="scatter algorithm of the adjoint-type passes")
     p.add_argument("--images", type=int, default=0,
                    help="override the number of images held in HBM (profiling runs)")
+    p.add_argument("--config-file", default=None,
+                   help="JSON object whose keys override the named workload's fields "
+                        "(M, n_img, B, interp, K, df, snr, blobs, seed)")
     return p.parse_args()
+
+
+def workload_config(args):
+    """The named workload, with the fields of --config-file (a JSON object)
+    and --images applied on top."""
+    cfg = dict(CONFIGS[args.config])
+    if getattr(args, "config_file", None):
+        with open(args.config_file) as f:
+            extra = json.load(f)
+        unknown = set(extra) - set(cfg)
+        if unknown:
+            raise SystemExit(f"--config-file: unknown workload fields {sorted(unknown)}")
+        if "df" in extra and extra["df"] is not None:
+            extra["df"] = tuple(extra["df"])
+        cfg.update(extra)
+    if args.images:
+        cfg["n_img"] = max(cfg["B"], args.images)
+    return cfg
 
 
 # ------------------------------------------------------------------ helpers
@@ -1186,9 +1207,7 @@ def emit_aux(name, payload):
 
 def main():
     args = parse()
-    cfg = dict(CONFIGS[args.config])
-    if args.images:
-        cfg["n_img"] = max(cfg["B"], args.images)
+    cfg = workload_config(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

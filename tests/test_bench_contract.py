@@ -4,6 +4,8 @@ one-image sample."""
 import json
 import os
 import subprocess
+
+import pytest
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -131,3 +133,20 @@ def test_batches_cover_the_dataset_once():
     assert sum(n for _, n in bl) == 50000
     assert all(s == i * 1024 for i, (s, _) in enumerate(bl))
     assert bench.batches(1000, 100) == [(i * 100, 100) for i in range(10)]
+
+
+def test_config_file_overrides_the_named_workload(tmp_path):
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    f = tmp_path / "w.json"
+    f.write_text(json.dumps({"M": 96, "n_img": 4096, "df": [0.5, 3.5], "snr": 0.2}))
+    args = argparse.Namespace(config="m128", config_file=str(f), images=0)
+    cfg = bench.workload_config(args)
+    assert cfg["M"] == 96 and cfg["n_img"] == 4096 and cfg["df"] == (0.5, 3.5)
+    assert cfg["B"] == bench.CONFIGS["m128"]["B"] and cfg["snr"] == 0.2
+    f.write_text(json.dumps({"bogus": 1}))
+    with pytest.raises(SystemExit):
+        bench.workload_config(args)
+    args = argparse.Namespace(config="m32", config_file=None, images=5000)
+    assert bench.workload_config(args)["n_img"] == 5000
