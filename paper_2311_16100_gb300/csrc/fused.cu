@@ -195,6 +195,16 @@ __device__ __forceinline__ void ld_patch(const float4* __restrict__ p, float (&a
       : "l"(p));
 }
 
+// Place of voxel (x, y, z)'s patch in the patch buffer: the grid in 2 x 2 x 2
+// blocks of voxels, block-major, z-, y-, x-major within a block, so that a
+// z-plane of a block (4 patches) is one 128-byte line and cells a step apart
+// share lines more often than in row order
+__device__ __forceinline__ size_t patch_slot(int M, int x, int y, int z) {
+  const int Mh = M >> 1;
+  return ((((size_t)(z >> 1) * Mh + (y >> 1)) * Mh + (x >> 1)) << 3) +
+         (((z & 1) << 2) | ((y & 1) << 1) | (x & 1));
+}
+
 // gather from the 2 x 2 patch layout with precomputed corner weights
 // (base_in cells): one 32-byte load per z-plane of the cell; weight
 // w8[4 dz + 2 dy + dx] goes with patch element dx + 2 dy
@@ -207,7 +217,7 @@ __device__ __forceinline__ float2 gather_patch_w(const Geo& G, const Cell& c,
   for (int dz = 0; dz < 2; ++dz) {
     const int z = c.z0 + dz;
     if (z >= M) continue;
-    const size_t j = ((size_t)z * M + c.y0) * M + c.x0;
+    const size_t j = patch_slot(M, c.x0, c.y0, z);
     if (!CS_IN(j, (size_t)M * M * M)) continue;
     float a[8];
     ld_patch(dq + 2 * j, a);
@@ -227,7 +237,7 @@ __device__ __forceinline__ float2 gather_cell_patch_slow(const Geo& G, const Cel
   for (int k = 0; k < 8; ++k) {
     if (!corner_in(G, c, k)) continue;
     const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-    const size_t j = ((size_t)(c.z0 + dz) * G.M + (c.y0 + dy)) * G.M + (c.x0 + dx);
+    const size_t j = patch_slot(G.M, c.x0 + dx, c.y0 + dy, c.z0 + dz);
     if (!CS_IN(j, (size_t)G.M * G.M * G.M)) continue;
     const float4 a = __ldg(dq + 2 * j);
     const float w = corner_w(c, k);
@@ -908,26 +918,30 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
   }
 }
 
-// 2 x 2 (x, y) patch layout of d for the curvature pass: patch j =
-// (d[j], d[j+1], d[j+M], d[j+M+1]), 0 past the grid's edge in x or y; one
-// thread per patch, written as two consecutive 16-byte stores (a warp's
-// stores cover 1 KB contiguously).  Written by k_step_post directly instead
-// (d[j] stored into four patches, 8 bytes each): slower (curvature 0.107 ->
-// 0.115 ms and step 0.616 -> 0.620 ms at 128^3).
+// 2 x 2 (x, y) patch layout of d for the curvature pass: the patch of voxel
+// j = (x, y, z) is (d[j], d[j+1], d[j+M], d[j+M+1]), 0 past the grid's edge
+// in x or y, stored at patch_slot(x, y, z).  Thread t writes patch slot t
+// (two consecutive 16-byte stores: a warp's stores cover 1 KB contiguously)
+// and reads the four values it holds.  Written by k_step_post directly
+// instead (d[j] stored into four patches, 8 bytes each): slower (curvature
+// 0.107 -> 0.115 ms and step 0.616 -> 0.620 ms at 128^3).
 __global__ void __launch_bounds__(256)
 k_patches(int M, const float2* __restrict__ dn, float4* __restrict__ dq) {
   grid_dep_wait();
-  const int n = M * M * M;
+  const int n = M * M * M, Mh = M >> 1;
   const float2 z2 = make_float2(0.f, 0.f);
-  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
-    const int x = j % M, y = (j / M) % M;
+  for (int t = blockIdx.x * 256 + threadIdx.x; t < n; t += gridDim.x * 256) {
+    const int in = t & 7, blk = t >> 3;
+    const int x = 2 * (blk % Mh) + (in & 1), y = 2 * ((blk / Mh) % Mh) + ((in >> 1) & 1);
+    const int z = 2 * (blk / (Mh * Mh)) + (in >> 2);
+    const int j = (z * M + y) * M + x;
     const bool xin = x + 1 < M, yin = y + 1 < M;
     const float2 a = dn[j];
     const float2 b = xin ? dn[j + 1] : z2;
     const float2 c = yin ? dn[j + M] : z2;
     const float2 d = xin && yin ? dn[j + M + 1] : z2;
-    dq[2 * (size_t)j] = make_float4(a.x, a.y, b.x, b.y);
-    dq[2 * (size_t)j + 1] = make_float4(c.x, c.y, d.x, d.y);
+    dq[2 * (size_t)t] = make_float4(a.x, a.y, b.x, b.y);
+    dq[2 * (size_t)t + 1] = make_float4(c.x, c.y, d.x, d.y);
   }
 }
 
