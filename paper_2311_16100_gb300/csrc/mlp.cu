@@ -56,14 +56,6 @@ __device__ __forceinline__ float gelu_f(float x) {
   const float hx = 0.5f * x;
   return fmaf(hx, t, hx);
 }
-// 2 GELU(x) = x + x tanh(u): five operations.  Exactly twice gelu_f (a power
-// of two scales every rounding alike); the forward kernel takes the factor
-// 1/2 into the next layer's weights instead.
-__device__ __forceinline__ float gelu2_f(float x) {
-  const float c = 0.7978845608028654f, c3 = 0.7978845608028654f * 0.044715f;
-  const float t = tanh_hw(x * fmaf(c3, x * x, c));
-  return fmaf(x, t, x);
-}
 // d/dx GELU = s + x s (1 - s) 2c (1 + 3 * 0.044715 x^2), s = 0.5 (1 + tanh(u))
 __device__ __forceinline__ float gelu_grad_s(float x, float s) {
   const float c = 0.7978845608028654f;
@@ -77,17 +69,90 @@ __device__ __forceinline__ unsigned short bf16bits(float x) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
-// features of voxel j; in_ball: |k|^2 <= r2
-__device__ __forceinline__ void features(int j, int M, const float* __restrict__ cov,
-                                         const float* __restrict__ c2w, float x[3], int r2,
-                                         bool& in_ball) {
-  const int half = M / 2;
-  const int ix = j % M, iy = (j / M) % M, iz = j / (M * M);
-  const int kx = ix - half, ky = iy - half, kz = iz - half;
+// ---- packed FP32 pairs (sm_100 family): one instruction performs two IEEE
+// round-to-nearest operations, each lane bit-identical to the scalar one.
+// The tensor-core kernels evaluate units two at a time with these: the
+// scalar work around the MMAs (the activations and their derivatives) is
+// what bounds them, and pairing halves its instruction count.
+constexpr float kGc = 0.7978845608028654f;       // sqrt(2/pi)
+constexpr float kGc3 = 0.7978845608028654f * 0.044715f;
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 tanh2(float2 u) { return make_float2(tanh_hw(u.x), tanh_hw(u.y)); }
+// 2 GELU(x) = x + x tanh(u) of both lanes: five operations.  Exactly twice
+// gelu_f (a power of two scales every rounding alike); the forward kernel
+// takes the factor 1/2 into the next layer's weights instead.
+__device__ __forceinline__ float2 gelu2_x2(float2 x) {
+  const float2 t = tanh2(mul2(x, fma2(dup2(kGc3), mul2(x, x), dup2(kGc))));
+  return fma2(x, t, x);
+}
+// gelu_f of both lanes
+__device__ __forceinline__ float2 gelu_x2(float2 x) {
+  const float2 t = tanh2(mul2(x, fma2(dup2(kGc3), mul2(x, x), dup2(kGc))));
+  const float2 hx = mul2(dup2(0.5f), x);
+  return fma2(hx, t, hx);
+}
+// gelu_sig of both lanes
+__device__ __forceinline__ float2 gelu_sig_x2(float2 x) {
+  const float2 q = mul2(mul2(dup2(0.044715f), x), x);
+  const float2 t = tanh2(mul2(dup2(kGc), fma2(q, x, x)));
+  return fma2(dup2(0.5f), t, dup2(0.5f));
+}
+// gelu_grad_s of both lanes, given xs = x s (1 - s is s (-1) + 1: exact
+// product, one rounding, as the scalar subtraction)
+__device__ __forceinline__ float2 gelu_grad_x2(float2 x, float2 s, float2 xs) {
+  const float2 p = mul2(xs, fma2(s, dup2(-1.f), dup2(1.f)));
+  const float2 g = mul2(dup2(2.f * kGc), fma2(dup2(3.f * 0.044715f), mul2(x, x), dup2(1.f)));
+  return fma2(p, g, s);
+}
+// two BF16 (round to nearest even), the first in the low half
+__device__ __forceinline__ uint32_t bf16x2_bits(float2 v) {
+  const __nv_bfloat162 b = __floats2bfloat162_rn(v.x, v.y);
+  return *reinterpret_cast<const uint32_t*>(&b);
+}
+
+// Grid of the features: M, M/2 and their reciprocals.
+struct FeatGrid {
+  int M, half;
+  float inv_M, inv_half;
+};
+__device__ __forceinline__ FeatGrid feat_grid(int M) {
+  return FeatGrid{M, M / 2, 1.f / (float)M, 1.f / (float)(M / 2)};
+}
+// q = a / d, *rem = a mod d for 0 <= a < 2^27, 1 <= d <= 512: the float
+// quotient a * (1/d) is within 20/d of a/d (float(a) within 4, 1/d and the
+// product within 2^-24 relative each), so below 1 for d >= 20 and far below
+// it for smaller d (then a < 2^24 and float(a) is exact); one correction
+// step makes it exact.
+__device__ __forceinline__ int div_grid(int a, int d, float inv_d, int* rem) {
+  int q = (int)((float)a * inv_d);
+  int r = a - q * d;
+  if (r < 0) {
+    --q;
+    r += d;
+  } else if (r >= d) {
+    ++q;
+    r -= d;
+  }
+  *rem = r;
+  return q;
+}
+// features of voxel j (cov_j, c2w_j: its inputs); in_ball: |k|^2 <= r2.
+// log1p(c) for c >= 0 as the
+// hardware logarithm of 1 + c (absolute error a few 1e-7: far below the
+// BF16 rounding of the first hidden layer)
+__device__ __forceinline__ void features(int j, const FeatGrid& G, float cov_j, float c2w_j,
+                                         float x[3], int r2, bool& in_ball) {
+  int ix, iy;
+  const int jm = div_grid(j, G.M, G.inv_M, &ix);
+  const int iz = div_grid(jm, G.M, G.inv_M, &iy);
+  const int kx = ix - G.half, ky = iy - G.half, kz = iz - G.half;
   const int q = kx * kx + ky * ky + kz * kz;
-  x[0] = sqrtf((float)q) / (float)half;
-  x[1] = log1pf(fmaxf(__ldg(cov + j), 0.f));
-  x[2] = log1pf(fmaxf(__ldg(c2w + j), 0.f));
+  x[0] = sqrtf((float)q) * G.inv_half;
+  x[1] = __logf(1.f + fmaxf(cov_j, 0.f));
+  x[2] = __logf(1.f + fmaxf(c2w_j, 0.f));
   in_ball = q <= r2;
 }
 
@@ -181,23 +246,30 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive FP32 columns, issued without waiting: the registers are
+// valid after tmem_wait16 on the same array, which names them as operands so
+// that no use of them is scheduled before the wait
+__device__ __forceinline__ void tmem_issue16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :: "memory");
+}
+
 // byte offset of element (row, k) in a K-major canonical tile with K extent
 // kext (LBO = 128 bytes, SBO = kext/8 * 128 bytes)
 __device__ __forceinline__ uint32_t core_off(int row, int k, int kext) {
   return (uint32_t)((row >> 3) * (kext / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 +
                     (k & 7) * 2);
-}
-
-
-// eight consecutive K elements of one row of a K-major canonical tile are
-// 16 contiguous bytes: stored with one 128-bit shared-memory store
-__device__ __forceinline__ void st_bf16x8(unsigned char* base, uint32_t off, const float* v) {
-  uint4 q;
-  q.x = (uint32_t)bf16bits(v[0]) | ((uint32_t)bf16bits(v[1]) << 16);
-  q.y = (uint32_t)bf16bits(v[2]) | ((uint32_t)bf16bits(v[3]) << 16);
-  q.z = (uint32_t)bf16bits(v[4]) | ((uint32_t)bf16bits(v[5]) << 16);
-  q.w = (uint32_t)bf16bits(v[6]) | ((uint32_t)bf16bits(v[7]) << 16);
-  *reinterpret_cast<uint4*>(base + off) = q;
 }
 
 
@@ -222,7 +294,7 @@ __device__ __forceinline__ void warp_reduce_scatter(float (&v)[N], int lane) {
 struct FwdSmem {
   unsigned short W2[kHid * kHid];       // B operand: rows o (N), K = i; bf(W2 / 2)
   unsigned short H1[kRows * kHid];      // A operand: rows = voxels, K = i; bf(2 H1)
-  float4 L1[kHid];                      // (W1[i][0..2], b1[i]): one load per unit
+  float4 L1[kHid];                      // layer 1 by unit pairs: see pair_l1
   float4 b2[kHid / 4];                  // b2, four units per load
   float4 w3[kHid / 4];                  // w3 / 2, four units per load
   float b3;
@@ -231,6 +303,7 @@ struct FwdSmem {
 };
 
 constexpr int kFeat = 2 * kHid;        // a voxel's row of the gradient kernel: dA2 | H1
+constexpr int kSmallTc = 2 * kHid + 1;  // db2, dw3, db3 (tensor-core gradient kernel)
 struct GradSmem {
   // [voxel][feature], K-major with K extent 128: features 0..63 = bf(dA2)
   // (A of the backward MMA), 64..127 = bf(H1) (A of the forward MMA); read
@@ -238,10 +311,11 @@ struct GradSmem {
   unsigned short XV[kRows * kFeat];
   unsigned short W2[kHid * kHid];       // forward B: rows o, K = i
   unsigned short W2T[kHid * kHid];      // backward B: rows i, K = o
-  float4 L1[kHid];                      // (W1[i][0..2], b1[i])
-  float2 L2[kHid];                      // (b2[o], w3[o])
+  float4 L1[kHid];                      // layer 1 by unit pairs: see pair_l1
+  float4 L2[kHid / 2];                  // (b2[o], b2[o+1], w3[o], w3[o+1]), o even
+  float4 X[kRows];                      // (x0, x1, x2, 1) of the tile's voxels
   float b3;
-  float small[kSmall];                  // dW1, db1, db2, dw3, db3 of this CTA
+  float small[kSmallTc];                // db2, dw3, db3 of this CTA
   unsigned long long bar;
   uint32_t tmem;
 };
@@ -260,9 +334,29 @@ __device__ __forceinline__ void load_params(const float* __restrict__ p, float* 
   if (threadIdx.x == 0) *b3 = p[ob3];
 }
 
+// Layer 1 in unit pairs: entries 2p and 2p+1 of L1 hold units 2p, 2p+1 as
+// (W1[2p][0], W1[2p+1][0], W1[2p][1], W1[2p+1][1]) and
+// (W1[2p][2], W1[2p+1][2], b1[2p], b1[2p+1]).
+__device__ __forceinline__ void pair_l1(const float* __restrict__ params, float4* L1) {
+  for (int p = threadIdx.x; p < kHid / 2; p += blockDim.x) {
+    const float* w = params + oW1 + 6 * p;
+    L1[2 * p] = make_float4(w[0], w[3], w[1], w[4]);
+    L1[2 * p + 1] = make_float4(w[2], w[5], params[ob1 + 2 * p], params[ob1 + 2 * p + 1]);
+  }
+}
+// pre-activations of units 2p, 2p+1: ((W1 x_0 + b1) + W1 x_1) + W1 x_2, the
+// order of the scalar kernels
+__device__ __forceinline__ float2 layer1_x2(const float4* L1, int p, float2 X0, float2 X1,
+                                           float2 X2) {
+  const float4 qa = L1[2 * p], qb = L1[2 * p + 1];
+  float2 a = fma2(make_float2(qa.x, qa.y), X0, make_float2(qb.z, qb.w));
+  a = fma2(make_float2(qa.z, qa.w), X1, a);
+  return fma2(make_float2(qb.x, qb.y), X2, a);
+}
+
 // ------------------------------------------------------ tensor-core kernels
 // logd[j] = MLP(features(j)) + offset (exp_out: exp(logd) + offset instead)
-__global__ void __launch_bounds__(kRows)
+__global__ void __launch_bounds__(kRows, 8)
 k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restrict__ cov,
                  const float* __restrict__ c2w, float* __restrict__ out, int exp_out,
                  float offset, int* __restrict__ err) {
@@ -270,14 +364,13 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
   FwdSmem& S = *reinterpret_cast<FwdSmem*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
   const int n = M * M * M;
+  const FeatGrid G = feat_grid(M);
   const int n_tiles = (n + kRows - 1) / kRows;
-  // Both activations are evaluated as 2 GELU (gelu2_f, one multiplication
+  // Both activations are evaluated as 2 GELU (gelu2_x2, one multiplication
   // fewer each); the factor 1/2 goes into W2 (halving commutes with the BF16
   // rounding) and into w3, so every product and sum equals the plain
   // network's.
-  for (int i = threadIdx.x; i < kHid; i += blockDim.x)
-    S.L1[i] = make_float4(params[oW1 + 3 * i], params[oW1 + 3 * i + 1], params[oW1 + 3 * i + 2],
-                          params[ob1 + i]);
+  pair_l1(params, S.L1);
   for (int i = threadIdx.x; i < kHid / 4; i += blockDim.x) {
     S.b2[i] = make_float4(params[ob2 + 4 * i], params[ob2 + 4 * i + 1], params[ob2 + 4 * i + 2],
                           params[ob2 + 4 * i + 3]);
@@ -305,22 +398,32 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
   const uint32_t idesc = umma_idesc(128, 64);
   uint32_t phase = 0;
   bool ok = true;
+  // inputs of the next tile, loaded one tile ahead
+  float cov_n = 0.f, c2w_n = 0.f;
+  if (blockIdx.x * kRows + t < n) {
+    cov_n = __ldg(cov + blockIdx.x * kRows + t);
+    c2w_n = __ldg(c2w + blockIdx.x * kRows + t);
+  }
   for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
     const int j = tile * kRows + t;
+    const float cov_j = cov_n, c2w_j = c2w_n;
+    const int jn = j + (int)gridDim.x * kRows;
+    if (jn < n) {
+      cov_n = __ldg(cov + jn);
+      c2w_n = __ldg(c2w + jn);
+    }
     float x[3] = {0.f, 0.f, 0.f};
     bool inb = false;
-    if (j < n) features(j, M, cov, c2w, x, 0x7fffffff, inb);
+    if (j < n) features(j, G, cov_j, c2w_j, x, 0x7fffffff, inb);
     unsigned char* H1b = reinterpret_cast<unsigned char*>(S.H1);
+    const float2 X0 = dup2(x[0]), X1 = dup2(x[1]), X2 = dup2(x[2]);
 #pragma unroll 2
     for (int i0 = 0; i0 < kHid; i0 += 8) {
-      float h[8];
+      uint32_t w[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int i = i0 + u;
-        const float4 q = S.L1[i];
-        h[u] = gelu2_f(fmaf(q.z, x[2], fmaf(q.y, x[1], fmaf(q.x, x[0], q.w))));
-      }
-      st_bf16x8(H1b, core_off(t, i0, kHid), h);
+      for (int p = 0; p < 4; ++p)
+        w[p] = bf16x2_bits(gelu2_x2(layer1_x2(S.L1, i0 / 2 + p, X0, X1, X2)));
+      *reinterpret_cast<uint4*>(H1b + core_off(t, i0, kHid)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     fence_async_smem();
     fence_before();
@@ -338,20 +441,32 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
     phase ^= 1u;
     fence_after();
     if (!ok) break;
-    float y = S.b3;
+    // output: units 4m, 4m+1 and 4m+2, 4m+3 summed in four chains, then
+    // added; the next 16 columns are loaded while these are evaluated
+    float2 ya = make_float2(S.b3, 0.f), yb = make_float2(0.f, 0.f);
+    uint32_t a2[2][16];
+    tmem_issue16(lane_addr, a2[0]);
+    tmem_wait16(a2[0]);
 #pragma unroll
     for (int c = 0; c < kHid; c += 16) {
-      float a2[16];
-      tmem_ld16(lane_addr + c, a2);
+      uint32_t (&cur)[16] = a2[(c / 16) & 1];
+      if (c + 16 < kHid) tmem_issue16(lane_addr + c + 16, a2[(c / 16 + 1) & 1]);
 #pragma unroll
       for (int u = 0; u < 16; u += 4) {
         const float4 bb = S.b2[(c + u) / 4], ww = S.w3[(c + u) / 4];
-        y = fmaf(ww.x, gelu2_f(a2[u] + bb.x), y);
-        y = fmaf(ww.y, gelu2_f(a2[u + 1] + bb.y), y);
-        y = fmaf(ww.z, gelu2_f(a2[u + 2] + bb.z), y);
-        y = fmaf(ww.w, gelu2_f(a2[u + 3] + bb.w), y);
+        ya = fma2(make_float2(ww.x, ww.y),
+                  gelu2_x2(add2(make_float2(__uint_as_float(cur[u]), __uint_as_float(cur[u + 1])),
+                                make_float2(bb.x, bb.y))),
+                  ya);
+        yb = fma2(make_float2(ww.z, ww.w),
+                  gelu2_x2(add2(make_float2(__uint_as_float(cur[u + 2]),
+                                            __uint_as_float(cur[u + 3])),
+                                make_float2(bb.z, bb.w))),
+                  yb);
       }
+      if (c + 16 < kHid) tmem_wait16(a2[(c / 16 + 1) & 1]);
     }
+    const float y = (ya.x + ya.y) + (yb.x + yb.y);
     if (j < n) out[j] = (exp_out ? expf(y) : y) + offset;
     fence_before();
     __syncthreads();
@@ -369,9 +484,20 @@ k_mlp_forward_tc(int M, const float* __restrict__ params, const float* __restric
 // into grad with atomics), and the sum of squared residuals into *sse.
 // 128 TMEM columns per CTA (the layer-2 accumulator, reused for the
 // backward product, and the weight gradient) and at most 128 registers per
-// thread: four CTAs per SM (gradient 0.72 -> 0.63 ms at 128^3 against the
-// earlier build with a separate transposed Gram operand, 256 columns and
-// two CTAs per SM).
+// thread: four CTAs per SM.  Units are evaluated in pairs with packed FP32
+// instructions.  dW1 and db1 are sums over voxels of dA1 x: each tile's dA1
+// (FP32, the tile's rows of the shared buffer once the MMAs have read them)
+// is summed column-wise, thread t accumulating unit t/2 over every other
+// voxel across all the CTA's tiles, so no per-tile reduction is needed.
+// Byte offset of dA1[v][i] in that buffer: rows of 64 floats, 16-byte chunks
+// permuted by a bit reversal of v mod 8, so that the row-wise stores and
+// the column-wise loads are both free of bank conflicts.
+__device__ __forceinline__ uint32_t da1_off(int v, int i) {
+  const int r = v & 7;
+  const int sw = ((r & 1) << 2) | (r & 2) | (r >> 2);
+  return (uint32_t)(v * 256 + (((i >> 2) ^ sw) << 4) + ((i & 3) << 2));
+}
+
 __global__ void __launch_bounds__(kRows, 4)
 k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
               const float* __restrict__ cov, const float* __restrict__ c2w,
@@ -381,12 +507,12 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
   GradSmem& S = *reinterpret_cast<GradSmem*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int n = M * M * M;
+  const FeatGrid G = feat_grid(M);
   const int n_tiles = (n + kRows - 1) / kRows;
-  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
-    S.L1[i] = make_float4(params[oW1 + 3 * i], params[oW1 + 3 * i + 1], params[oW1 + 3 * i + 2],
-                          params[ob1 + i]);
-    S.L2[i] = make_float2(params[ob2 + i], params[ow3 + i]);
-  }
+  pair_l1(params, S.L1);
+  for (int p = threadIdx.x; p < kHid / 2; p += blockDim.x)
+    S.L2[p] = make_float4(params[ob2 + 2 * p], params[ob2 + 2 * p + 1], params[ow3 + 2 * p],
+                          params[ow3 + 2 * p + 1]);
   if (t == 0) S.b3 = params[ob3];
   for (int e = t; e < kHid * kHid; e += kRows) {
     const int o = e / kHid, i = e % kHid;
@@ -396,7 +522,7 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
     *reinterpret_cast<unsigned short*>(reinterpret_cast<unsigned char*>(S.W2T) +
                                        core_off(i, o, kHid)) = w;
   }
-  for (int i = t; i < kSmall; i += kRows) S.small[i] = 0.f;
+  for (int i = t; i < kSmallTc; i += kRows) S.small[i] = 0.f;
   if (t == 0) bar_init(smem_u32(&S.bar));
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;"
@@ -418,21 +544,42 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
   int tiles_done = 0;
   double my_sse = 0.0;
   unsigned char* XVb = reinterpret_cast<unsigned char*>(S.XV);
+  // dW1 column sums of this thread: unit iu, voxels of parity hv
+  const int iu = t >> 1, hv = t & 1;
+  float2 g01 = make_float2(0.f, 0.f), g23 = make_float2(0.f, 0.f);
+  uint32_t coff[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) coff[q] = da1_off(2 * q + hv, iu) - (uint32_t)((2 * q + hv) * 256);
+  // inputs of the next tile, loaded one tile ahead
+  float cov_n = 0.f, c2w_n = 0.f, tgt_n = 0.f;
+  if (blockIdx.x * kRows + t < n) {
+    cov_n = __ldg(cov + blockIdx.x * kRows + t);
+    c2w_n = __ldg(c2w + blockIdx.x * kRows + t);
+    tgt_n = __ldg(target + blockIdx.x * kRows + t);
+  }
   for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
     const int j = tile * kRows + t;
+    const float cov_j = cov_n, c2w_j = c2w_n, tgt_j = tgt_n;
+    const int jn = j + (int)gridDim.x * kRows;
+    if (jn < n) {
+      cov_n = __ldg(cov + jn);
+      c2w_n = __ldg(c2w + jn);
+      tgt_n = __ldg(target + jn);
+    }
     float x[3] = {0.f, 0.f, 0.f};
     bool inb = false;
-    if (j < n) features(j, M, cov, c2w, x, r2, inb);
+    if (j < n) features(j, G, cov_j, c2w_j, x, r2, inb);
+    S.X[t] = make_float4(x[0], x[1], x[2], 1.f);
+    const float2 X0 = dup2(x[0]), X1 = dup2(x[1]), X2 = dup2(x[2]);
     // ---- forward, layer 1 -> features 64..127 of this voxel's row
 #pragma unroll 2
     for (int i0 = 0; i0 < kHid; i0 += 8) {
-      float h[8];
+      uint32_t w[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float4 q = S.L1[i0 + u];
-        h[u] = gelu_f(fmaf(q.z, x[2], fmaf(q.y, x[1], fmaf(q.x, x[0], q.w))));
-      }
-      st_bf16x8(XVb, core_off(t, kHid + i0, kFeat), h);
+      for (int p = 0; p < 4; ++p)
+        w[p] = bf16x2_bits(gelu_x2(layer1_x2(S.L1, i0 / 2 + p, X0, X1, X2)));
+      *reinterpret_cast<uint4*>(XVb + core_off(t, kHid + i0, kFeat)) =
+          make_uint4(w[0], w[1], w[2], w[3]);
     }
     fence_async_smem();
     fence_before();
@@ -452,46 +599,57 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
     if (!ok) break;
     // ---- forward, layers 2-3, loss, backward through layer 3 (the
     // pre-activation is read from tensor memory twice instead of being held
-    // in 64 registers: 86 registers, no spills, gradient 0.631 -> 0.620 ms)
-    float y = S.b3;
+    // in 64 registers)
+    float2 ya = make_float2(S.b3, 0.f), yb = make_float2(0.f, 0.f);
 #pragma unroll
     for (int c = 0; c < kHid; c += 16) {
       float a2[16];
       tmem_ld16(d1 + lane_off + c, a2);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const float2 q = S.L2[c + u];
-        y = fmaf(q.y, gelu_f(a2[u] + q.x), y);
+      for (int u = 0; u < 16; u += 4) {
+        const float4 q = S.L2[(c + u) / 2], q1 = S.L2[(c + u) / 2 + 1];
+        ya = fma2(make_float2(q.z, q.w),
+                  gelu_x2(add2(make_float2(a2[u], a2[u + 1]), make_float2(q.x, q.y))), ya);
+        yb = fma2(make_float2(q1.z, q1.w),
+                  gelu_x2(add2(make_float2(a2[u + 2], a2[u + 3]), make_float2(q1.x, q1.y))), yb);
       }
     }
-    const float r = inb ? y - __ldg(target + j) : 0.f;
+    const float y = (ya.x + ya.y) + (yb.x + yb.y);
+    const float r = inb ? y - tgt_j : 0.f;
     my_sse += (double)r * r;
     const float dy = 2.f * r * inv_n;
+    const float2 DY = dup2(dy);
     float acc_db3 = dy;
     // dA2 -> features 0..63 of this voxel's row; dw3, db2
 #pragma unroll
     for (int c = 0; c < kHid; c += 16) {
-      float v[32], dab[8], a2[16];
+      float v[32], a2[16];
+      uint32_t dab[4];
       tmem_ld16(d1 + lane_off + c, a2);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int o = c + u;
-        const float a = a2[u] + S.L2[o].x;
-        const float sg = gelu_sig(a);             // one tanh for GELU and GELU'
-        const float h2 = a * sg;
-        const float da = dy * S.L2[o].y * gelu_grad_s(a, sg);
-        dab[u & 7] = da;
-        if ((u & 7) == 7) st_bf16x8(XVb, core_off(t, o - 7, kFeat), dab);
-        v[u] = dy * h2;          // dw3[o]
-        v[16 + u] = da;          // db2[o]
+      for (int u = 0; u < 16; u += 2) {
+        const float4 q = S.L2[(c + u) / 2];
+        const float2 a = add2(make_float2(a2[u], a2[u + 1]), make_float2(q.x, q.y));
+        const float2 sg = gelu_sig_x2(a);       // one tanh for GELU and GELU'
+        const float2 h2 = mul2(a, sg);
+        const float2 da = mul2(mul2(DY, make_float2(q.z, q.w)), gelu_grad_x2(a, sg, h2));
+        dab[(u & 7) >> 1] = bf16x2_bits(da);
+        if ((u & 7) == 6)
+          *reinterpret_cast<uint4*>(XVb + core_off(t, c + u - 6, kFeat)) =
+              make_uint4(dab[0], dab[1], dab[2], dab[3]);
+        const float2 dw = mul2(DY, h2);
+        v[u] = dw.x;             // dw3[o]
+        v[u + 1] = dw.y;
+        v[16 + u] = da.x;        // db2[o]
+        v[17 + u] = da.y;
       }
       warp_reduce_scatter(v, lane);
       // lane l holds element l: dw3[c + l] (l < 16) or db2[c + l - 16]
-      atomicAdd(&S.small[lane < 16 ? 192 + 64 + 64 + c + lane : 192 + 64 + c + lane - 16], v[0]);
+      atomicAdd(&S.small[lane < 16 ? kHid + c + lane : c + lane - 16], v[0]);
     }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) acc_db3 += __shfl_xor_sync(0xffffffffu, acc_db3, s);
-    if (lane == 0) atomicAdd(&S.small[kSmall - 1], acc_db3);
+    if (lane == 0) atomicAdd(&S.small[2 * kHid], acc_db3);
     fence_async_smem();
     fence_before();
     __syncthreads();
@@ -520,28 +678,36 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
     fence_after();
     if (!ok) break;
     ++tiles_done;
-    // ---- backward through layer 1: dA1 = dH1 * gelu'(A1); dW1, db1
+    // ---- backward through layer 1: dA1 = dH1 * gelu'(A1) into this
+    // voxel's row of the buffer (both MMAs have read it)
 #pragma unroll
     for (int c = 0; c < kHid; c += 8) {
       float dh[8];
       tmem_ld8(d1 + lane_off + c, dh);
-      // v[4u + f] = dA1 x_f (f < 3) and dA1 (f = 3) of unit c + u
-      float v[32];
+      float4 da1[2];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float4 q = S.L1[c + u];
-        const float a = fmaf(q.z, x[2], fmaf(q.y, x[1], fmaf(q.x, x[0], q.w)));
-        const float da1 = dh[u] * gelu_grad_f(a);
-        v[4 * u] = da1 * x[0];
-        v[4 * u + 1] = da1 * x[1];
-        v[4 * u + 2] = da1 * x[2];
-        v[4 * u + 3] = da1;
+      for (int p = 0; p < 4; ++p) {
+        const float2 a = layer1_x2(S.L1, c / 2 + p, X0, X1, X2);
+        const float2 sg = gelu_sig_x2(a);
+        const float2 d = mul2(make_float2(dh[2 * p], dh[2 * p + 1]),
+                              gelu_grad_x2(a, sg, mul2(a, sg)));
+        if (p & 1) { da1[p >> 1].z = d.x; da1[p >> 1].w = d.y; }
+        else { da1[p >> 1].x = d.x; da1[p >> 1].y = d.y; }
       }
-      warp_reduce_scatter(v, lane);
-      // lane l holds element l: unit c + l/4, quantity l%4 (x0, x1, x2, bias)
-      {
-        const int i = c + (lane >> 2), f = lane & 3;
-        atomicAdd(f < 3 ? &S.small[3 * i + f] : &S.small[192 + i], v[0]);
+      *reinterpret_cast<float4*>(XVb + da1_off(t, c)) = da1[0];
+      *reinterpret_cast<float4*>(XVb + da1_off(t, c + 4)) = da1[1];
+    }
+    __syncthreads();
+    // dW1[iu][0..2], db1[iu] += sum over this parity's voxels of dA1 (x, 1)
+    {
+      const unsigned char* col = XVb + hv * 256;
+      const float4* xs = S.X + hv;
+#pragma unroll 4
+      for (int k = 0; k < kRows / 2; ++k) {
+        const float d = *reinterpret_cast<const float*>(col + k * 512 + coff[k & 3]);
+        const float4 xv = xs[2 * k];
+        g01 = fma2(dup2(d), make_float2(xv.x, xv.y), g01);
+        g23 = fma2(dup2(d), make_float2(xv.z, xv.w), g23);
       }
     }
     fence_before();
@@ -562,15 +728,21 @@ k_mlp_grad_tc(int M, int r2, float inv_n, const float* __restrict__ params,
       for (int u = 0; u < 16; ++u) atomicAdd(grad + oW2 + t * kHid + c + u, gv[u]);
     }
   }
+  // dW1, db1: the two voxel parities of unit iu, added by the even thread
+  g01.x += __shfl_xor_sync(0xffffffffu, g01.x, 1);
+  g01.y += __shfl_xor_sync(0xffffffffu, g01.y, 1);
+  g23.x += __shfl_xor_sync(0xffffffffu, g23.x, 1);
+  g23.y += __shfl_xor_sync(0xffffffffu, g23.y, 1);
+  if (ok && tiles_done > 0 && hv == 0) {
+    atomicAdd(grad + oW1 + 3 * iu, g01.x);
+    atomicAdd(grad + oW1 + 3 * iu + 1, g01.y);
+    atomicAdd(grad + oW1 + 3 * iu + 2, g23.x);
+    atomicAdd(grad + ob1 + iu, g23.y);
+  }
   __syncthreads();
-  for (int i = t; i < kSmall; i += kRows) {
+  for (int i = t; i < kSmallTc; i += kRows) {
     const float v = S.small[i];
-    int dst;
-    if (i < 192) dst = oW1 + i;
-    else if (i < 256) dst = ob1 + (i - 192);
-    else if (i < 320) dst = ob2 + (i - 256);
-    else if (i < 384) dst = ow3 + (i - 320);
-    else dst = ob3;
+    const int dst = i < kHid ? ob2 + i : (i < 2 * kHid ? ow3 + (i - kHid) : ob3);
     atomicAdd(grad + dst, v);
   }
   double s = block_sum(my_sse);
@@ -593,10 +765,11 @@ k_mlp_forward_ref(int M, const float* __restrict__ params, const float* __restri
   for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) W2[e] = bf16r(params[oW2 + e]);
   __syncthreads();
   const int n = M * M * M;
+  const FeatGrid G = feat_grid(M);
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     float x[3];
     bool inb;
-    features(j, M, cov, c2w, x, 0x7fffffff, inb);
+    features(j, G, __ldg(cov + j), __ldg(c2w + j), x, 0x7fffffff, inb);
     float h1[kHid];
 #pragma unroll
     for (int i = 0; i < kHid; ++i)
@@ -636,12 +809,13 @@ k_mlp_grad_ref(int M, int r2, float inv_n, const float* __restrict__ params,
   double my_sse = 0.0;
   __syncthreads();
   const int n = M * M * M;
+  const FeatGrid G = feat_grid(M);
   const int n_tiles = (n + kRows - 1) / kRows;
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int j = tile * kRows + t;
     float x[3] = {0.f, 0.f, 0.f};
     bool inb = false;
-    if (j < n) features(j, M, cov, c2w, x, r2, inb);
+    if (j < n) features(j, G, __ldg(cov + j), __ldg(c2w + j), x, r2, inb);
     float h1[kHid];
 #pragma unroll
     for (int i = 0; i < kHid; ++i) {
