@@ -10,6 +10,13 @@
 
 namespace cs {
 
+// Packed FP32 pairs (sm_100 family): one instruction performs two IEEE
+// round-to-nearest operations, each lane bit-identical to the scalar one.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
 // Kernel-side copy of the geometry.  The CTF phase (in units of pi) is
 //   chi/pi = a_i q - b q^2,  a_i = ka * defocus_i,
 // ka = lam / (M pix)^2 and b = Cs lam^3 / (2 (M pix)^4), prepared on the

@@ -155,15 +155,19 @@ __device__ __forceinline__ bool base_in(const Geo& G, const Cell& c) {
 
 // Corner weights of a cell whose base corner is inside the grid, k = dx +
 // 2 dy + 4 dz; corners past the grid's upper edge get weight 0.
+// The products are taken two at a time (packed pairs, the same roundings).
 __device__ __forceinline__ void cell_weights(const Geo& G, const Cell& c, float w8[8]) {
   const float wx1 = c.x0 + 1 < G.M ? c.tx : 0.f, wy1 = c.y0 + 1 < G.M ? c.ty : 0.f;
   const float wz1 = c.z0 + 1 < G.M ? c.tz : 0.f;
   const float wx0 = 1.f - c.tx, wy0 = 1.f - c.ty, wz0 = 1.f - c.tz;
-  const float wzy[4] = {wz0 * wy0, wz0 * wy1, wz1 * wy0, wz1 * wy1};
+  const float2 wy = make_float2(wy0, wy1), wx = make_float2(wx0, wx1);
+  const float2 z0 = mul2(dup2(wz0), wy), z1 = mul2(dup2(wz1), wy);
+  const float wzy[4] = {z0.x, z0.y, z1.x, z1.y};
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    w8[2 * r] = wzy[r] * wx0;
-    w8[2 * r + 1] = wzy[r] * wx1;
+    const float2 q = mul2(dup2(wzy[r]), wx);
+    w8[2 * r] = q.x;
+    w8[2 * r + 1] = q.y;
   }
 }
 
@@ -172,7 +176,7 @@ __device__ __forceinline__ float2 gather_pairs_w(const Geo& G, const Cell& c,
                                                  const float4* __restrict__ vp,
                                                  const float w8[8]) {
   const int M = G.M;
-  float re = 0.f, im = 0.f;
+  float2 acc = make_float2(0.f, 0.f);        // (re, im), packed pairs
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int y = c.y0 + (r & 1), z = c.z0 + (r >> 1);
@@ -180,10 +184,10 @@ __device__ __forceinline__ float2 gather_pairs_w(const Geo& G, const Cell& c,
     const size_t j = ((size_t)z * M + y) * M + c.x0;
     if (!CS_IN(j, (size_t)M * M * M)) continue;
     const float4 a = __ldg(vp + j);
-    re = fmaf(w8[2 * r], a.x, fmaf(w8[2 * r + 1], a.z, re));
-    im = fmaf(w8[2 * r], a.y, fmaf(w8[2 * r + 1], a.w, im));
+    acc = fma2(dup2(w8[2 * r]), make_float2(a.x, a.y),
+               fma2(dup2(w8[2 * r + 1]), make_float2(a.z, a.w), acc));
   }
-  return make_float2(re, im);
+  return acc;
 }
 
 // 32-byte load of one 2 x 2 (x, y) patch of complex values:
@@ -212,7 +216,7 @@ __device__ __forceinline__ float2 gather_patch_w(const Geo& G, const Cell& c,
                                                  const float4* __restrict__ dq,
                                                  const float w8[8]) {
   const int M = G.M;
-  float re = 0.f, im = 0.f;
+  float2 acc = make_float2(0.f, 0.f);        // (re, im), packed pairs
 #pragma unroll
   for (int dz = 0; dz < 2; ++dz) {
     const int z = c.z0 + dz;
@@ -222,10 +226,12 @@ __device__ __forceinline__ float2 gather_patch_w(const Geo& G, const Cell& c,
     float a[8];
     ld_patch(dq + 2 * j, a);
     const float* w = w8 + 4 * dz;
-    re = fmaf(w[0], a[0], fmaf(w[1], a[2], fmaf(w[2], a[4], fmaf(w[3], a[6], re))));
-    im = fmaf(w[0], a[1], fmaf(w[1], a[3], fmaf(w[2], a[5], fmaf(w[3], a[7], im))));
+    acc = fma2(dup2(w[0]), make_float2(a[0], a[1]),
+               fma2(dup2(w[1]), make_float2(a[2], a[3]),
+                    fma2(dup2(w[2]), make_float2(a[4], a[5]),
+                         fma2(dup2(w[3]), make_float2(a[6], a[7]), acc))));
   }
-  return make_float2(re, im);
+  return acc;
 }
 
 // per-corner gather from the patch layout (element 0 of patch j is d[j]);
@@ -279,7 +285,8 @@ __device__ __forceinline__ void scatter_c2_w(const Geo& G, const Cell& c, float2
     const size_t j = ((size_t)z * M + y) * M + xb;
     if (!CS_IN(j + 1, (size_t)M * M * M)) continue;     // the pair (j, j + 1)
     float4* p = reinterpret_cast<float4*>(base + j);
-    red_add_keep(p, make_float4(a0 * val.x, a0 * val.y, a1 * val.x, a1 * val.y), pol);
+    const float2 q0 = mul2(dup2(a0), val), q1 = mul2(dup2(a1), val);
+    red_add_keep(p, make_float4(q0.x, q0.y, q1.x, q1.y), pol);
   }
 }
 
@@ -619,11 +626,11 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
         r = make_float2(fmaf(C, a.x, -r.x), fmaf(C, a.y, -r.y));
         acc = fmaf(r.x, r.x, fmaf(r.y, r.y, acc));
       }
-      const float sc = A.scale * C;
+      const float2 sr = mul2(dup2(A.scale * C), r);
       if (inb)
-        scatter_c2_w(G, c, make_float2(sc * r.x, sc * r.y), A.E, A.O, w8, pol);
+        scatter_c2_w(G, c, sr, A.E, A.O, w8, pol);
       else
-        scatter_cell_c2(G, c, make_float2(sc * r.x, sc * r.y), A.E, A.O);
+        scatter_cell_c2(G, c, sr, A.E, A.O);
     }
     if (FL & F_CURV) {
       const float2 a = inb ? gather_patch_w(G, c, A.dq, w8) : gather_cell_patch_slow(G, c, A.dq);
@@ -698,7 +705,12 @@ __device__ __forceinline__ float fused_traverse(const FusedArgs& A, int blk, int
       }
       float vals[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) vals[j] = sc * w8[j] * fmaf(-2.0f * invK, S[j], wsum);
+      for (int j = 0; j < 8; j += 2) {
+        const float2 v = mul2(mul2(dup2(sc), make_float2(w8[j], w8[j + 1])),
+                              fma2(dup2(-2.0f * invK), make_float2(S[j], S[j + 1]), dup2(wsum)));
+        vals[j] = v.x;
+        vals[j + 1] = v.y;
+      }
       scatter_cell_r4(G, c, vals, A.P, pol);
     }
   }
@@ -759,7 +771,8 @@ k_pairs(int M, const float2* __restrict__ v, float4* __restrict__ vp) {
 }
 
 // Set-up of a step's traversal in one pass over the voxels: E = O = 0,
-// the four patch buffers P = 0 (zero_p), vp = pair layout of v.  Thread q
+// the four patch buffers P = 0 (zero_p), vp = pair layout of v, all written
+// under the policy that keeps them in L2 for the traversal that follows.  Thread q
 // handles voxels q + k n/4, k = 0..3 (M is even, so n = M^3 is a multiple of
 // 4): the zeroing is done with 16-byte stores, and every access of a warp
 // stays contiguous across its lanes.
@@ -790,7 +803,8 @@ k_step_prep(int M, const float2* __restrict__ v, float2* __restrict__ E, float2*
       c[k] = (j % M) != M - 1 ? v[j + 1] : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) vp[q + k * n4] = make_float4(a[k].x, a[k].y, c[k].x, c[k].y);
+    for (int k = 0; k < 4; ++k)
+      st_keep(vp + q + k * n4, make_float4(a[k].x, a[k].y, c[k].x, c[k].y), pol);
   }
 }
 

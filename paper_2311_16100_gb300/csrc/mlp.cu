@@ -69,17 +69,12 @@ __device__ __forceinline__ unsigned short bf16bits(float x) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
-// ---- packed FP32 pairs (sm_100 family): one instruction performs two IEEE
-// round-to-nearest operations, each lane bit-identical to the scalar one.
-// The tensor-core kernels evaluate units two at a time with these: the
-// scalar work around the MMAs (the activations and their derivatives) is
-// what bounds them, and pairing halves its instruction count.
+// ---- the activations of two units at once, with the packed FP32 pairs of
+// device.cuh (fma2 and kin): the scalar work around the MMAs (the
+// activations and their derivatives) is what bounds the tensor-core
+// kernels, and pairing halves its instruction count.
 constexpr float kGc = 0.7978845608028654f;       // sqrt(2/pi)
 constexpr float kGc3 = 0.7978845608028654f * 0.044715f;
-__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 tanh2(float2 u) { return make_float2(tanh_hw(u.x), tanh_hw(u.y)); }
 // 2 GELU(x) = x + x tanh(u) of both lanes: five operations.  Exactly twice
 // gelu_f (a power of two scales every rounding alike); the forward kernel
