@@ -45,13 +45,24 @@ def gelu_grad(x):
     return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * c * (1.0 + 3 * 0.044715 * x * x)
 
 
-def features(M, coverage, ctf2w):
-    """Per-voxel features [M^3][3]: |k| / (M/2), log1p(coverage), log1p(sum C^2 w)."""
-    k = np.arange(M) - M // 2
-    kr = np.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2)
-    f = np.stack([kr.ravel() / (M / 2), np.log1p(np.asarray(coverage, np.float64).ravel()),
-                  np.log1p(np.asarray(ctf2w, np.float64).ravel())], axis=1)
-    return f
+def features(M, coverage, ctf2w, idx=None):
+    """Per-voxel features [M^3][3]: |k| / (M/2), log1p(coverage), log1p(sum C^2 w);
+    with idx, only the voxels of those linear indices (z-major: j = (z M + y) M + x)."""
+    if idx is None:
+        k = np.arange(M) - M // 2
+        kr = np.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2)
+        kr = kr.ravel()
+        cov = np.asarray(coverage, np.float64).ravel()
+        c2w = np.asarray(ctf2w, np.float64).ravel()
+    else:
+        j = np.asarray(idx, np.int64)
+        kx = j % M - M // 2
+        ky = (j // M) % M - M // 2
+        kz = j // (M * M) - M // 2
+        kr = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+        cov = np.asarray(coverage).ravel()[j].astype(np.float64)
+        c2w = np.asarray(ctf2w).ravel()[j].astype(np.float64)
+    return np.stack([kr / (M / 2), np.log1p(cov), np.log1p(c2w)], axis=1)
 
 
 def init_params(seed):

@@ -154,6 +154,28 @@ def test_network_forward_multi_tile(hn, tc, M, sample):
 
 
 @pytest.mark.parametrize("tc", [True, False])
+@pytest.mark.parametrize("M", [250, 510])
+def test_network_forward_large_grid_sampled(hn, tc, M):
+    """Grids whose voxel indices exceed 2^24 (510^3) or are not powers of two
+    (250): the kernels take a voxel's coordinates from a float reciprocal of
+    M with one correction step; 40 000 sampled voxels against the oracle."""
+    g = np.random.default_rng(500 + M)
+    cov = (g.random((M, M, M), dtype=np.float32) * 800).astype(np.float32)
+    c2w = (g.random((M, M, M), dtype=np.float32) * 300).astype(np.float32)
+    from paper_2311_16100_gb300.learned import init_params
+    P = init_params(M)
+    d = torch.device("cuda")
+    y = hn.mlp_forward(M, torch.from_numpy(P).to(d), torch.from_numpy(cov).to(d),
+                       torch.from_numpy(c2w).to(d), tensor_cores=tc)
+    hn.check_device_status()
+    # the sample includes the grid's last voxels (the largest indices)
+    idx = np.concatenate([g.choice(M ** 3, size=40000, replace=False),
+                          np.arange(M ** 3 - 256, M ** 3)])
+    yo, _ = mlp.forward(_as_dict(P), mlp.features(M, cov, c2w, idx))
+    assert rel_l2(y.cpu().numpy().ravel()[idx], yo) <= 1e-3
+
+
+@pytest.mark.parametrize("tc", [True, False])
 def test_network_gradient_multi_tile(hn, tc):
     M, r = 64, 31
     cov, c2w, tgt, P = _net_inputs(M, 400)

@@ -717,3 +717,15 @@ def test_hutchinson_rows_equal_the_full_estimate(interp):
                           [((M // 2) * M + M // 2) * M + M // 2]])
     rows = O.hutchinson_diag_at(sel, R, df, M, r, interp, CTF, lam, scale, K, 21, 4)
     np.testing.assert_allclose(rows, full[sel], rtol=1e-12, atol=1e-12)
+
+
+def test_network_features_at_selected_voxels_equal_the_full_grid():
+    """features(..., idx) takes voxels by linear index (z-major) and gives the
+    rows of the whole-grid features."""
+    M = 10
+    g = np.random.default_rng(7)
+    cov, c2w = g.uniform(0, 50, (M, M, M)), g.uniform(0, 5, (M, M, M))
+    X = O.mlp.features(M, cov, c2w)
+    idx = np.concatenate([g.choice(M ** 3, 40, replace=False), [0, M ** 3 - 1]])
+    np.testing.assert_array_equal(O.mlp.features(M, cov, c2w, idx), X[idx])
+
