@@ -863,7 +863,7 @@ k_combine_r4(int M, float* __restrict__ P, float base, float coef,
 //   HUTCH: D_est = lambda + patches; D_avg = ((k-1)/k) D_avg + D_est/k;
 //          D = beta D + (1-beta) D_avg; D-hat = max(|D|, alpha)
 //   FIXED: D-hat = max(|D|, alpha);  PLAIN: D-hat = 1
-//   g = lambda v + E + shift(O);  d = g / D-hat, written in pair layout;
+//   g = lambda v + E + shift(O);  d = g / D-hat, written in natural layout (dn);
 //   partials of |g|^2/D-hat, |d|^2 and |v|^2.
 __global__ void __launch_bounds__(256)
 k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float beta,

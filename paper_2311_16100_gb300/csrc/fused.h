@@ -85,7 +85,8 @@ cudaError_t launch_disc_table(int M, int r, const FusedWs& w, cudaStream_t s);
 // pixels outside the disc are -1; w.tile_org[ch] is chunk ch's origin.
 cudaError_t launch_disc_table_tiled(int M, int r, int block, const FusedWs& w, cudaStream_t s);
 // One trilinear traversal with the given flags (partials: one per block).
-// vol: natural layout, vp: its pair layout (F_GRAD, F_CURV); probe words
+// vol: natural layout, vp: its pair layout (F_GRAD; F_CURV reads the patch
+// layout of the direction, w.dq, written by launch_patches); probe words
 // (F_HUTCH) come from (seed, block), block = *k_dev + 1 when k_dev != NULL.
 // block = threads per block (128 or 256); slabs = z-slabs (one launch each;
 // 0: slab_count).
