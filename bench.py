@@ -117,12 +117,18 @@ KERNEL_SOURCES = {
 
 
 def kernel_source_hash(kernel="loss_grad"):
+    """Hash of the code of the kernel's sources: line comments, trailing
+    blanks and empty lines are left out, so that a comment edit keeps the
+    recorded counters valid and any code edit voids them."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2311_16100_gb300", "csrc")
     files = KERNEL_SOURCES.get(kernel) or sorted(
         f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
     for f in files:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        for line in open(os.path.join(csrc, f), encoding="utf-8"):
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
