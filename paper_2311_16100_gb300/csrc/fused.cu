@@ -865,6 +865,17 @@ k_combine_r4(int M, float* __restrict__ P, float base, float coef,
 //   FIXED: D-hat = max(|D|, alpha);  PLAIN: D-hat = 1
 //   g = lambda v + E + shift(O);  d = g / D-hat, written in natural layout (dn);
 //   partials of |g|^2/D-hat, |d|^2 and |v|^2.
+// A thread takes a 2 x 2 (x, y) block of voxels of one z-plane (x, y even):
+// the block is one patch of the patch buffer with even origin, two patches
+// of each buffer with one odd origin coordinate and four of the buffer with
+// both odd, so the buffers are read as whole 16-byte patches; the natural
+// layouts are read and written as aligned pairs of voxels along x.  The
+// patch sums of a voxel are added in the order (0,0), (1,0), (0,1), (1,1) of
+// the buffers' origin parities.
+__device__ __forceinline__ float4 ld_patch4(const float* __restrict__ buf, size_t patch) {
+  return *reinterpret_cast<const float4*>(buf + 4 * patch);
+}
+
 __global__ void __launch_bounds__(256)
 k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float beta,
             const double* __restrict__ sc, float2* __restrict__ E, float2* __restrict__ O,
@@ -872,8 +883,9 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
             float2* __restrict__ dn, double* __restrict__ partG, double* __restrict__ partV,
             int nb) {
   grid_dep_wait();
-  const int n = M * M * M, Mh = M / 2;
-  const size_t nbuf = (size_t)n;
+  const int Mh = M / 2;
+  const size_t nbuf = (size_t)M * M * M;
+  const int nblk = Mh * Mh * M;
   const double k = sc[CS_S_K] + 1.0;
   const float wold = (float)((k - 1.0) / k), wnew = (float)(1.0 / k);
   const float alpha = (float)sc[CS_S_ALPHA];
@@ -881,46 +893,100 @@ k_step_post(int M, int mode, const float2* __restrict__ v, float lambda, float b
   // small fraction of the FP32 rate), warp sums in FP32, the block's warp
   // sums added in FP64
   float aG = 0.f, aD = 0.f, aV = 0.f;
-  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
-    const int x = j % M, y = (j / M) % M, z = j / (M * M);
-    float dh = 1.0f;
+  for (int bi = blockIdx.x * 256 + threadIdx.x; bi < nblk; bi += gridDim.x * 256) {
+    const int X = bi % Mh, Y = (bi / Mh) % Mh, z = bi / (Mh * Mh);
+    const int x = 2 * X, y = 2 * Y;
+    const size_t j0 = ((size_t)z * M + y) * M + x;       // (x, y); row y + 1 at j0 + M
+    const size_t jr[2] = {j0, j0 + M};
+    // voxel order within the block: (x, y), (x+1, y), (x, y+1), (x+1, y+1)
+    float dh[4] = {1.f, 1.f, 1.f, 1.f};
     if (mode == CS_HUTCHINSON) {
-      float e = lambda;
-#pragma unroll
-      for (int py = 0; py < 2; ++py) {
-#pragma unroll
-        for (int px = 0; px < 2; ++px) {
-          const int xx = x - px, yy = y - py;
-          if (xx < 0 || yy < 0) continue;
-          float* buf = P + (size_t)(py * 2 + px) * nbuf;
-          const size_t slot =
-              4 * (((size_t)z * Mh + (yy >> 1)) * Mh + (xx >> 1)) + 2 * (yy & 1) + (xx & 1);
-          e += buf[slot];
-        }
+      const size_t pz = (size_t)z * Mh;
+      const size_t pXY = (pz + Y) * Mh + X;                // patch (X, Y)
+      float e[4] = {lambda, lambda, lambda, lambda};
+      {   // origin parity (0, 0): patch (X, Y)
+        const float4 p = ld_patch4(P, pXY);
+        e[0] += p.x; e[1] += p.y; e[2] += p.z; e[3] += p.w;
       }
-      const float a = fmaf(wold, Davg[j], wnew * e);
-      const float d = fmaf(beta, D[j], (1.0f - beta) * a);
-      Davg[j] = a;
-      D[j] = d;
-      dh = fmaxf(fabsf(d), alpha);
+      {   // (1, 0): patches (X-1, Y) (elements 1, 3) and (X, Y) (0, 2)
+        const float* buf = P + nbuf;
+        const float4 r = ld_patch4(buf, pXY);
+        if (X > 0) {
+          const float4 l = ld_patch4(buf, pXY - 1);
+          e[0] += l.y;
+          e[2] += l.w;
+        }
+        e[1] += r.x;
+        e[3] += r.z;
+      }
+      {   // (0, 1): patches (X, Y-1) (elements 2, 3) and (X, Y) (0, 1)
+        const float* buf = P + 2 * nbuf;
+        if (Y > 0) {
+          const float4 u = ld_patch4(buf, pXY - Mh);
+          e[0] += u.z;
+          e[1] += u.w;
+        }
+        const float4 w = ld_patch4(buf, pXY);
+        e[2] += w.x;
+        e[3] += w.y;
+      }
+      {   // (1, 1): patches (X-1, Y-1) (3), (X, Y-1) (2), (X-1, Y) (1), (X, Y) (0)
+        const float* buf = P + 3 * nbuf;
+        if (Y > 0) {
+          if (X > 0) e[0] += ld_patch4(buf, pXY - Mh - 1).w;
+          e[1] += ld_patch4(buf, pXY - Mh).z;
+        }
+        if (X > 0) e[2] += ld_patch4(buf, pXY - 1).y;
+        e[3] += ld_patch4(buf, pXY).x;
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const float2 da = *reinterpret_cast<const float2*>(Davg + jr[r]);
+        const float2 dd = *reinterpret_cast<const float2*>(D + jr[r]);
+        const float a0 = fmaf(wold, da.x, wnew * e[2 * r]);
+        const float a1 = fmaf(wold, da.y, wnew * e[2 * r + 1]);
+        const float d0 = fmaf(beta, dd.x, (1.0f - beta) * a0);
+        const float d1 = fmaf(beta, dd.y, (1.0f - beta) * a1);
+        *reinterpret_cast<float2*>(Davg + jr[r]) = make_float2(a0, a1);
+        *reinterpret_cast<float2*>(D + jr[r]) = make_float2(d0, d1);
+        dh[2 * r] = fmaxf(fabsf(d0), alpha);
+        dh[2 * r + 1] = fmaxf(fabsf(d1), alpha);
+      }
     } else if (mode == CS_FIXED) {
-      dh = fmaxf(fabsf(D[j]), alpha);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const float2 dd = *reinterpret_cast<const float2*>(D + jr[r]);
+        dh[2 * r] = fmaxf(fabsf(dd.x), alpha);
+        dh[2 * r + 1] = fmaxf(fabsf(dd.y), alpha);
+      }
     }
-    const float2 vv = v[j];
-    float2 g = E[j];
-    if (x >= 1) {
-      const float2 o = O[j - 1];
-      g.x += o.x;
-      g.y += o.y;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const size_t j = jr[r];
+      const float4 vv = *reinterpret_cast<const float4*>(v + j);
+      float4 g = *reinterpret_cast<const float4*>(E + j);
+      if (x >= 1) {
+        const float2 o = O[j - 1];
+        g.x += o.x;
+        g.y += o.y;
+      }
+      const float2 o1 = O[j];
+      g.z += o1.x;
+      g.w += o1.y;
+      g.x = fmaf(lambda, vv.x, g.x);
+      g.y = fmaf(lambda, vv.y, g.y);
+      g.z = fmaf(lambda, vv.z, g.z);
+      g.w = fmaf(lambda, vv.w, g.w);
+      const float i0 = 1.0f / dh[2 * r], i1 = 1.0f / dh[2 * r + 1];
+      const float4 d = make_float4(g.x * i0, g.y * i0, g.z * i1, g.w * i1);
+      *reinterpret_cast<float4*>(dn + j) = d;
+      aG += fmaf(g.x, g.x, g.y * g.y) * i0;
+      aG += fmaf(g.z, g.z, g.w * g.w) * i1;
+      aD += fmaf(d.x, d.x, d.y * d.y);
+      aD += fmaf(d.z, d.z, d.w * d.w);
+      aV += fmaf(vv.x, vv.x, vv.y * vv.y);
+      aV += fmaf(vv.z, vv.z, vv.w * vv.w);
     }
-    g.x = fmaf(lambda, vv.x, g.x);
-    g.y = fmaf(lambda, vv.y, g.y);
-    const float inv = 1.0f / dh;
-    const float2 d = make_float2(g.x * inv, g.y * inv);
-    dn[j] = d;
-    aG += fmaf(g.x, g.x, g.y * g.y) * inv;
-    aD += fmaf(d.x, d.x, d.y * d.y);
-    aV += fmaf(vv.x, vv.x, vv.y * vv.y);
   }
   const double tG = block_sum_f(aG);
   const double tD = block_sum_f(aD);
@@ -1268,7 +1334,7 @@ cudaError_t launch_step_post(int M, int mode, const float2* v, float lambda, flo
                              const double* scalars, const FusedWs& w, float* D, float* Davg,
                              double* partG, double* partV, int* nb, int num_sms,
                              cudaStream_t s) {
-  const int g = elem_grid(M * M * M, num_sms);
+  const int g = elem_grid(M * M * M / 4, num_sms);     // a thread per 2 x 2 block
   *nb = g;
   const cudaError_t e = launch_pdl(k_step_post, g, 256, s, M, mode, v, lambda, beta, scalars,
                                    w.E, w.O, w.P, D, Davg, w.dn, partG, partV, g);

@@ -60,6 +60,22 @@ namespace cs {
 extern std::atomic<uint64_t> g_launches;
 inline void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
+// Dynamic shared memory limit of a kernel, raised once per device: the
+// attribute belongs to the kernel on the current device, so a process that
+// uses several GPUs sets it on each (done: one bit per device below 64;
+// devices past that set it at every call).
+template <typename K>
+cudaError_t ensure_smem_limit(K* kernel, int bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
 // Launch with programmatic stream serialisation: the kernel's blocks may be
 // scheduled while the previous kernel in the stream finishes; the kernel
 // must call grid_dep_wait() before its first access to memory.

@@ -135,9 +135,8 @@ __device__ __forceinline__ int div_grid(int a, int d, float inv_d, int* rem) {
   return q;
 }
 // features of voxel j (cov_j, c2w_j: its inputs); in_ball: |k|^2 <= r2.
-// log1p(c) for c >= 0 as the
-// hardware logarithm of 1 + c (absolute error a few 1e-7: far below the
-// BF16 rounding of the first hidden layer)
+// log1p(c) for c >= 0 as the hardware logarithm of 1 + c (absolute error a
+// few 1e-7: far below the BF16 rounding of the first hidden layer)
 __device__ __forceinline__ void features(int j, const FeatGrid& G, float cov_j, float c2w_j,
                                          float x[3], int r2, bool& in_ball) {
   int ix, iy;
@@ -980,13 +979,10 @@ cudaError_t launch_mlp_forward(int M, const float* params, const float* cov, con
     count_launches(1);
     return cudaGetLastError();
   }
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_tc,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(FwdSmem));
+  static std::atomic<uint64_t> configured{0};
+  {
+    const cudaError_t e = ensure_smem_limit(k_mlp_forward_tc, (int)sizeof(FwdSmem), configured);
     if (e != cudaSuccess) return e;
-    configured = true;
   }
   // eight CTAs per SM: 8 x 64 TMEM columns, the whole tensor memory
   const int tiles = (n + kRows - 1) / kRows;
@@ -1004,24 +1000,20 @@ cudaError_t launch_mlp_grad(int M, int r2, float inv_n, const float* params, con
   const int tiles = (n + kRows - 1) / kRows;
   if (!tc) {
     const size_t dyn = sizeof(float) * (kHid * kHid + 2 * kRows * (kHid + 1));
-    static bool configured_ref = false;
-    if (!configured_ref) {
-      cudaError_t e = cudaFuncSetAttribute(k_mlp_grad_ref,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    static std::atomic<uint64_t> configured_ref{0};
+    {
+      const cudaError_t e = ensure_smem_limit(k_mlp_grad_ref, (int)dyn, configured_ref);
       if (e != cudaSuccess) return e;
-      configured_ref = true;
     }
     const int g = tiles < num_sms * 2 ? tiles : num_sms * 2;
     k_mlp_grad_ref<<<g, kRows, dyn, s>>>(M, r2, inv_n, params, cov, c2w, target, grad, sse);
     count_launches(1);
     return cudaGetLastError();
   }
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kGradSmemBytes);
+  static std::atomic<uint64_t> configured{0};
+  {
+    const cudaError_t e = ensure_smem_limit(k_mlp_grad_tc, (int)kGradSmemBytes, configured);
     if (e != cudaSuccess) return e;
-    configured = true;
   }
   // four CTAs per SM: 4 x 128 TMEM columns, the whole tensor memory
   const int g = tiles < num_sms * 4 ? tiles : num_sms * 4;

@@ -452,19 +452,20 @@ k_tile(TileArgs A) {
 template <int OP, int I>
 cudaError_t launch_engine(const TileArgs& A, int num_sms, cudaStream_t s) {
   constexpr size_t sm = smem_bytes<OP>();
-  static bool configured = false;
-  static int blocks_per_sm = 1;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_tile<OP, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+  // the shared-memory limit per device; the residency once (every device
+  // of a process is the same GB300)
+  static std::atomic<uint64_t> configured{0};
+  static std::atomic<int> blocks_per_sm{0};
+  cudaError_t e = ensure_smem_limit(k_tile<OP, I>, (int)sm, configured);
+  if (e != cudaSuccess) return e;
+  int bps = blocks_per_sm.load(std::memory_order_acquire);
+  if (bps < 1) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_tile<OP, I>, kTileThreads, sm);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_tile<OP, I>,
-                                                      kTileThreads, sm);
-    if (e != cudaSuccess) return e;
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-    configured = true;
+    if (bps < 1) bps = 1;
+    blocks_per_sm.store(bps, std::memory_order_release);
   }
-  k_tile<OP, I><<<num_sms * blocks_per_sm, kTileThreads, sm, s>>>(A);
+  k_tile<OP, I><<<num_sms * bps, kTileThreads, sm, s>>>(A);
   count_launches(1);
   return cudaGetLastError();
 }
