@@ -93,19 +93,23 @@ def test_gpu_arm_record_is_compact_and_complete():
     cfg = dict(bench.CONFIGS["m128"])
     tte = {"m32_nearest": _stub_race(["plain", "precomputed", "hutchinson"]),
            "m64_trilinear_ctf": _stub_race(["plain", "precomputed", "hutchinson"])}
-    learned = {"time_to_rel_err_64_snr10_b4096": _stub_race(
-        ["plain", "precomputed", "hutchinson", "learned", "exact_diagonal_control"])}
+    race64 = _stub_race(["plain", "precomputed", "hutchinson", "learned",
+                         "exact_diagonal_control"])
+    race64["setup_ms"] = {"learned": 1.234, "exact_diagonal_control": 4.56,
+                          "precomputed": 78.9}
+    learned = {"time_to_rel_err_64_snr10_b4096": race64}
     cpu = {"value": 72.6, "unit": "images/s", "cores": 16, "kind": "oracle",
            "sample": "one Algorithm-1 step of the FP64 numpy oracle per host core, "
                      "16 images each of the 128^3 workload, 16 single-threaded replicas "
                      "started together, 22.0 s wall",
-           "sample_short": "one literal Algorithm-1 step of the FP64 oracle per core, "
-                           "16 images each, 16 replicas, 22.0 s",
+           "sample_short": "FP64 oracle: one literal Algorithm-1 step of 16 images per core, "
+                           "16 replicas, 22.0 s",
            "single_core": {"value": 10.8}, "operators_single_core": {"x": [1] * 500}}
     m2 = bench.metric2_summary(tte, learned)
     line = bench.contract_line(args, cfg, 1, _stub_gpu_result(), cpu, m2)
     text = json.dumps(line)
-    assert len(text) < 2048, len(text)
+    # under 2 KB with room for the live figures' longer numbers
+    assert len(text) < 1950, len(text)
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
               "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
               "roofline", "roofline_l2_reductions", "e2e", "cpu_baseline", "clocks",
@@ -121,7 +125,10 @@ def test_gpu_arm_record_is_compact_and_complete():
     assert "50000 images" in line["config"]["workload"]
     assert line["config"]["images_in_hbm_per_gpu"] == 50000
     assert set(m2) == {"m32_snr0.1", "m64_snr0.05", "m64_snr10_b4096"}
-    assert m2["m64_snr10_b4096"]["learned"] == [0.1235, 139.4]
+    # fixed-D arms carry their set-up time third; the others have none
+    assert m2["m64_snr10_b4096"]["learned"] == [0.1235, 139.4, 1.2]
+    assert m2["m64_snr10_b4096"]["pre"][2] == 78.9
+    assert len(m2["m64_snr10_b4096"]["alg1"]) == 2 and len(m2["m32_snr0.1"]["pre"]) == 2
     assert len(json.dumps(m2)) < 600
 
 
