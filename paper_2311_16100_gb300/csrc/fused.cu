@@ -770,41 +770,51 @@ k_pairs(int M, const float2* __restrict__ v, float4* __restrict__ vp) {
   }
 }
 
+// one 32-byte store of eight floats under an L2 policy
+__device__ __forceinline__ void st_keep8(float* p, float4 a, float4 b, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8}, %9;"
+               :: "l"(p), "f"(a.x), "f"(a.y), "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z),
+                  "f"(b.w), "l"(pol) : "memory");
+}
+
 // Set-up of a step's traversal in one pass over the voxels: E = O = 0,
 // the four patch buffers P = 0 (zero_p), vp = pair layout of v, all written
-// under the policy that keeps them in L2 for the traversal that follows.  Thread q
-// handles voxels q + k n/4, k = 0..3 (M is even, so n = M^3 is a multiple of
-// 4): the zeroing is done with 16-byte stores, and every access of a warp
-// stays contiguous across its lanes.
+// under the policy that keeps them in L2 for the traversal that follows.
+// With n = M^3 (a multiple of 8), thread q < n/4 writes 32-byte chunk q of
+// E and of O (four voxels each), chunks q and q + n/4 of the patch buffers
+// (n/2 chunks in all) and of the pair layout (two voxels per chunk): every
+// store covers a whole sector, and a warp's stores are contiguous.
 __global__ void __launch_bounds__(256)
 k_step_prep(int M, const float2* __restrict__ v, float2* __restrict__ E, float2* __restrict__ O,
             float* __restrict__ P, float4* __restrict__ vp, int zero_p) {
   grid_dep_wait();
   const int n = M * M * M, n4 = n / 4;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4* E4 = reinterpret_cast<float4*>(E);
-  float4* O4 = reinterpret_cast<float4*>(O);
-  float4* P4 = reinterpret_cast<float4*>(P);
+  float* Ef = reinterpret_cast<float*>(E);
+  float* Of = reinterpret_cast<float*>(O);
+  float* vpf = reinterpret_cast<float*>(vp);
   const uint64_t pol = l2_keep_policy();     // the accumulators stay in L2
   for (int q = blockIdx.x * 256 + threadIdx.x; q < n4; q += gridDim.x * 256) {
-    st_keep(E4 + q, z4, pol);
-    st_keep(E4 + q + n4, z4, pol);
-    st_keep(O4 + q, z4, pol);
-    st_keep(O4 + q + n4, z4, pol);
+    st_keep8(Ef + 8 * (size_t)q, z4, z4, pol);
+    st_keep8(Of + 8 * (size_t)q, z4, z4, pol);
     if (zero_p) {
-#pragma unroll
-      for (int b = 0; b < 4; ++b) st_keep(P4 + q + b * n4, z4, pol);
+      st_keep8(P + 8 * (size_t)q, z4, z4, pol);
+      st_keep8(P + 8 * ((size_t)q + n4), z4, z4, pol);
     }
-    float2 a[4], c[4];
+    float4 a[2];
+    float2 c[2];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int j = q + k * n4;
-      a[k] = v[j];
-      c[k] = (j % M) != M - 1 ? v[j + 1] : make_float2(0.f, 0.f);
+    for (int k = 0; k < 2; ++k) {
+      const int j = 2 * (q + k * n4);          // voxels j, j + 1 (j even)
+      a[k] = *reinterpret_cast<const float4*>(v + j);
+      c[k] = ((j + 1) % M) != M - 1 ? v[j + 2] : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      st_keep(vp + q + k * n4, make_float4(a[k].x, a[k].y, c[k].x, c[k].y), pol);
+    for (int k = 0; k < 2; ++k) {
+      const int j = 2 * (q + k * n4);
+      // (v[j], v[j+1]) and (v[j+1], v[j+2]); x = M - 1 at j + 1 reads 0
+      st_keep8(vpf + 4 * (size_t)j, a[k], make_float4(a[k].z, a[k].w, c[k].x, c[k].y), pol);
+    }
   }
 }
 
