@@ -132,3 +132,50 @@ def test_disc_packed_host_steps_match_device_steps(algo):
     h_host.check_device_status()
     h_dev.close()
     h_host.close()
+
+
+def test_disc_packed_host_steps_full_size():
+    """The benchmark's end-to-end path at its size: 128^3, batches of 1024
+    images given as their disc pixels in pinned host memory, trilinear + CTF,
+    32 probes; two steps give the iterates of the same steps on the full
+    images held on the device (inputs made on the device: a random volume,
+    its slices plus noise)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_16100_gb300 import ops, synth
+    M, r, B, nb, lam = 128, 63, 1024, 2, 0.01
+    N = B * nb
+    geom = ops.Geometry(M, r, "trilinear", ops.CTF())
+    h_dev, h_host = ops.Handle(0), ops.Handle(0)
+    vol = torch.from_numpy(synth.complex_normal((M, M, M), 91, 1.0).astype(np.complex64)).cuda()
+    quat = torch.from_numpy(synth.shoemake_quaternions(N, 92).astype(np.float32))
+    df = torch.from_numpy(synth.defocus_angstrom(N, 93).astype(np.float32))
+    rot_all = h_dev.quat_to_rot(quat.cuda())
+    images = h_dev.slice_project(geom, vol, rot_all, df.cuda())
+    gen = torch.Generator(device="cuda").manual_seed(94)
+    images = images + 0.3 * torch.complex(torch.randn(images.shape, generator=gen, device="cuda"),
+                                          torch.randn(images.shape, generator=gen, device="cuda"))
+    alpha = float(h_dev.threshold_alpha(geom, df.cuda(), N, lam))
+    states = [ops.SGDState((0.3 * vol).contiguous(), mode="hutchinson", alpha=alpha, eta0=1.0,
+                           beta=0.9, armijo_c=0.5, n_probes=32, seed=95) for _ in range(2)]
+    st_dev, st_host = states
+    disc = ops.pack_disc(images.cpu(), r).pin_memory()
+    qh, dfh = quat.pin_memory(), df.pin_memory()
+    losses = torch.zeros(nb, dtype=torch.float64).pin_memory()
+    dev_losses = []
+    for k in range(nb):
+        sl = slice(k * B, (k + 1) * B)
+        h_host.precond_sgd_step_host_disc(geom, st_host, disc[sl], qh[sl], dfh[sl], lam,
+                                          float(nb), loss_host=losses[k])
+        h_dev.precond_sgd_step(geom, st_dev, images[sl].contiguous(), rot_all[sl].contiguous(),
+                               df[sl].cuda(), lam, float(nb))
+        dev_losses.append(st_dev.scalars[3].clone())
+    torch.cuda.synchronize()
+    assert rel_l2(st_host.v.cpu().numpy(), st_dev.v.cpu().numpy()) <= 1e-6
+    assert rel_l2(st_host.D.cpu().numpy(), st_dev.D.cpu().numpy()) <= 1e-6
+    assert float(st_host.scalars[0]) == float(st_dev.scalars[0])
+    for k in range(nb):
+        assert abs(float(losses[k]) - float(dev_losses[k])) <= 1e-6 * abs(float(dev_losses[k]))
+    h_host.check_device_status()
+    h_dev.close()
+    h_host.close()
