@@ -254,7 +254,7 @@ __device__ __forceinline__ float2 gather_cell_patch_slow(const Geo& G, const Cel
 }
 
 // L2 policy that keeps lines (the accumulators) in L2 ahead of others, and
-// a 16-byte reduction / store under it
+// a 16-byte reduction under it
 __device__ __forceinline__ uint64_t l2_keep_policy() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
@@ -262,10 +262,6 @@ __device__ __forceinline__ uint64_t l2_keep_policy() {
 }
 __device__ __forceinline__ void red_add_keep(float4* p, float4 v, uint64_t pol) {
   asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
-               :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
-}
-__device__ __forceinline__ void st_keep(float4* p, float4 v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
                :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
 }
 

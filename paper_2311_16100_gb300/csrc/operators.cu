@@ -243,7 +243,7 @@ k_hutchinson(Geo G, const uint32_t* __restrict__ bits, const float* __restrict__
     make_stencil<I>(G, R, it.kx, it.ky, S);
     float C = image_ctf(G, df, it.b, it.q);
     const float sc = scale * C * C;
-    const int nv = G.M * G.M * G.M;
+    [[maybe_unused]] const int nv = G.M * G.M * G.M;   // range checks (debug build)
     if (I == 0) {
       if (S.w[0] != 0.0f && CS_IN(S.idx[0], nv)) atomicAdd(diag + S.idx[0], sc);
       continue;
