@@ -239,11 +239,16 @@ def test_threshold_alpha(h):
                                            ("plain", "trilinear", 24),
                                            ("hutchinson", "nearest", 24),
                                            ("fixed", "trilinear", 24),
-                                           ("hutchinson", "trilinear", 26)])
+                                           ("hutchinson", "trilinear", 26),
+                                           ("hutchinson", "trilinear", 4),
+                                           ("hutchinson", "trilinear", 6),
+                                           ("fixed", "trilinear", 10)])
 def test_precond_sgd_steps_follow_oracle(h, mode, interp, M):
     """Three iterations of Algorithm 1 on consecutive mini-batches: the same
     eta choices as the literal oracle loop and iterates within tolerance
-    (M = 26: x rows of a length that is not a multiple of 4)."""
+    (M = 26: x rows of a length that is not a multiple of 4; M = 4, 6, 10:
+    the smallest grids, where the element-wise kernels' 2 x 2 voxel blocks and
+    32-byte chunks meet the grid's edges on every side)."""
     from paper_2311_16100_gb300.ops import SGDState
     B, nb = 12, 3
     c = Case(M, B * nb, interp=interp, ctf=True, seed=29)
